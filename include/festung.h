@@ -1,0 +1,174 @@
+/*
+ * festung.h -- C ABI of the GB300 (sm_103a) LDG diffusion solver.
+ *
+ * The library discretises  dt c - div(d grad c) = f  on a triangle mesh with the
+ * local discontinuous Galerkin (LDG) method of FESTUNG Part I (arXiv:1408.3877):
+ * orthonormal modal bases of order p = 0..4 (Sec. 2.4.1), the flux unknown
+ * z = -grad c (Sec. 2.2), central fluxes with the 1/|E| penalty (Sec. 2.4.4) and
+ * implicit Euler in time (Sec. 2.5).  The flux unknown is eliminated element by
+ * element through the block-diagonal mass matrix, M = 2|T_k| I (Sec. 3.6.1), so a
+ * step solves, for the coefficients C^{n+1},
+ *
+ *   S C = M C + tau (eta (S + S_D) C - sum_m A_m M^{-1} B_m C)                 (E1)
+ *       = M C^n + tau (eta K_D - K_N + L + sum_m A_m M^{-1} J_D^m)  =: b       (E2)
+ *
+ * with B_m = -H^m + Q^m + Q_N^m and A_m = -G^m + R^m + R_D^m the block rows of the
+ * system matrix of eq. timeDepSystem.  S is applied matrix-free by CUDA kernels and
+ * the step is solved by BiCGStab (CG when S is symmetric, i.e. when d_h is
+ * elementwise constant).
+ *
+ * Conventions for every call:
+ *  - Return value 0 (FESTUNG_OK) on success, a negative FESTUNG_E* code otherwise;
+ *    festung_last_error() then returns a message.  A failed call leaves the
+ *    context's state (C, coefficients, boundary data) unchanged.
+ *  - Host arrays are read (or written) during the call only; the caller keeps
+ *    ownership.  Arrays flagged FESTUNG_DEVICE are device pointers of the current
+ *    CUDA device, read in stream order on the context's stream.
+ *  - Indices are 0-based.  Local edge n of triangle k lies opposite its vertex n
+ *    and runs from vertex n+1 to vertex n+2 (mod 3), counter-clockwise.
+ *  - "Samples" are values of a function at the physical quadrature points that
+ *    festung_quad_points() returns, in the same order.
+ *  - Coefficient arrays of the public state are K x N row-major (element-major,
+ *    the paper's global ordering (k-1)N + i).  Vectors handed to festung_apply()
+ *    use the library's device layout N x K (row j holds coefficient j of all
+ *    elements), which is the K x N array stored column-major.
+ *  - All calls on one context must come from one host thread at a time.
+ */
+#ifndef FESTUNG_H
+#define FESTUNG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FESTUNG_OK        0
+#define FESTUNG_EINVAL   -1   /* bad argument (range, NULL, unsupported order)           */
+#define FESTUNG_EMESH    -2   /* invalid mesh: orientation, non-manifold edge, markers    */
+#define FESTUNG_ENOMEM   -3   /* device or host allocation failed                        */
+#define FESTUNG_ECUDA    -4   /* CUDA runtime error                                      */
+#define FESTUNG_ENOCONV  -5   /* Krylov solve did not reach the tolerance in max_iter    */
+#define FESTUNG_ESTATE   -6   /* call out of order (e.g. apply before setup)              */
+#define FESTUNG_EDATA    -7   /* NaN/Inf in inputs or a non-positive diffusion sample     */
+
+#define FESTUNG_HOST      0
+#define FESTUNG_DEVICE    1
+
+#define FESTUNG_FP64      0   /* operator and Krylov iterations in FP64                   */
+#define FESTUNG_FP32      1   /* FP32 operator (FP32 copies of geometry, tables, D)       */
+#define FESTUNG_MIXED     2   /* step only: FP32 inner Krylov, FP64 residual refinement   */
+
+#define FESTUNG_BDR_INTERIOR  0
+#define FESTUNG_BDR_DIRICHLET 1
+#define FESTUNG_BDR_NEUMANN   2
+
+#define FESTUNG_SOLVER_CG        1
+#define FESTUNG_SOLVER_BICGSTAB  2
+
+typedef struct festung_ctx festung_ctx;
+
+typedef struct festung_step_opts {
+    double tol;          /* stop when ||b - S C||_2 <= tol ||b||_2 (unpreconditioned, over K x N) */
+    int    max_iter;     /* bound on Krylov iterations (all inner iterations in FESTUNG_MIXED)  */
+    int    prec;         /* FESTUNG_FP64 or FESTUNG_MIXED                                       */
+    double inner_tol;    /* FESTUNG_MIXED: relative reduction per inner FP32 solve (e.g. 1e-4)  */
+    int    max_outer;    /* FESTUNG_MIXED: bound on refinement sweeps                          */
+    int    solver;       /* 0: choose (CG iff S is symmetric); else FESTUNG_SOLVER_*            */
+} festung_step_opts;
+
+typedef struct festung_step_info {
+    int    iterations;   /* Krylov iterations (summed over refinement sweeps)                  */
+    int    outer;        /* refinement sweeps (1 for FESTUNG_FP64)                              */
+    double rel_residual; /* final ||b - S C||_2 / ||b||_2, evaluated in FP64                    */
+    int    solver;       /* FESTUNG_SOLVER_CG or FESTUNG_SOLVER_BICGSTAB                        */
+    int    symmetric;    /* 1 if d_h is elementwise constant (S symmetric, Sec. 2.4.3-2.4.4)   */
+} festung_step_info;
+
+/* Build the grid lists of Tab. 1 (Sec. 3.1, routine generateGridData): edges,
+ * neighbours, the affine maps F_k(x^) = B_k x^ + a_k1 (eq. affinemappings) and edge
+ * normals, and upload them to the current device.
+ *   coordV   numV x 2 vertex coordinates, row-major (host).
+ *   V0T      numT x 3 vertex indices of each triangle, counter-clockwise (host).
+ *   bdr_type numT x 3 type of local edge n of triangle k: FESTUNG_BDR_* (host).
+ *            Interior edges must be 0; every boundary edge must be 1 or 2.
+ *   out      receives the new context (owns all device memory it allocates).
+ * Errors: EINVAL (NULL, sizes), EMESH (det B_k <= 0, an edge shared by more than
+ * two triangles or traversed twice in one direction, marker mismatch, bad index),
+ * EDATA (non-finite coordinates), ENOMEM, ECUDA. */
+int festung_mesh_create(const double *coordV, int64_t numV,
+                        const int32_t *V0T, int64_t numT,
+                        const int8_t *bdr_type, festung_ctx **out);
+
+/* Choose the order and quadrature (Sec. 3.3) and build the basis/quadrature tables.
+ *   p          polynomial degree 0..4, N = (p+1)(p+2)/2 (Sec. 2.4.1).
+ *   quad_order exactness degree of the triangle rule: 0 selects 2p (the paper's
+ *              choice); otherwise 2p or 2p+1 (degree 3 is served by the degree-4
+ *              rule, degrees >= 7 by a collapsed Gauss rule).  Edges use
+ *              Gauss-Legendre exact to degree max(quad_order, 2p+1).
+ *   eta        penalty coefficient > 0 (Sec. 2.4, eta = 1 in the paper).
+ * Resets C to zero and D to the constant 1.  Errors: EINVAL, ENOMEM, ECUDA. */
+int festung_setup(festung_ctx *ctx, int p, int quad_order, double eta);
+
+/* Sizes after setup: K triangles, N local DOFs, R2 triangle and R1 edge quadrature
+ * points (any pointer may be NULL). */
+int festung_sizes(const festung_ctx *ctx, int64_t *K, int *N, int *R2, int *R1);
+
+/* Physical quadrature points F_k(q_r) (host outputs, either may be NULL):
+ *   xy   K x R2 x 2 triangle points;   exy  K x 3 x R1 x 2 Gauss points of every
+ *   local edge n, ordered along gamma_n (eq. gammaMap). */
+int festung_quad_points(const festung_ctx *ctx, double *xy, double *exy);
+
+/* L2 projection of d(t^{n+1}) (Sec. 3.4): d_samples is K x R2 at the triangle
+ * points.  Every sample must be finite and > 0 (else EDATA).  loc: FESTUNG_HOST or
+ * FESTUNG_DEVICE (FP64).  Decides whether S is symmetric (d_h elementwise constant). */
+int festung_set_coeff(festung_ctx *ctx, const double *d_samples, int loc);
+
+/* L2 projection of the source f(t^{n+1}) (K x R2 samples); NULL sets f = 0. */
+int festung_set_source(festung_ctx *ctx, const double *f_samples, int loc);
+
+/* Boundary data at t^{n+1} at the edge Gauss points, each K x 3 x R1: c_D is read
+ * on Dirichlet edges, g_N = -grad c . nu on Neumann edges (Sec. 1.1); other
+ * entries are ignored.  NULL means zero. */
+int festung_set_bc(festung_ctx *ctx, const double *cD, const double *gN, int loc);
+
+/* Set C: K x N coefficients (is_samples = 0), or K x R2 samples of c^0 that are
+ * L2-projected (is_samples = 1, Sec. 3.4). */
+int festung_set_state(festung_ctx *ctx, const double *C, int is_samples, int loc);
+
+/* Copy C (K x N, FP64) out to host or device memory. */
+int festung_get_state(const festung_ctx *ctx, double *C, int loc);
+
+/* y = S x of (E1) with the current D and time step dt (dt = 0 gives y = M x).
+ *   x, y  device arrays in the N x K layout, FP64 (prec = FESTUNG_FP64) or FP32
+ *         (prec = FESTUNG_FP32); x and y must not overlap; 16-byte aligned.
+ * Boundary data does not enter (S is the homogeneous operator). Runs on the
+ * context's stream and returns without synchronising. */
+int festung_apply(festung_ctx *ctx, const void *x, void *y, int prec, double dt);
+
+/* One implicit-Euler step of size dt (Sec. 2.5): forms b of (E2) from the current
+ * C, D, f and boundary data, solves (E1) from the initial guess C^n and, only on
+ * success, replaces C by C^{n+1}.  opts may be NULL (tol 1e-10, max_iter 20000,
+ * FESTUNG_MIXED, inner_tol 1e-4, max_outer 50).  info may be NULL.  Synchronises
+ * the context's stream.  Errors: ENOCONV (C unchanged), EINVAL, ESTATE, ECUDA. */
+int festung_step(festung_ctx *ctx, double dt, const festung_step_opts *opts,
+                 festung_step_info *info);
+
+/* Discretisation error ||c_h - c||_{L2} (Sec. 3.5) from samples of the exact c at
+ * the triangle points (K x R2, host). */
+int festung_l2_error(const festung_ctx *ctx, const double *c_samples, double *err);
+
+/* Use this CUDA stream (cudaStream_t) for all later work; NULL = legacy default. */
+int festung_set_stream(festung_ctx *ctx, void *stream);
+
+/* Message of the last failed call on ctx (or of the last failed festung_mesh_create
+ * when ctx is NULL).  Valid until the next call on the context. */
+const char *festung_last_error(const festung_ctx *ctx);
+
+/* Free the context and all its device memory.  NULL is a no-op. */
+void festung_destroy(festung_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FESTUNG_H */

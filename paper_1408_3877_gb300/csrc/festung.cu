@@ -1,0 +1,1192 @@
+// C ABI of the GB300 LDG solver: context, data upload, operator apply and the
+// implicit-Euler step (BiCGStab / CG with device-resident scalars, optionally FP32
+// inner iterations under FP64 residual refinement).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "internal.h"
+#include "krylov.cuh"
+#include "dispatch.h"
+#include "ops.h"
+
+using namespace festung;
+
+namespace festung {
+
+TableOffsets table_offsets(int N, int R2, int R1) {
+    TableOffsets o;
+    o.phiQ = 0;
+    o.wphiQ = R2 * N;
+    o.gw1 = 2 * R2 * N;
+    o.gw2 = 3 * R2 * N;
+    o.H1 = 4 * R2 * N;
+    o.H2 = o.H1 + N * N;
+    o.phiE = o.H2 + N * N;
+    o.wphiE = o.phiE + 3 * R1 * N;
+    o.total = o.wphiE + 3 * R1 * N;
+    return o;
+}
+
+template <typename T>
+struct Vecs {
+    T *Z1 = nullptr, *Z2 = nullptr;                      // flux unknowns of the apply
+    T *r = nullptr, *r0 = nullptr, *p = nullptr, *ph = nullptr, *v = nullptr;
+    T *s = nullptr, *sh = nullptr, *t = nullptr, *x = nullptr, *b = nullptr;
+    T *inv = nullptr;                                     // 1 / (2|T_k|), length K
+    bool krylov = false;
+};
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    int solver = 0, chunk = 0;
+    double tau = 0.0;
+    const void *x = nullptr, *b = nullptr;
+};
+
+struct Workspace {
+    Vecs<double> d;
+    Vecs<float> f;
+    double *part = nullptr;  // reduction partials [4][nblk]
+    KScal *scal = nullptr;   // device scalars
+    KScal *h_scal = nullptr; // pinned host mirror
+    int nblk = 0;
+    double *scratch64 = nullptr;  // W^1, W^2 of the Dirichlet lift (2 x N x K)
+    int *d_flags = nullptr, *h_flags = nullptr;
+    GraphCache g64, g32;
+};
+
+int elem_grid(const festung_ctx *c) {
+    const int64_t need = (c->K + 255) / 256;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)c->num_sms * 8));
+}
+
+}  // namespace festung
+
+namespace {
+
+thread_local std::string g_create_err;
+
+#define FCK(call)                                                                  \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            c->err = std::string(#call) + ": " + cudaGetErrorString(e_);           \
+            return e_ == cudaErrorMemoryAllocation ? FESTUNG_ENOMEM : FESTUNG_ECUDA; \
+        }                                                                          \
+    } while (0)
+
+template <typename T> const T *geomB(const festung_ctx *c);
+template <> const double *geomB<double>(const festung_ctx *c) { return c->dB; }
+template <> const float *geomB<float>(const festung_ctx *c) { return c->fB; }
+template <typename T> Vecs<T> &vecs(festung_ctx *c);
+template <> Vecs<double> &vecs<double>(festung_ctx *c) { return c->ws->d; }
+template <> Vecs<float> &vecs<float>(festung_ctx *c) { return c->ws->f; }
+
+// ---------------------------------------------------------------------------
+// projection of samples (K x R2, row-major) onto the basis (Sec. 3.4)
+// ---------------------------------------------------------------------------
+__global__ void k_project(const double *__restrict__ samp, double *__restrict__ out, float *__restrict__ out32,
+                          const double *__restrict__ wphiQ, int64_t K, int N, int R2, int check_positive,
+                          int *__restrict__ flags) {
+    extern __shared__ double sw[];
+    for (int i = threadIdx.x; i < R2 * N; i += blockDim.x) sw[i] = wphiQ[i];
+    __syncthreads();
+    int fl = 0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x) {
+        double acc[NMAX];
+        for (int j = 0; j < N; ++j) acc[j] = 0.0;
+        const double first = samp[k * R2];
+        for (int r = 0; r < R2; ++r) {
+            const double v = samp[k * R2 + r];
+            if (!isfinite(v)) fl |= 1;
+            if (check_positive && !(v > 0.0)) fl |= 2;
+            if (v != first) fl |= 4;
+            for (int j = 0; j < N; ++j) acc[j] += sw[r * N + j] * v;
+        }
+        for (int j = 0; j < N; ++j) {
+            out[j * K + k] = acc[j];
+            if (out32) out32[j * K + k] = (float)acc[j];
+        }
+    }
+    if (fl) atomicOr(flags, fl);
+}
+
+__global__ void k_check_finite(const double *__restrict__ a, int64_t n, int *__restrict__ flags) {
+    int fl = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(a[i])) fl = 1;
+    if (fl) atomicOr(flags, 1);
+}
+
+// K x N (row-major) <-> N x K
+__global__ void k_to_internal(const double *__restrict__ a, double *__restrict__ b, int64_t K, int N) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < K * N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = i / N;
+        const int j = (int)(i - k * N);
+        b[j * K + k] = a[i];
+    }
+}
+__global__ void k_to_public(const double *__restrict__ b, double *__restrict__ a, int64_t K, int N) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < K * N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = i / N;
+        const int j = (int)(i - k * N);
+        a[i] = b[j * K + k];
+    }
+}
+
+template <typename T>
+__global__ void k_inv_det(const T *__restrict__ B, T *__restrict__ inv, int64_t K) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x)
+        inv[k] = T(1) / (B[k] * B[3 * K + k] - B[K + k] * B[2 * K + k]);
+}
+
+// ---------------------------------------------------------------------------
+// Krylov vector kernels (N x K vectors, one thread per element, FP32 or FP64)
+// ---------------------------------------------------------------------------
+#define ELEM_LOOP(k) for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x)
+
+// r = b - y (y = S x, or y = null for x = 0); r0 = r; p = v = 0; partials (r,r), (b,b)
+template <typename T>
+__global__ void k_kr_init(int64_t K, int N, const T *b, const T *y, T *r, T *r0, T *p, T *v, double *part) {
+    using A = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
+    A acc[2] = {A(0), A(0)};
+    ELEM_LOOP(k) {
+        for (int j = 0; j < N; ++j) {
+            const int64_t i = j * K + k;
+            const T bi = b[i];
+            const T ri = y ? bi - y[i] : bi;
+            r[i] = ri;
+            r0[i] = ri;
+            if (p) p[i] = T(0);
+            if (v) v[i] = T(0);
+            acc[0] += (A)ri * (A)ri;
+            acc[1] += (A)bi * (A)bi;
+        }
+    }
+    block_partials<2>(acc, part);
+}
+
+__global__ void k_fin_init(KScal *sc, const double *part, int nblk, double tol) {
+    const double r2 = sum_partials(part, 0, nblk);
+    const double b2 = sum_partials(part, 1, nblk);
+    if (threadIdx.x == 0) {
+        sc->r2 = r2;
+        sc->b2 = b2;
+        sc->tol2 = tol * tol;
+        sc->rho = r2;
+        sc->alpha = 1.0;
+        sc->omega = 1.0;
+        sc->beta = 0.0;
+        sc->den = 0.0;
+        sc->iter = 0;
+        sc->breakdown = 0;
+        sc->sconv = 0;
+        sc->done = (r2 <= sc->tol2 * b2) ? 1 : 0;
+    }
+}
+
+// BiCGStab (right preconditioner P^{-1} = M^{-1}): p = r + beta (p - omega v); ph = P^{-1} p
+template <typename T>
+__global__ void k_bicg_p(int64_t K, int N, const T *r, T *p, const T *v, T *ph, const T *inv, const KScal *sc) {
+    if (sc->done) return;
+    const T beta = (T)sc->beta, omega = (T)sc->omega;
+    ELEM_LOOP(k) {
+        const T iv = inv[k];
+        for (int j = 0; j < N; ++j) {
+            const int64_t i = j * K + k;
+            const T pi = r[i] + beta * (p[i] - omega * v[i]);
+            p[i] = pi;
+            ph[i] = pi * iv;
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_dot1(int64_t K, int N, const T *a, const T *b, double *part, const KScal *sc) {
+    if (sc->done) return;
+    using A = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
+    A acc[1] = {A(0)};
+    ELEM_LOOP(k) {
+        for (int j = 0; j < N; ++j) acc[0] += (A)a[j * K + k] * (A)b[j * K + k];
+    }
+    block_partials<1>(acc, part);
+}
+
+__global__ void k_fin_alpha(KScal *sc, const double *part, int nblk) {
+    if (sc->done) return;
+    const double den = sum_partials(part, 0, nblk);
+    if (threadIdx.x == 0) {
+        sc->den = den;
+        if (!(fabs(den) > 1e-300) || !isfinite(den)) {
+            sc->breakdown = 1;
+            sc->done = 1;
+        } else {
+            sc->alpha = sc->rho / den;
+        }
+    }
+}
+
+// s = r - alpha v; sh = P^{-1} s; partial (s, s)
+template <typename T>
+__global__ void k_bicg_s(int64_t K, int N, const T *r, const T *v, T *s, T *sh, const T *inv, double *part,
+                         const KScal *sc) {
+    if (sc->done) return;
+    using A = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
+    const T alpha = (T)sc->alpha;
+    A acc[1] = {A(0)};
+    ELEM_LOOP(k) {
+        const T iv = inv[k];
+        for (int j = 0; j < N; ++j) {
+            const int64_t i = j * K + k;
+            const T si = r[i] - alpha * v[i];
+            s[i] = si;
+            sh[i] = si * iv;
+            acc[0] += (A)si * (A)si;
+        }
+    }
+    block_partials<1>(acc, part);
+}
+
+__global__ void k_fin_s(KScal *sc, const double *part, int nblk) {
+    if (sc->done) return;
+    const double s2 = sum_partials(part, 0, nblk);
+    if (threadIdx.x == 0 && s2 <= sc->tol2 * sc->b2) {
+        sc->sconv = 1;
+        sc->r2 = s2;
+        sc->iter += 1;
+        sc->done = 1;
+    }
+}
+
+template <typename T>
+__global__ void k_dot2(int64_t K, int N, const T *t, const T *s, double *part, const KScal *sc) {
+    if (sc->done) return;
+    using A = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
+    A acc[2] = {A(0), A(0)};
+    ELEM_LOOP(k) {
+        for (int j = 0; j < N; ++j) {
+            const A ti = (A)t[j * K + k];
+            acc[0] += ti * (A)s[j * K + k];
+            acc[1] += ti * ti;
+        }
+    }
+    block_partials<2>(acc, part);
+}
+
+__global__ void k_fin_omega(KScal *sc, const double *part, int nblk) {
+    if (sc->done) return;
+    const double ts = sum_partials(part, 0, nblk);
+    const double tt = sum_partials(part, 1, nblk);
+    if (threadIdx.x == 0) {
+        if (!(tt > 0.0) || !isfinite(ts) || ts == 0.0) {
+            sc->breakdown = 1;
+            sc->done = 1;
+        } else {
+            sc->omega = ts / tt;
+        }
+    }
+}
+
+// x += alpha ph + omega sh; r = s - omega t; partials (r0, r), (r, r)
+template <typename T>
+__global__ void k_bicg_xr(int64_t K, int N, T *x, const T *ph, const T *sh, const T *s, const T *t, T *r,
+                          const T *r0, double *part, const KScal *sc) {
+    if (sc->done) return;
+    using A = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
+    const T alpha = (T)sc->alpha, omega = (T)sc->omega;
+    A acc[2] = {A(0), A(0)};
+    ELEM_LOOP(k) {
+        for (int j = 0; j < N; ++j) {
+            const int64_t i = j * K + k;
+            x[i] += alpha * ph[i] + omega * sh[i];
+            const T ri = s[i] - omega * t[i];
+            r[i] = ri;
+            acc[0] += (A)r0[i] * (A)ri;
+            acc[1] += (A)ri * (A)ri;
+        }
+    }
+    block_partials<2>(acc, part);
+}
+
+__global__ void k_fin_iter(KScal *sc, const double *part, int nblk) {
+    if (sc->done) return;
+    const double rho_new = sum_partials(part, 0, nblk);
+    const double r2 = sum_partials(part, 1, nblk);
+    if (threadIdx.x == 0) {
+        sc->iter += 1;
+        sc->r2 = r2;
+        if (r2 <= sc->tol2 * sc->b2) {
+            sc->done = 1;
+        } else if (!(fabs(rho_new) > 1e-300) || !isfinite(rho_new)) {
+            sc->breakdown = 1;
+            sc->done = 1;
+        } else {
+            sc->beta = (rho_new / sc->rho) * (sc->alpha / sc->omega);
+            sc->rho = rho_new;
+        }
+    }
+}
+
+// x += alpha ph (used when BiCGStab converged on s)
+template <typename T>
+__global__ void k_axpy_alpha(int64_t K, int N, T *x, const T *ph, const KScal *sc) {
+    const T alpha = (T)sc->alpha;
+    ELEM_LOOP(k) {
+        for (int j = 0; j < N; ++j) x[j * K + k] += alpha * ph[j * K + k];
+    }
+}
+
+// CG (SPD case, preconditioner M^{-1}): init z = P^{-1} r, p = z; partial (r, z)
+template <typename T>
+__global__ void k_cg_init(int64_t K, int N, const T *r, T *p, const T *inv, double *part) {
+    using A = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
+    A acc[1] = {A(0)};
+    ELEM_LOOP(k) {
+        const T iv = inv[k];
+        for (int j = 0; j < N; ++j) {
+            const int64_t i = j * K + k;
+            const T zi = r[i] * iv;
+            p[i] = zi;
+            acc[0] += (A)r[i] * (A)zi;
+        }
+    }
+    block_partials<1>(acc, part);
+}
+
+__global__ void k_fin_cg_init(KScal *sc, const double *part, int nblk) {
+    const double rz = sum_partials(part, 0, nblk);
+    if (threadIdx.x == 0) sc->rho = rz;
+}
+
+__global__ void k_fin_cg_alpha(KScal *sc, const double *part, int nblk) {
+    if (sc->done) return;
+    const double pq = sum_partials(part, 0, nblk);
+    if (threadIdx.x == 0) {
+        if (!(pq > 0.0) || !isfinite(pq)) {
+            sc->breakdown = 1;
+            sc->done = 1;
+        } else {
+            sc->alpha = sc->rho / pq;
+        }
+    }
+}
+
+// x += alpha p; r -= alpha q; z = P^{-1} r; partials (r, z), (r, r)
+template <typename T>
+__global__ void k_cg_xr(int64_t K, int N, T *x, const T *p, const T *q, T *r, T *z, const T *inv, double *part,
+                        const KScal *sc) {
+    if (sc->done) return;
+    using A = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
+    const T alpha = (T)sc->alpha;
+    A acc[2] = {A(0), A(0)};
+    ELEM_LOOP(k) {
+        const T iv = inv[k];
+        for (int j = 0; j < N; ++j) {
+            const int64_t i = j * K + k;
+            x[i] += alpha * p[i];
+            const T ri = r[i] - alpha * q[i];
+            r[i] = ri;
+            const T zi = ri * iv;
+            z[i] = zi;
+            acc[0] += (A)ri * (A)zi;
+            acc[1] += (A)ri * (A)ri;
+        }
+    }
+    block_partials<2>(acc, part);
+}
+
+__global__ void k_fin_cg_iter(KScal *sc, const double *part, int nblk) {
+    if (sc->done) return;
+    const double rz = sum_partials(part, 0, nblk);
+    const double r2 = sum_partials(part, 1, nblk);
+    if (threadIdx.x == 0) {
+        sc->iter += 1;
+        sc->r2 = r2;
+        if (r2 <= sc->tol2 * sc->b2) {
+            sc->done = 1;
+        } else {
+            sc->beta = rz / sc->rho;
+            sc->rho = rz;
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_cg_p(int64_t K, int N, T *p, const T *z, const KScal *sc) {
+    if (sc->done) return;
+    const T beta = (T)sc->beta;
+    ELEM_LOOP(k) {
+        for (int j = 0; j < N; ++j) p[j * K + k] = z[j * K + k] + beta * p[j * K + k];
+    }
+}
+
+// refinement helpers
+__global__ void k_residual64(int64_t n, const double *b, const double *y, double *r, double *part) {
+    double acc[2] = {0.0, 0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double ri = b[i] - y[i];
+        r[i] = ri;
+        acc[0] += ri * ri;
+        acc[1] += b[i] * b[i];
+    }
+    block_partials<2>(acc, part);
+}
+
+__global__ void k_fin_sums(double *out, const double *part, int nblk, int np) {
+    for (int p = 0; p < np; ++p) {
+        const double v = sum_partials(part, p, nblk);
+        if (threadIdx.x == 0) out[p] = v;
+    }
+}
+
+__global__ void k_scale_to_f32(int64_t n, const double *a, float *b, double s) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)(a[i] * s);
+}
+
+__global__ void k_add_f32(int64_t n, double *x, const float *d, double s) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += s * (double)d[i];
+}
+
+__global__ void k_commit_coeff(int64_t n, const double *src, double *d, float *f) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = src[i];
+        d[i] = v;
+        f[i] = (float)v;
+    }
+}
+
+__global__ void k_zero_f32(int64_t n, float *a) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = 0.0f;
+}
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+int alloc_vecs(festung_ctx *c, Vecs<T> &V, bool krylov) {
+    const size_t n = (size_t)c->K * c->N * sizeof(T);
+    if (!V.Z1) {
+        FCK(cudaMalloc(&V.Z1, n));
+        FCK(cudaMalloc(&V.Z2, n));
+    }
+    if (krylov && !V.krylov) {
+        T **ptrs[] = {&V.r, &V.r0, &V.p, &V.ph, &V.v, &V.s, &V.sh, &V.t, &V.x, &V.b};
+        for (T **q : ptrs) FCK(cudaMalloc(q, n));
+        FCK(cudaMalloc(&V.inv, (size_t)c->K * sizeof(T)));
+        k_inv_det<T><<<elem_grid(c), 256, 0, c->stream>>>(geomB<T>(c), V.inv, c->K);
+        FCK(cudaGetLastError());
+        V.krylov = true;
+    }
+    return FESTUNG_OK;
+}
+
+template <typename T>
+void free_vecs(Vecs<T> &V) {
+    T *ptrs[] = {V.Z1, V.Z2, V.r, V.r0, V.p, V.ph, V.v, V.s, V.sh, V.t, V.x, V.b, V.inv};
+    for (T *q : ptrs)
+        if (q) cudaFree(q);
+    V = Vecs<T>();
+}
+
+int ensure_ws(festung_ctx *c) {
+    if (!c->ws) {
+        c->ws = new (std::nothrow) Workspace();
+        if (!c->ws) {
+            c->err = "host allocation failed";
+            return FESTUNG_ENOMEM;
+        }
+        Workspace &w = *c->ws;
+        w.nblk = std::max(1, std::min(c->num_sms * 4, (int)((c->K + RED_THREADS - 1) / RED_THREADS)));
+        FCK(cudaMalloc(&w.part, sizeof(double) * 4 * w.nblk));
+        FCK(cudaMalloc(&w.scal, sizeof(KScal)));
+        FCK(cudaMallocHost(&w.h_scal, sizeof(KScal)));
+        FCK(cudaMalloc(&w.d_flags, sizeof(int) * 4));
+        FCK(cudaMallocHost(&w.h_flags, sizeof(int) * 4));
+    }
+    return FESTUNG_OK;
+}
+
+void reset_graphs(festung_ctx *c) {
+    if (!c->ws) return;
+    for (GraphCache *g : {&c->ws->g64, &c->ws->g32}) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        *g = GraphCache();
+    }
+}
+
+void free_ctx_device(festung_ctx *c) {
+    reset_graphs(c);
+    if (c->ws) {
+        free_vecs(c->ws->d);
+        free_vecs(c->ws->f);
+        if (c->ws->part) cudaFree(c->ws->part);
+        if (c->ws->scal) cudaFree(c->ws->scal);
+        if (c->ws->h_scal) cudaFreeHost(c->ws->h_scal);
+        if (c->ws->scratch64) cudaFree(c->ws->scratch64);
+        if (c->ws->d_flags) cudaFree(c->ws->d_flags);
+        if (c->ws->h_flags) cudaFreeHost(c->ws->h_flags);
+        delete c->ws;
+        c->ws = nullptr;
+    }
+    void *ptrs[] = {c->dTab, c->fTab, c->dC, c->dD, c->dF, c->fD, c->dCD, c->dGN, c->dSamp};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    c->dTab = nullptr;
+    c->fTab = nullptr;
+    c->dC = c->dD = c->dF = c->dCD = c->dGN = c->dSamp = nullptr;
+    c->fD = nullptr;
+}
+
+int small_grid(int64_t n, const festung_ctx *c) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 8));
+}
+
+// Copy an input array (host or device) into the device buffer dst and check finiteness.
+int upload_checked(festung_ctx *c, const double *src, int loc, double *dst, int64_t n) {
+    if (loc == FESTUNG_HOST)
+        FCK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    else
+        FCK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    int rc = ensure_ws(c);
+    if (rc) return rc;
+    FCK(cudaMemsetAsync(c->ws->d_flags, 0, sizeof(int), c->stream));
+    k_check_finite<<<small_grid(n, c), 256, 0, c->stream>>>(dst, n, c->ws->d_flags);
+    FCK(cudaGetLastError());
+    FCK(cudaMemcpyAsync(c->ws->h_flags, c->ws->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    FCK(cudaStreamSynchronize(c->stream));
+    if (c->ws->h_flags[0]) {
+        c->err = "non-finite value in input";
+        return FESTUNG_EDATA;
+    }
+    return FESTUNG_OK;
+}
+
+// project K x R2 samples into out (N x K); flags: bit0 non-finite, bit1 non-positive, bit2 non-constant
+int project_samples(festung_ctx *c, const double *samples, int loc, double *out, float *out32, int check_pos,
+                    int *flags_out) {
+    int rc = ensure_ws(c);
+    if (rc) return rc;
+    const int64_t n = c->K * c->R2;
+    const double *src = samples;
+    if (loc == FESTUNG_HOST) {
+        FCK(cudaMemcpyAsync(c->dSamp, samples, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        src = c->dSamp;
+    }
+    FCK(cudaMemsetAsync(c->ws->d_flags, 0, sizeof(int), c->stream));
+    const TableOffsets o = table_offsets(c->N, c->R2, c->R1);
+    k_project<<<elem_grid(c), 256, sizeof(double) * c->R2 * c->N, c->stream>>>(
+        src, out, out32, c->dTab + o.wphiQ, c->K, c->N, c->R2, check_pos, c->ws->d_flags);
+    FCK(cudaGetLastError());
+    FCK(cudaMemcpyAsync(c->ws->h_flags, c->ws->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    FCK(cudaStreamSynchronize(c->stream));
+    *flags_out = c->ws->h_flags[0];
+    return FESTUNG_OK;
+}
+
+bool ready(festung_ctx *c) {
+    if (!c) return false;
+    if (c->p < 0) {
+        c->err = "festung_setup has not been called";
+        return false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Krylov drivers
+// ---------------------------------------------------------------------------
+constexpr int CHUNK = 8;  // iterations per captured graph
+
+// record `CHUNK` iterations of the solver on stream st
+template <typename T>
+void record_iterations(festung_ctx *c, int solver, T tau, cudaStream_t st) {
+    Workspace &w = *c->ws;
+    Vecs<T> &V = vecs<T>(c);
+    const int64_t K = c->K;
+    const int N = c->N, g = w.nblk;
+    const int *skip = &w.scal->done;
+    for (int it = 0; it < CHUNK; ++it) {
+        if (solver == FESTUNG_SOLVER_BICGSTAB) {
+            k_bicg_p<T><<<g, RED_THREADS, 0, st>>>(K, N, V.r, V.p, V.v, V.ph, V.inv, w.scal);
+            launch_apply<T>(c, V.ph, V.v, V.Z1, V.Z2, tau, skip, st);
+            k_dot1<T><<<g, RED_THREADS, 0, st>>>(K, N, V.r0, V.v, w.part, w.scal);
+            k_fin_alpha<<<1, 1024, 0, st>>>(w.scal, w.part, g);
+            k_bicg_s<T><<<g, RED_THREADS, 0, st>>>(K, N, V.r, V.v, V.s, V.sh, V.inv, w.part, w.scal);
+            k_fin_s<<<1, 1024, 0, st>>>(w.scal, w.part, g);
+            launch_apply<T>(c, V.sh, V.t, V.Z1, V.Z2, tau, skip, st);
+            k_dot2<T><<<g, RED_THREADS, 0, st>>>(K, N, V.t, V.s, w.part, w.scal);
+            k_fin_omega<<<1, 1024, 0, st>>>(w.scal, w.part, g);
+            k_bicg_xr<T><<<g, RED_THREADS, 0, st>>>(K, N, V.x, V.ph, V.sh, V.s, V.t, V.r, V.r0, w.part, w.scal);
+            k_fin_iter<<<1, 1024, 0, st>>>(w.scal, w.part, g);
+        } else {
+            // CG: p (search), v = S p, s = z
+            launch_apply<T>(c, V.p, V.v, V.Z1, V.Z2, tau, skip, st);
+            k_dot1<T><<<g, RED_THREADS, 0, st>>>(K, N, V.p, V.v, w.part, w.scal);
+            k_fin_cg_alpha<<<1, 1024, 0, st>>>(w.scal, w.part, g);
+            k_cg_xr<T><<<g, RED_THREADS, 0, st>>>(K, N, V.x, V.p, V.v, V.r, V.s, V.inv, w.part, w.scal);
+            k_fin_cg_iter<<<1, 1024, 0, st>>>(w.scal, w.part, g);
+            k_cg_p<T><<<g, RED_THREADS, 0, st>>>(K, N, V.p, V.s, w.scal);
+        }
+    }
+}
+
+template <typename T>
+GraphCache &graph_of(festung_ctx *c);
+template <>
+GraphCache &graph_of<double>(festung_ctx *c) { return c->ws->g64; }
+template <>
+GraphCache &graph_of<float>(festung_ctx *c) { return c->ws->g32; }
+
+// Solve S x = b (vectors V.x, V.b of precision T) to ||r|| <= tol ||b||.
+// x_zero: x is 0 on entry.  Returns iterations in *iters and the final recursive ||r||^2, ||b||^2.
+template <typename T>
+int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_iter, bool x_zero, int *iters,
+                 double *r2, double *b2, bool *conv) {
+    Workspace &w = *c->ws;
+    Vecs<T> &V = vecs<T>(c);
+    const int64_t K = c->K;
+    const int N = c->N, g = w.nblk;
+    cudaStream_t st = c->stream;
+    int total = 0;
+    *conv = false;
+    for (int restart = 0; restart < 8; ++restart) {
+        // r = b - S x
+        if (x_zero && restart == 0) {
+            k_kr_init<T><<<g, RED_THREADS, 0, st>>>(K, N, V.b, nullptr, V.r, V.r0, V.p, V.v, w.part);
+        } else {
+            launch_apply<T>(c, V.x, V.t, V.Z1, V.Z2, (T)tau, nullptr, st);
+            k_kr_init<T><<<g, RED_THREADS, 0, st>>>(K, N, V.b, V.t, V.r, V.r0, V.p, V.v, w.part);
+        }
+        k_fin_init<<<1, 1024, 0, st>>>(w.scal, w.part, g, tol);
+        if (solver == FESTUNG_SOLVER_CG) {
+            k_cg_init<T><<<g, RED_THREADS, 0, st>>>(K, N, V.r, V.p, V.inv, w.part);
+            k_fin_cg_init<<<1, 1024, 0, st>>>(w.scal, w.part, g);
+        }
+        FCK(cudaGetLastError());
+        // capture (or reuse) a graph of CHUNK iterations
+        GraphCache &gc = graph_of<T>(c);
+        if (!gc.exec || gc.solver != solver || gc.tau != tau) {
+            if (gc.exec) cudaGraphExecDestroy(gc.exec);
+            gc.exec = nullptr;
+            cudaStream_t cs;
+            FCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            cudaGraph_t graph;
+            FCK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            record_iterations<T>(c, solver, (T)tau, cs);
+            FCK(cudaStreamEndCapture(cs, &graph));
+            FCK(cudaGraphInstantiate(&gc.exec, graph, 0));
+            cudaGraphDestroy(graph);
+            cudaStreamDestroy(cs);
+            gc.solver = solver;
+            gc.tau = tau;
+        }
+        bool brk = false;
+        while (true) {
+            FCK(cudaMemcpyAsync(w.h_scal, w.scal, sizeof(KScal), cudaMemcpyDeviceToHost, st));
+            FCK(cudaStreamSynchronize(st));
+            const KScal h = *w.h_scal;
+            if (h.done) {
+                if (h.sconv) {
+                    k_axpy_alpha<T><<<g, RED_THREADS, 0, st>>>(K, N, V.x, V.ph, w.scal);
+                    FCK(cudaGetLastError());
+                }
+                total += h.iter;
+                *r2 = h.r2;
+                *b2 = h.b2;
+                if (h.breakdown) {
+                    brk = true;
+                } else {
+                    *conv = true;
+                }
+                break;
+            }
+            if (total + h.iter >= max_iter) {
+                total += h.iter;
+                *r2 = h.r2;
+                *b2 = h.b2;
+                *iters = total;
+                return FESTUNG_OK;
+            }
+            FCK(cudaGraphLaunch(gc.exec, st));
+        }
+        if (!brk) break;
+        // breakdown: restart from the current iterate
+    }
+    *iters = total;
+    return FESTUNG_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int festung_mesh_create(const double *coordV, int64_t numV, const int32_t *V0T, int64_t numT,
+                        const int8_t *bdr_type, festung_ctx **out) {
+    g_create_err.clear();
+    if (!out) {
+        g_create_err = "out is NULL";
+        return FESTUNG_EINVAL;
+    }
+    *out = nullptr;
+    if (!coordV || !V0T || !bdr_type || numV < 3 || numT < 1) {
+        g_create_err = "NULL array or empty mesh";
+        return FESTUNG_EINVAL;
+    }
+    festung_ctx *c = new (std::nothrow) festung_ctx();
+    if (!c) return FESTUNG_ENOMEM;
+    c->K = numT;
+    c->numV = numV;
+    std::vector<int32_t> nbr;
+    int rc = build_mesh(coordV, numV, V0T, numT, bdr_type, c->hB, nbr, c->err);
+    if (rc) {
+        g_create_err = c->err;
+        delete c;
+        return rc;
+    }
+    c->coordV.assign(coordV, coordV + 2 * numV);
+    c->V0T.assign(V0T, V0T + 3 * numT);
+    c->bdr.assign(bdr_type, bdr_type + 3 * numT);
+    for (int64_t i = 0; i < 3 * numT; ++i) {
+        if (bdr_type[i] == FESTUNG_BDR_DIRICHLET) c->has_dirichlet = true;
+        if (bdr_type[i] == FESTUNG_BDR_NEUMANN) c->has_neumann = true;
+    }
+    auto fail = [&](cudaError_t e) {
+        g_create_err = std::string("CUDA: ") + cudaGetErrorString(e);
+        free_ctx_device(c);
+        if (c->dB) cudaFree(c->dB);
+        if (c->fB) cudaFree(c->fB);
+        if (c->dNbr) cudaFree(c->dNbr);
+        delete c;
+        return e == cudaErrorMemoryAllocation ? FESTUNG_ENOMEM : FESTUNG_ECUDA;
+    };
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(e);
+    e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return fail(e);
+    const int64_t K = numT;
+    if ((e = cudaMalloc(&c->dB, 4 * K * sizeof(double))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&c->fB, 4 * K * sizeof(float))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&c->dNbr, 3 * K * sizeof(int32_t))) != cudaSuccess) return fail(e);
+    std::vector<float> fB(c->hB.begin(), c->hB.end());
+    if ((e = cudaMemcpy(c->dB, c->hB.data(), 4 * K * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(e);
+    if ((e = cudaMemcpy(c->fB, fB.data(), 4 * K * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(e);
+    if ((e = cudaMemcpy(c->dNbr, nbr.data(), 3 * K * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(e);
+    *out = c;
+    return FESTUNG_OK;
+}
+
+int festung_setup(festung_ctx *c, int p, int quad_order, double eta) {
+    if (!c) return FESTUNG_EINVAL;
+    if (p < 0 || p > PMAX) {
+        c->err = "p must be in 0..4";
+        return FESTUNG_EINVAL;
+    }
+    if (!(eta > 0.0) || !std::isfinite(eta)) {
+        c->err = "eta must be positive";
+        return FESTUNG_EINVAL;
+    }
+    int qT = quad_order == 0 ? std::max(1, 2 * p) : quad_order;
+    if (quad_order != 0 && !(quad_order == 2 * p || quad_order == 2 * p + 1 || (p == 0 && quad_order == 1))) {
+        c->err = "quad_order must be 0, 2p or 2p+1";
+        return FESTUNG_EINVAL;
+    }
+    HostTables T;
+    build_tables(p, qT, T);
+    if (!dispatch(T.N, T.R2, T.R1, [](auto, auto, auto) {})) {
+        c->err = "unsupported quadrature combination";
+        return FESTUNG_EINVAL;
+    }
+    // release previous order-dependent buffers
+    free_ctx_device(c);
+    c->p = p;
+    c->N = T.N;
+    c->R2 = T.R2;
+    c->R1 = T.R1;
+    c->qT = qT;
+    c->eta = eta;
+    c->tab = T;
+    const TableOffsets o = table_offsets(T.N, T.R2, T.R1);
+    std::vector<double> h(o.total, 0.0);
+    std::copy(T.phiQ.begin(), T.phiQ.end(), h.begin() + o.phiQ);
+    std::copy(T.wphiQ.begin(), T.wphiQ.end(), h.begin() + o.wphiQ);
+    std::copy(T.gw1.begin(), T.gw1.end(), h.begin() + o.gw1);
+    std::copy(T.gw2.begin(), T.gw2.end(), h.begin() + o.gw2);
+    std::copy(T.H1.begin(), T.H1.end(), h.begin() + o.H1);
+    std::copy(T.H2.begin(), T.H2.end(), h.begin() + o.H2);
+    std::copy(T.phiE.begin(), T.phiE.end(), h.begin() + o.phiE);
+    std::copy(T.wphiE.begin(), T.wphiE.end(), h.begin() + o.wphiE);
+    std::vector<float> hf(h.begin(), h.end());
+    const int64_t K = c->K, N = c->N;
+    FCK(cudaMalloc(&c->dTab, o.total * sizeof(double)));
+    FCK(cudaMalloc(&c->fTab, o.total * sizeof(float)));
+    FCK(cudaMemcpy(c->dTab, h.data(), o.total * sizeof(double), cudaMemcpyHostToDevice));
+    FCK(cudaMemcpy(c->fTab, hf.data(), o.total * sizeof(float), cudaMemcpyHostToDevice));
+    FCK(cudaMalloc(&c->dC, K * N * sizeof(double)));
+    FCK(cudaMalloc(&c->dD, K * N * sizeof(double)));
+    FCK(cudaMalloc(&c->fD, K * N * sizeof(float)));
+    FCK(cudaMalloc(&c->dF, K * N * sizeof(double)));
+    FCK(cudaMalloc(&c->dCD, K * 3 * c->R1 * sizeof(double)));
+    FCK(cudaMalloc(&c->dGN, K * 3 * c->R1 * sizeof(double)));
+    FCK(cudaMalloc(&c->dSamp, K * c->R2 * sizeof(double)));
+    FCK(cudaMemset(c->dC, 0, K * N * sizeof(double)));
+    FCK(cudaMemset(c->dF, 0, K * N * sizeof(double)));
+    FCK(cudaMemset(c->dCD, 0, K * 3 * c->R1 * sizeof(double)));
+    FCK(cudaMemset(c->dGN, 0, K * 3 * c->R1 * sizeof(double)));
+    // D = projection of d = 1: only the first mode, 1 / phi_1 = 1/sqrt(2)
+    std::vector<double> ones((size_t)K * c->R2, 1.0);
+    FCK(cudaMemcpy(c->dSamp, ones.data(), ones.size() * sizeof(double), cudaMemcpyHostToDevice));
+    int flags = 0;
+    int rc = project_samples(c, c->dSamp, FESTUNG_DEVICE, c->dD, c->fD, 1, &flags);
+    if (rc) return rc;
+    c->symmetric = true;
+    c->source_zero = true;
+    c->bc_zero = true;
+    return FESTUNG_OK;
+}
+
+int festung_sizes(const festung_ctx *c, int64_t *K, int *N, int *R2, int *R1) {
+    if (!c) return FESTUNG_EINVAL;
+    if (K) *K = c->K;
+    if (N) *N = c->N;
+    if (R2) *R2 = c->R2;
+    if (R1) *R1 = c->R1;
+    return FESTUNG_OK;
+}
+
+int festung_quad_points(const festung_ctx *cc, double *xy, double *exy) {
+    festung_ctx *c = const_cast<festung_ctx *>(cc);
+    if (!ready(c)) return c ? FESTUNG_ESTATE : FESTUNG_EINVAL;
+    const int64_t K = c->K;
+    const HostTables &T = c->tab;
+    for (int64_t k = 0; k < K; ++k) {
+        const double b11 = c->hB[k], b12 = c->hB[K + k], b21 = c->hB[2 * K + k], b22 = c->hB[3 * K + k];
+        const double *a1 = &c->coordV[2 * (int64_t)c->V0T[3 * k]];
+        if (xy)
+            for (int r = 0; r < c->R2; ++r) {
+                const double q1 = T.tri.x1[r], q2 = T.tri.x2[r];
+                xy[(k * c->R2 + r) * 2 + 0] = b11 * q1 + b12 * q2 + a1[0];
+                xy[(k * c->R2 + r) * 2 + 1] = b21 * q1 + b22 * q2 + a1[1];
+            }
+        if (exy)
+            for (int n = 0; n < 3; ++n)
+                for (int r = 0; r < c->R1; ++r) {
+                    const double s = T.edge.s[r];
+                    double q1 = 0, q2 = 0;
+                    if (n == 0) { q1 = 1.0 - s; q2 = s; }
+                    if (n == 1) { q1 = 0.0; q2 = 1.0 - s; }
+                    if (n == 2) { q1 = s; q2 = 0.0; }
+                    const int64_t o = ((k * 3 + n) * c->R1 + r) * 2;
+                    exy[o + 0] = b11 * q1 + b12 * q2 + a1[0];
+                    exy[o + 1] = b21 * q1 + b22 * q2 + a1[1];
+                }
+    }
+    return FESTUNG_OK;
+}
+
+int festung_set_coeff(festung_ctx *c, const double *d_samples, int loc) {
+    if (!ready(c)) return c ? FESTUNG_ESTATE : FESTUNG_EINVAL;
+    if (!d_samples || (loc != FESTUNG_HOST && loc != FESTUNG_DEVICE)) {
+        c->err = "d_samples is NULL or bad loc";
+        return FESTUNG_EINVAL;
+    }
+    int rc = ensure_ws(c);
+    if (rc) return rc;
+    const int64_t KN = c->K * c->N;
+    // project into scratch, validate, then commit (state unchanged on failure)
+    Workspace &w = *c->ws;
+    if (!w.scratch64) FCK(cudaMalloc(&w.scratch64, 2 * KN * sizeof(double)));
+    int flags = 0;
+    rc = project_samples(c, d_samples, loc, w.scratch64, nullptr, 1, &flags);
+    if (rc) return rc;
+    if (flags & 3) {
+        c->err = (flags & 1) ? "non-finite diffusion sample" : "diffusion sample <= 0";
+        return FESTUNG_EDATA;
+    }
+    k_commit_coeff<<<small_grid(KN, c), 256, 0, c->stream>>>(KN, w.scratch64, c->dD, c->fD);
+    FCK(cudaGetLastError());
+    c->symmetric = !(flags & 4);
+    return FESTUNG_OK;
+}
+
+int festung_set_source(festung_ctx *c, const double *f_samples, int loc) {
+    if (!ready(c)) return c ? FESTUNG_ESTATE : FESTUNG_EINVAL;
+    if (!f_samples) {
+        FCK(cudaMemsetAsync(c->dF, 0, c->K * c->N * sizeof(double), c->stream));
+        c->source_zero = true;
+        return FESTUNG_OK;
+    }
+    int rc = ensure_ws(c);
+    if (rc) return rc;
+    Workspace &w = *c->ws;
+    if (!w.scratch64) FCK(cudaMalloc(&w.scratch64, 2 * c->K * c->N * sizeof(double)));
+    int flags = 0;
+    rc = project_samples(c, f_samples, loc, w.scratch64, nullptr, 0, &flags);
+    if (rc) return rc;
+    if (flags & 1) {
+        c->err = "non-finite source sample";
+        return FESTUNG_EDATA;
+    }
+    FCK(cudaMemcpyAsync(c->dF, w.scratch64, c->K * c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    c->source_zero = false;
+    return FESTUNG_OK;
+}
+
+int festung_set_bc(festung_ctx *c, const double *cD, const double *gN, int loc) {
+    if (!ready(c)) return c ? FESTUNG_ESTATE : FESTUNG_EINVAL;
+    const int64_t n = c->K * 3 * c->R1;
+    int rc;
+    if (cD) {
+        if ((rc = upload_checked(c, cD, loc, c->dCD, n))) return rc;
+    } else {
+        FCK(cudaMemsetAsync(c->dCD, 0, n * sizeof(double), c->stream));
+    }
+    if (gN) {
+        if ((rc = upload_checked(c, gN, loc, c->dGN, n))) return rc;
+    } else {
+        FCK(cudaMemsetAsync(c->dGN, 0, n * sizeof(double), c->stream));
+    }
+    c->bc_zero = !cD && !gN;
+    return FESTUNG_OK;
+}
+
+int festung_set_state(festung_ctx *c, const double *C, int is_samples, int loc) {
+    if (!ready(c)) return c ? FESTUNG_ESTATE : FESTUNG_EINVAL;
+    if (!C) {
+        c->err = "C is NULL";
+        return FESTUNG_EINVAL;
+    }
+    int rc = ensure_ws(c);
+    if (rc) return rc;
+    Workspace &w = *c->ws;
+    const int64_t KN = c->K * c->N;
+    if (!w.scratch64) FCK(cudaMalloc(&w.scratch64, 2 * KN * sizeof(double)));
+    if (is_samples) {
+        int flags = 0;
+        rc = project_samples(c, C, loc, w.scratch64, nullptr, 0, &flags);
+        if (rc) return rc;
+        if (flags & 1) {
+            c->err = "non-finite sample";
+            return FESTUNG_EDATA;
+        }
+        FCK(cudaMemcpyAsync(c->dC, w.scratch64, KN * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        double *tmp = w.scratch64 + KN;
+        rc = upload_checked(c, C, loc, tmp, KN);
+        if (rc) return rc;
+        k_to_internal<<<small_grid(KN, c), 256, 0, c->stream>>>(tmp, c->dC, c->K, c->N);
+        FCK(cudaGetLastError());
+    }
+    FCK(cudaStreamSynchronize(c->stream));
+    return FESTUNG_OK;
+}
+
+int festung_get_state(const festung_ctx *cc, double *C, int loc) {
+    festung_ctx *c = const_cast<festung_ctx *>(cc);
+    if (!ready(c)) return c ? FESTUNG_ESTATE : FESTUNG_EINVAL;
+    if (!C) {
+        c->err = "C is NULL";
+        return FESTUNG_EINVAL;
+    }
+    int rc = ensure_ws(c);
+    if (rc) return rc;
+    Workspace &w = *c->ws;
+    const int64_t KN = c->K * c->N;
+    if (!w.scratch64) FCK(cudaMalloc(&w.scratch64, 2 * KN * sizeof(double)));
+    double *dst = (loc == FESTUNG_DEVICE) ? C : w.scratch64;
+    k_to_public<<<small_grid(KN, c), 256, 0, c->stream>>>(c->dC, dst, c->K, c->N);
+    FCK(cudaGetLastError());
+    if (loc == FESTUNG_HOST)
+        FCK(cudaMemcpyAsync(C, w.scratch64, KN * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    FCK(cudaStreamSynchronize(c->stream));
+    return FESTUNG_OK;
+}
+
+int festung_apply(festung_ctx *c, const void *x, void *y, int prec, double dt) {
+    if (!ready(c)) return c ? FESTUNG_ESTATE : FESTUNG_EINVAL;
+    if (!x || !y || x == y || !(dt >= 0.0) || (prec != FESTUNG_FP64 && prec != FESTUNG_FP32)) {
+        c->err = "bad apply arguments";
+        return FESTUNG_EINVAL;
+    }
+    int rc = ensure_ws(c);
+    if (rc) return rc;
+    if (prec == FESTUNG_FP64) {
+        if ((rc = alloc_vecs<double>(c, c->ws->d, false))) return rc;
+        launch_apply<double>(c, (const double *)x, (double *)y, c->ws->d.Z1, c->ws->d.Z2, dt, nullptr, c->stream);
+    } else {
+        if ((rc = alloc_vecs<float>(c, c->ws->f, false))) return rc;
+        launch_apply<float>(c, (const float *)x, (float *)y, c->ws->f.Z1, c->ws->f.Z2, (float)dt, nullptr,
+                            c->stream);
+    }
+    FCK(cudaGetLastError());
+    return FESTUNG_OK;
+}
+
+int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festung_step_info *info) {
+    if (!ready(c)) return c ? FESTUNG_ESTATE : FESTUNG_EINVAL;
+    festung_step_opts o;
+    o.tol = 1e-10;
+    o.max_iter = 20000;
+    o.prec = FESTUNG_MIXED;
+    o.inner_tol = 1e-4;
+    o.max_outer = 50;
+    o.solver = 0;
+    if (opts) o = *opts;
+    if (!(dt > 0.0) || !(o.tol > 0.0) || o.max_iter < 1 ||
+        (o.prec != FESTUNG_FP64 && o.prec != FESTUNG_MIXED) || o.max_outer < 1 ||
+        !(o.inner_tol > 0.0 && o.inner_tol < 1.0)) {
+        c->err = "bad step arguments";
+        return FESTUNG_EINVAL;
+    }
+    int rc = ensure_ws(c);
+    if (rc) return rc;
+    Workspace &w = *c->ws;
+    if ((rc = alloc_vecs<double>(c, w.d, true))) return rc;
+    if (o.prec == FESTUNG_MIXED && (rc = alloc_vecs<float>(c, w.f, true))) return rc;
+    const int solver = o.solver ? o.solver : (c->symmetric ? FESTUNG_SOLVER_CG : FESTUNG_SOLVER_BICGSTAB);
+    const int64_t K = c->K, KN = K * c->N;
+    cudaStream_t st = c->stream;
+    Vecs<double> &V = w.d;
+    if (!w.scratch64) FCK(cudaMalloc(&w.scratch64, 2 * KN * sizeof(double)));
+    // right-hand side b (E2): W^m = M^{-1} J_D^m, then b = M C^n + tau (M F + eta K_D - K_N + sum A_m W^m)
+    double *W1 = w.scratch64, *W2 = w.scratch64 + KN;
+    launch_rhs(c, W1, W2, V.b, dt, st);
+    FCK(cudaGetLastError());
+    FCK(cudaMemcpyAsync(V.x, c->dC, KN * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    int iters = 0, outer = 0;
+    double r2 = 0, b2 = 0;
+    bool conv = false;
+    double relres = 0.0;
+    if (o.prec == FESTUNG_FP64) {
+        // FP64 Krylov; verify with the true residual and restart if the recursion drifted
+        for (outer = 1; outer <= o.max_outer; ++outer) {
+            int it = 0;
+            rc = krylov_solve<double>(c, solver, dt, o.tol, o.max_iter - iters, false, &it, &r2, &b2, &conv);
+            if (rc) return rc;
+            iters += it;
+            launch_apply<double>(c, V.x, V.t, V.Z1, V.Z2, dt, nullptr, st);
+            k_residual64<<<w.nblk, RED_THREADS, 0, st>>>(KN, V.b, V.t, V.r, w.part);
+            double h[2];
+            k_fin_sums<<<1, 1024, 0, st>>>(W1, w.part, w.nblk, 2);
+            FCK(cudaMemcpyAsync(h, W1, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+            FCK(cudaStreamSynchronize(st));
+            relres = h[1] > 0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
+            if (relres <= o.tol) {
+                conv = true;
+                break;
+            }
+            conv = false;
+            if (iters >= o.max_iter) break;
+        }
+    } else {
+        // mixed precision: FP64 residual, FP32 inner solve of S d = r / ||r||, C += ||r|| d
+        Vecs<float> &F = w.f;
+        for (outer = 1; outer <= o.max_outer; ++outer) {
+            launch_apply<double>(c, V.x, V.t, V.Z1, V.Z2, dt, nullptr, st);
+            k_residual64<<<w.nblk, RED_THREADS, 0, st>>>(KN, V.b, V.t, V.r, w.part);
+            k_fin_sums<<<1, 1024, 0, st>>>(W1, w.part, w.nblk, 2);
+            double h[2];
+            FCK(cudaMemcpyAsync(h, W1, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+            FCK(cudaStreamSynchronize(st));
+            const double rn = std::sqrt(h[0]), bn = std::sqrt(h[1]);
+            relres = bn > 0 ? rn / bn : rn;
+            if (relres <= o.tol || rn == 0.0) {
+                conv = true;
+                break;
+            }
+            if (iters >= o.max_iter) break;
+            k_scale_to_f32<<<small_grid(KN, c), 256, 0, st>>>(KN, V.r, F.b, 1.0 / rn);
+            k_zero_f32<<<small_grid(KN, c), 256, 0, st>>>(KN, F.x);
+            int it = 0;
+            bool cin = false;
+            double ir2, ib2;
+            rc = krylov_solve<float>(c, solver, dt, o.inner_tol, o.max_iter - iters, true, &it, &ir2, &ib2, &cin);
+            if (rc) return rc;
+            iters += it;
+            k_add_f32<<<small_grid(KN, c), 256, 0, st>>>(KN, V.x, F.x, rn);
+            FCK(cudaGetLastError());
+        }
+        if (outer > o.max_outer) outer = o.max_outer;
+    }
+    if (info) {
+        info->iterations = iters;
+        info->outer = outer;
+        info->rel_residual = relres;
+        info->solver = solver;
+        info->symmetric = c->symmetric ? 1 : 0;
+    }
+    if (!conv) {
+        c->err = "Krylov solve did not converge (relative residual " + std::to_string(relres) + ")";
+        return FESTUNG_ENOCONV;
+    }
+    FCK(cudaMemcpyAsync(c->dC, V.x, KN * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    FCK(cudaStreamSynchronize(st));
+    return FESTUNG_OK;
+}
+
+int festung_l2_error(const festung_ctx *cc, const double *c_samples, double *err) {
+    festung_ctx *c = const_cast<festung_ctx *>(cc);
+    if (!ready(c)) return c ? FESTUNG_ESTATE : FESTUNG_EINVAL;
+    if (!c_samples || !err) {
+        c->err = "NULL argument";
+        return FESTUNG_EINVAL;
+    }
+    const int64_t K = c->K, N = c->N;
+    std::vector<double> C(K * N);
+    int rc = festung_get_state(c, C.data(), FESTUNG_HOST);
+    if (rc) return rc;
+    const HostTables &T = c->tab;
+    double s = 0.0;
+    for (int64_t k = 0; k < K; ++k) {
+        const double det = c->hB[k] * c->hB[3 * K + k] - c->hB[K + k] * c->hB[2 * K + k];
+        double e = 0.0;
+        for (int r = 0; r < c->R2; ++r) {
+            double ch = 0.0;
+            for (int j = 0; j < N; ++j) ch += C[k * N + j] * T.phiQ[r * N + j];
+            const double d = ch - c_samples[k * c->R2 + r];
+            e += T.tri.w[r] * d * d;
+        }
+        s += det * e;
+    }
+    *err = std::sqrt(s);
+    return FESTUNG_OK;
+}
+
+int festung_set_stream(festung_ctx *c, void *stream) {
+    if (!c) return FESTUNG_EINVAL;
+    c->stream = (cudaStream_t)stream;
+    return FESTUNG_OK;
+}
+
+const char *festung_last_error(const festung_ctx *c) {
+    if (!c) return g_create_err.c_str();
+    return c->err.c_str();
+}
+
+void festung_destroy(festung_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_ctx_device(c);
+    if (c->dB) cudaFree(c->dB);
+    if (c->fB) cudaFree(c->fB);
+    if (c->dNbr) cudaFree(c->dNbr);
+    delete c;
+}
+
+}  // extern "C"

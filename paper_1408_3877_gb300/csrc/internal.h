@@ -1,0 +1,102 @@
+// Internal declarations of the festung library (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/festung.h"
+
+namespace festung {
+
+constexpr int PMAX = 4;
+constexpr int NMAX = 15;
+constexpr int R2MAX = 25;
+constexpr int R1MAX = 5;
+
+struct Rule2D {
+    std::vector<double> x1, x2, w;
+};
+struct Rule1D {
+    std::vector<double> s, w;
+};
+
+int num_dofs(int p);
+int edge_points_for_degree(int q);
+Rule2D triangle_rule(int q);
+Rule1D gauss_legendre01(int n);
+void basis_eval(int N, double x1, double x2, double *phi, double *d1, double *d2);
+
+// Reference tables for one (p, quadrature) choice; row-major as indexed.
+struct HostTables {
+    int p = -1, N = 0, R2 = 0, R1 = 0, qT = 0;
+    Rule2D tri;
+    Rule1D edge;
+    std::vector<double> phiQ;   // [R2][N]  phi_j(q_r)
+    std::vector<double> wphiQ;  // [R2][N]  w_r phi_j(q_r)
+    std::vector<double> gw1;    // [R2][N]  w_r d_1 phi_i(q_r)
+    std::vector<double> gw2;    // [R2][N]  w_r d_2 phi_i(q_r)
+    std::vector<double> H1;     // [N][N]   int d_1 phi_i phi_j
+    std::vector<double> H2;     // [N][N]   int d_2 phi_i phi_j
+    std::vector<double> phiE;   // [3][R1][N] phi_j(gamma_n(s_r))
+    std::vector<double> wphiE;  // [3][R1][N] w_r phi_i(gamma_n(s_r))
+};
+void build_tables(int p, int qT, HostTables &T);
+
+// Mesh build (host): validates and produces SoA geometry and neighbour codes.
+// nbr code of local edge (k, n): interior (k+ << 2) | n+, Dirichlet -1, Neumann -2.
+int build_mesh(const double *coordV, int64_t numV, const int32_t *V0T, int64_t numT,
+               const int8_t *bdr, std::vector<double> &B /*4 x K*/, std::vector<int32_t> &nbr /*3 x K*/,
+               std::string &err);
+
+// Device-side view passed to kernels.
+template <typename T>
+struct DevMesh {
+    const T *B;          // 4 x K: B11, B12, B21, B22
+    const int32_t *nbr;  // 3 x K
+    int64_t K;
+};
+
+// Device table buffer in the layout of kernels (one contiguous block per precision).
+struct TableOffsets {
+    int phiQ, wphiQ, gw1, gw2, H1, H2, phiE, wphiE, total;
+};
+TableOffsets table_offsets(int N, int R2, int R1);
+
+struct Workspace;  // Krylov vectors
+
+}  // namespace festung
+
+struct festung_ctx {
+    int64_t K = 0, numV = 0;
+    std::vector<double> coordV;
+    std::vector<int32_t> V0T;
+    std::vector<int8_t> bdr;
+    std::vector<double> hB;  // 4 x K
+    bool has_dirichlet = false, has_neumann = false;
+    // device mesh
+    double *dB = nullptr;
+    float *fB = nullptr;
+    int32_t *dNbr = nullptr;
+    // order / tables
+    int p = -1, N = 0, R2 = 0, R1 = 0, qT = 0;
+    double eta = 1.0;
+    festung::HostTables tab;
+    double *dTab = nullptr;  // FP64 tables, layout table_offsets
+    float *fTab = nullptr;   // FP32 copy
+    // state and data (N x K unless noted)
+    double *dC = nullptr, *dD = nullptr, *dF = nullptr;
+    float *fD = nullptr;
+    double *dCD = nullptr, *dGN = nullptr;  // K x 3 x R1 boundary samples
+    double *dSamp = nullptr;                // K x R2 staging for projections
+    bool symmetric = true;
+    bool source_zero = true;
+    bool bc_zero = true;
+    // workspace
+    festung::Workspace *ws = nullptr;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    std::string err;
+};

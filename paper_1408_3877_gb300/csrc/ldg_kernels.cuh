@@ -1,0 +1,322 @@
+// Matrix-free LDG operator kernels (one thread per triangle, grid-stride).
+//
+// Vectors are stored N x K ("coefficient j of all triangles is contiguous"), so a
+// warp reading coefficient j of 32 consecutive triangles issues one coalesced
+// transaction.  Geometry is 4 x K (B11, B12, B21, B22) and the neighbour relation
+// 3 x K codes: (k+ << 2) | n+ for an interior edge, -1 Dirichlet, -2 Neumann.
+//
+// Reference tables (basis values and weighted gradients at the quadrature points)
+// are staged once per block in shared memory; every table read is warp-uniform
+// except the neighbour's edge trace, whose local edge n+ varies per thread.
+#pragma once
+
+#include <cstdint>
+
+#include "internal.h"
+
+namespace festung {
+
+constexpr int NBR_DIRICHLET = -1;
+constexpr int NBR_NEUMANN = -2;
+
+template <typename T, int N, int R2, int R1>
+struct SmemTab {
+    T phiQ[R2 * N];
+    T gw1[R2 * N];
+    T gw2[R2 * N];
+    T H1[N * N];
+    T H2[N * N];
+    T phiE[3 * R1 * N];
+    T wphiE[3 * R1 * N];
+};
+
+// Layout of the device table buffer (see table_offsets in festung.cu):
+// phiQ | wphiQ | gw1 | gw2 | H1 | H2 | phiE | wphiE
+template <typename T, int N, int R2, int R1>
+__device__ __forceinline__ void load_tables(SmemTab<T, N, R2, R1> &s, const T *__restrict__ g) {
+    const int o_phiQ = 0, o_gw1 = 2 * R2 * N, o_gw2 = 3 * R2 * N, o_H1 = 4 * R2 * N,
+              o_H2 = o_H1 + N * N, o_phiE = o_H2 + N * N, o_wphiE = o_phiE + 3 * R1 * N;
+    for (int i = threadIdx.x; i < R2 * N; i += blockDim.x) {
+        s.phiQ[i] = g[o_phiQ + i];
+        s.gw1[i] = g[o_gw1 + i];
+        s.gw2[i] = g[o_gw2 + i];
+    }
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+        s.H1[i] = g[o_H1 + i];
+        s.H2[i] = g[o_H2 + i];
+    }
+    for (int i = threadIdx.x; i < 3 * R1 * N; i += blockDim.x) {
+        s.phiE[i] = g[o_phiE + i];
+        s.wphiE[i] = g[o_wphiE + i];
+    }
+}
+
+// nu_kn |E_kn| (exterior normal times edge length) of local edge n from B_k:
+// edge 0: a3 - a2 = B(:,2) - B(:,1); edge 1: a1 - a3 = -B(:,2); edge 2: a2 - a1 = B(:,1);
+// the exterior normal of a counter-clockwise edge vector (ex, ey) is (ey, -ex).
+template <typename T>
+__device__ __forceinline__ void edge_normal(int n, T b11, T b12, T b21, T b22, T &nx, T &ny) {
+    T ex, ey;
+    if (n == 0) {
+        ex = b12 - b11;
+        ey = b22 - b21;
+    } else if (n == 1) {
+        ex = -b12;
+        ey = -b22;
+    } else {
+        ex = b11;
+        ey = b21;
+    }
+    nx = ey;
+    ny = -ex;
+}
+
+// Trace of a coefficient vector on local edge n at the R1 Gauss points.
+template <typename T, int N, int R1>
+__device__ __forceinline__ void trace_own(const T *phiE, int n, const T (&c)[N], T (&out)[R1]) {
+#pragma unroll
+    for (int r = 0; r < R1; ++r) {
+        T s = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) s += phiE[(n * R1 + r) * N + j] * c[j];
+        out[r] = s;
+    }
+}
+
+// Trace of the neighbour's field (global, N x K) on its edge n2, at the points that
+// coincide with our Gauss points: every edge-to-edge map reverses the orientation
+// (eq. mapEE), so our point r is the neighbour's point R1 - 1 - r.
+template <typename T, int N, int R1>
+__device__ __forceinline__ void trace_nbr(const T *phiE, const T *__restrict__ V, int64_t K, int64_t k2,
+                                          int n2, T (&out)[R1]) {
+#pragma unroll
+    for (int r = 0; r < R1; ++r) out[r] = T(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const T v = V[j * K + k2];
+#pragma unroll
+        for (int r = 0; r < R1; ++r) out[r] += phiE[(n2 * R1 + (R1 - 1 - r)) * N + j] * v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 1: Z^m = -M^{-1} (B_m x),  B_m = -H^m + Q^m + Q_N^m  (block rows 1-2 of
+// eq. timeDepSystem; H^m Sec. 3.6.2, Q^m eq. globQ, Q_N^m eq. globQm:N).
+// ---------------------------------------------------------------------------
+template <typename T, int N, int R2, int R1>
+__global__ void __launch_bounds__(256) k_flux(const T *__restrict__ X, T *__restrict__ Z1,
+                                              T *__restrict__ Z2, const T *__restrict__ Bg,
+                                              const int32_t *__restrict__ nbr, int64_t K,
+                                              const T *__restrict__ tabg, const int *__restrict__ skip) {
+    __shared__ SmemTab<T, N, R2, R1> s;
+    if (skip && *skip) return;
+    load_tables(s, tabg);
+    __syncthreads();
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        T x[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) x[j] = X[j * K + k];
+        const T b11 = Bg[k], b12 = Bg[K + k], b21 = Bg[2 * K + k], b22 = Bg[3 * K + k];
+        T a1[N], a2[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            T h1 = T(0), h2 = T(0);
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                h1 += s.H1[i * N + j] * x[j];
+                h2 += s.H2[i * N + j] * x[j];
+            }
+            // H^1 = B22 H^_1 - B21 H^_2, H^2 = -B12 H^_1 + B11 H^_2 (Sec. 3.6.2)
+            a1[i] = -(b22 * h1 - b21 * h2);
+            a2[i] = -(b11 * h2 - b12 * h1);
+        }
+#pragma unroll 1
+        for (int n = 0; n < 3; ++n) {
+            const int code = nbr[n * K + k];
+            if (code == NBR_DIRICHLET) continue;  // c_D enters the right-hand side only
+            T nx, ny;
+            edge_normal(n, b11, b12, b21, b22, nx, ny);
+            T f[R1];
+            trace_own<T, N, R1>(s.phiE, n, x, f);
+            if (code >= 0) {
+                T cp[R1];
+                trace_nbr<T, N, R1>(s.phiE, X, K, code >> 2, code & 3, cp);
+#pragma unroll
+                for (int r = 0; r < R1; ++r) f[r] = T(0.5) * (f[r] + cp[r]);
+            }
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                T t = T(0);
+#pragma unroll
+                for (int r = 0; r < R1; ++r) t += s.wphiE[(n * R1 + r) * N + i] * f[r];
+                a1[i] += nx * t;
+                a2[i] += ny * t;
+            }
+        }
+        const T inv = T(1) / (b11 * b22 - b12 * b21);  // M^{-1} = 1 / (2|T_k|)
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            Z1[i * K + k] = -a1[i] * inv;
+            Z2[i * K + k] = -a2[i] * inv;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 2.  MODE_APPLY:  y = M x + tau (eta (S + S_D) x + sum_m A_m Z^m)          (E1)
+//          MODE_RHS:    y = M x + tau (M F + eta K_D - K_N + sum_m A_m Z^m)     (E2)
+// with A_m = -G^m + R^m + R_D^m (G^m Sec. 3.6.3, R^m eq. globR, R_D^m eq. globR:D,
+// S eq. globS, S_D eq. globS:D, K_D eq. globK:D, K_N Sec. 3.6.12).  Volume terms use
+// the triangle rule, edge terms the Gauss rule, as the reference integrals do.
+// ---------------------------------------------------------------------------
+constexpr int MODE_APPLY = 0;
+constexpr int MODE_RHS = 1;
+
+template <typename T, int N, int R2, int R1, int MODE>
+__global__ void __launch_bounds__(256) k_apply(const T *__restrict__ X, const T *__restrict__ Z1,
+                                               const T *__restrict__ Z2, const T *__restrict__ Dc,
+                                               T *__restrict__ Y, const T *__restrict__ Bg,
+                                               const int32_t *__restrict__ nbr, int64_t K, T tau, T eta,
+                                               const T *__restrict__ tabg, const T *__restrict__ F,
+                                               const T *__restrict__ cD, const T *__restrict__ gN,
+                                               const int *__restrict__ skip) {
+    __shared__ SmemTab<T, N, R2, R1> s;
+    if (skip && *skip) return;
+    load_tables(s, tabg);
+    __syncthreads();
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        T x[N], z1[N], z2[N], d[N], acc[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            x[j] = X[j * K + k];
+            z1[j] = Z1[j * K + k];
+            z2[j] = Z2[j * K + k];
+            d[j] = Dc[j * K + k];
+            acc[j] = T(0);
+        }
+        const T b11 = Bg[k], b12 = Bg[K + k], b21 = Bg[2 * K + k], b22 = Bg[3 * K + k];
+        // volume term -sum_m G^m Z^m
+#pragma unroll 1
+        for (int r = 0; r < R2; ++r) {
+            T dv = T(0), w1 = T(0), w2 = T(0);
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                const T ph = s.phiQ[r * N + j];
+                dv += ph * d[j];
+                w1 += ph * z1[j];
+                w2 += ph * z2[j];
+            }
+            const T u = dv * (b22 * w1 - b12 * w2);
+            const T v = dv * (b11 * w2 - b21 * w1);
+#pragma unroll
+            for (int i = 0; i < N; ++i) acc[i] -= s.gw1[r * N + i] * u + s.gw2[r * N + i] * v;
+        }
+        // edge terms
+#pragma unroll 1
+        for (int n = 0; n < 3; ++n) {
+            const int code = nbr[n * K + k];
+            if (MODE == MODE_APPLY && code == NBR_NEUMANN) continue;
+            T nx, ny;
+            edge_normal(n, b11, b12, b21, b22, nx, ny);
+            T dm[R1], g[R1];
+            trace_own<T, N, R1>(s.phiE, n, d, dm);
+            if (code == NBR_NEUMANN) {
+                // -K_N: -|E| sum_r w_r phi_i d^- g_N
+                const T len = sqrt(nx * nx + ny * ny);
+#pragma unroll
+                for (int r = 0; r < R1; ++r) g[r] = -len * dm[r] * gN[(k * 3 + n) * R1 + r];
+            } else {
+                T zm1[R1], zm2[R1];
+                trace_own<T, N, R1>(s.phiE, n, z1, zm1);
+                trace_own<T, N, R1>(s.phiE, n, z2, zm2);
+                if (code >= 0) {
+                    const int64_t k2 = code >> 2;
+                    const int n2 = code & 3;
+                    T dp[R1], zp1[R1], zp2[R1];
+                    trace_nbr<T, N, R1>(s.phiE, Dc, K, k2, n2, dp);
+                    trace_nbr<T, N, R1>(s.phiE, Z1, K, k2, n2, zp1);
+                    trace_nbr<T, N, R1>(s.phiE, Z2, K, k2, n2, zp2);
+#pragma unroll
+                    for (int r = 0; r < R1; ++r)
+                        g[r] = T(0.5) * (nx * (dm[r] * zm1[r] + dp[r] * zp1[r]) +
+                                         ny * (dm[r] * zm2[r] + dp[r] * zp2[r]));
+                    if (MODE == MODE_APPLY) {
+                        T cm[R1], cp[R1];
+                        trace_own<T, N, R1>(s.phiE, n, x, cm);
+                        trace_nbr<T, N, R1>(s.phiE, X, K, k2, n2, cp);
+#pragma unroll
+                        for (int r = 0; r < R1; ++r) g[r] += eta * (cm[r] - cp[r]);
+                    }
+                } else {  // Dirichlet
+#pragma unroll
+                    for (int r = 0; r < R1; ++r) g[r] = dm[r] * (nx * zm1[r] + ny * zm2[r]);
+                    if (MODE == MODE_APPLY) {
+                        T cm[R1];
+                        trace_own<T, N, R1>(s.phiE, n, x, cm);
+#pragma unroll
+                        for (int r = 0; r < R1; ++r) g[r] += eta * cm[r];
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < R1; ++r) g[r] += eta * cD[(k * 3 + n) * R1 + r];
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                T t = T(0);
+#pragma unroll
+                for (int r = 0; r < R1; ++r) t += s.wphiE[(n * R1 + r) * N + i] * g[r];
+                acc[i] += t;
+            }
+        }
+        const T det = b11 * b22 - b12 * b21;  // M = 2|T_k| I (Sec. 3.6.1)
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            T mass = det * x[i];
+            if (MODE == MODE_RHS && F) acc[i] += det * F[i * K + k];
+            Y[i * K + k] = mass + tau * acc[i];
+        }
+    }
+}
+
+// W^m = M^{-1} J_D^m (Sec. 3.6.10): Dirichlet data lifted into the flux equation.
+template <typename T, int N, int R2, int R1>
+__global__ void __launch_bounds__(256) k_dirichlet_lift(T *__restrict__ W1, T *__restrict__ W2,
+                                                        const T *__restrict__ Bg,
+                                                        const int32_t *__restrict__ nbr, int64_t K,
+                                                        const T *__restrict__ tabg, const T *__restrict__ cD) {
+    __shared__ SmemTab<T, N, R2, R1> s;
+    load_tables(s, tabg);
+    __syncthreads();
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const T b11 = Bg[k], b12 = Bg[K + k], b21 = Bg[2 * K + k], b22 = Bg[3 * K + k];
+        T a1[N], a2[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) a1[i] = a2[i] = T(0);
+#pragma unroll
+        for (int n = 0; n < 3; ++n) {
+            if (nbr[n * K + k] != NBR_DIRICHLET) continue;
+            T nx, ny;
+            edge_normal(n, b11, b12, b21, b22, nx, ny);
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                T t = T(0);
+#pragma unroll
+                for (int r = 0; r < R1; ++r) t += s.wphiE[(n * R1 + r) * N + i] * cD[(k * 3 + n) * R1 + r];
+                a1[i] += nx * t;
+                a2[i] += ny * t;
+            }
+        }
+        const T inv = T(1) / (b11 * b22 - b12 * b21);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            W1[i * K + k] = a1[i] * inv;
+            W2[i * K + k] = a2[i] * inv;
+        }
+    }
+}
+
+}  // namespace festung

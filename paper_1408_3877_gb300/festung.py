@@ -1,0 +1,191 @@
+"""ctypes binding of the festung C ABI (include/festung.h).
+
+Argument marshalling only: every computation runs in the CUDA library.  Host arrays
+are numpy arrays; device arrays are torch CUDA tensors (torch provides device memory
+and streams).  Importing this module does not need a GPU; creating a context does.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfestung.so")
+
+OK, EINVAL, EMESH, ENOMEM, ECUDA, ENOCONV, ESTATE, EDATA = 0, -1, -2, -3, -4, -5, -6, -7
+HOST, DEVICE = 0, 1
+FP64, FP32, MIXED = 0, 1, 2
+SOLVER_CG, SOLVER_BICGSTAB = 1, 2
+BDR_INTERIOR, BDR_DIRICHLET, BDR_NEUMANN = 0, 1, 2
+
+EXPORTS = [
+    "festung_mesh_create", "festung_setup", "festung_sizes", "festung_quad_points",
+    "festung_set_coeff", "festung_set_source", "festung_set_bc", "festung_set_state",
+    "festung_get_state", "festung_apply", "festung_step", "festung_l2_error",
+    "festung_set_stream", "festung_last_error", "festung_destroy",
+]
+
+
+class StepOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("prec", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("solver", ctypes.c_int)]
+
+
+class StepInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("outer", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("solver", ctypes.c_int), ("symmetric", ctypes.c_int)]
+
+
+class FestungError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("festung error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def load(path=None):
+    """Load libfestung.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError("libfestung.so not built: run __graft_entry__.build() (%s missing)" % p)
+    lib = ctypes.CDLL(p)
+    vp, i64, dbl, cint = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    lib.festung_mesh_create.argtypes = [vp, i64, vp, i64, vp, ctypes.POINTER(vp)]
+    lib.festung_setup.argtypes = [vp, cint, cint, dbl]
+    lib.festung_sizes.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(cint), ctypes.POINTER(cint),
+                                  ctypes.POINTER(cint)]
+    lib.festung_quad_points.argtypes = [vp, vp, vp]
+    lib.festung_set_coeff.argtypes = [vp, vp, cint]
+    lib.festung_set_source.argtypes = [vp, vp, cint]
+    lib.festung_set_bc.argtypes = [vp, vp, vp, cint]
+    lib.festung_set_state.argtypes = [vp, vp, cint, cint]
+    lib.festung_get_state.argtypes = [vp, vp, cint]
+    lib.festung_apply.argtypes = [vp, vp, vp, cint, dbl]
+    lib.festung_step.argtypes = [vp, dbl, ctypes.POINTER(StepOpts), ctypes.POINTER(StepInfo)]
+    lib.festung_l2_error.argtypes = [vp, vp, ctypes.POINTER(dbl)]
+    lib.festung_set_stream.argtypes = [vp, vp]
+    lib.festung_last_error.argtypes = [vp]
+    lib.festung_last_error.restype = ctypes.c_char_p
+    lib.festung_destroy.argtypes = [vp]
+    lib.festung_destroy.restype = None
+    for name in EXPORTS:
+        if name not in ("festung_last_error", "festung_destroy"):
+            getattr(lib, name).restype = cint
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _ptr(a, dtype):
+    """(pointer, loc, keepalive) of a numpy array or a torch CUDA tensor."""
+    if a is None:
+        return None, HOST, None
+    if hasattr(a, "is_cuda") and a.is_cuda:
+        if not a.is_contiguous():
+            raise ValueError("device tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), DEVICE, a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data_as(ctypes.c_void_p), HOST, arr
+
+
+class Solver:
+    """One mesh and its LDG discretisation on the current CUDA device."""
+
+    def __init__(self, coordV, V0T, bdr_type):
+        self.lib = load()
+        cV = np.ascontiguousarray(coordV, dtype=np.float64)
+        T = np.ascontiguousarray(V0T, dtype=np.int32)
+        b = np.ascontiguousarray(bdr_type, dtype=np.int8)
+        h = ctypes.c_void_p()
+        rc = self.lib.festung_mesh_create(cV.ctypes.data, cV.shape[0], T.ctypes.data, T.shape[0], b.ctypes.data,
+                                          ctypes.byref(h))
+        if rc != OK:
+            raise FestungError(rc, self.lib.festung_last_error(None).decode())
+        self.h = h
+        self.K = T.shape[0]
+        self.N = self.R2 = self.R1 = None
+
+    def _check(self, rc):
+        if rc != OK:
+            raise FestungError(rc, self.lib.festung_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.festung_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def setup(self, p, quad_order=0, eta=1.0):
+        self._check(self.lib.festung_setup(self.h, p, quad_order, eta))
+        K, N, R2, R1 = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.festung_sizes(self.h, ctypes.byref(K), ctypes.byref(N), ctypes.byref(R2),
+                                           ctypes.byref(R1)))
+        self.p, self.N, self.R2, self.R1 = p, N.value, R2.value, R1.value
+        return self
+
+    def quad_points(self):
+        xy = np.zeros((self.K, self.R2, 2))
+        exy = np.zeros((self.K, 3, self.R1, 2))
+        self._check(self.lib.festung_quad_points(self.h, xy.ctypes.data, exy.ctypes.data))
+        return xy, exy
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream (or None for the legacy default stream)."""
+        self._check(self.lib.festung_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream if stream else 0)))
+
+    def set_coeff(self, d_samples):
+        p, loc, keep = _ptr(d_samples, np.float64)
+        self._check(self.lib.festung_set_coeff(self.h, p, loc))
+
+    def set_source(self, f_samples):
+        p, loc, keep = _ptr(f_samples, np.float64)
+        self._check(self.lib.festung_set_source(self.h, p, loc))
+
+    def set_bc(self, cD=None, gN=None):
+        p1, l1, k1 = _ptr(cD, np.float64)
+        p2, l2, k2 = _ptr(gN, np.float64)
+        loc = l1 if cD is not None else l2
+        if cD is not None and gN is not None and l1 != l2:
+            raise ValueError("cD and gN must both be host or both be device arrays")
+        self._check(self.lib.festung_set_bc(self.h, p1, p2, loc))
+
+    def set_state(self, C, is_samples=False):
+        p, loc, keep = _ptr(C, np.float64)
+        self._check(self.lib.festung_set_state(self.h, p, 1 if is_samples else 0, loc))
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.zeros((self.K, self.N))
+        p, loc, keep = _ptr(out, np.float64)
+        if loc == HOST and keep is not out:
+            raise ValueError("host output must be a contiguous float64 array")
+        self._check(self.lib.festung_get_state(self.h, p, loc))
+        return out
+
+    def apply(self, x, y, dt, prec=FP64):
+        """y = S x on device tensors of shape (N, K) (FP64 or FP32 by prec)."""
+        self._check(self.lib.festung_apply(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                           prec, dt))
+
+    def step(self, dt, tol=1e-10, prec=MIXED, max_iter=20000, inner_tol=1e-4, max_outer=50, solver=0):
+        o = StepOpts(tol, max_iter, prec, inner_tol, max_outer, solver)
+        info = StepInfo()
+        self._check(self.lib.festung_step(self.h, dt, ctypes.byref(o), ctypes.byref(info)))
+        return {"iterations": info.iterations, "outer": info.outer, "rel_residual": info.rel_residual,
+                "solver": info.solver, "symmetric": info.symmetric}
+
+    def l2_error(self, c_samples):
+        s = np.ascontiguousarray(c_samples, dtype=np.float64)
+        e = ctypes.c_double()
+        self._check(self.lib.festung_l2_error(self.h, s.ctypes.data, ctypes.byref(e)))
+        return e.value
