@@ -130,18 +130,26 @@ void gauss_jacobi(int n, double a, double b, std::vector<double> &x, std::vector
         if (s == M) xr = 1.0 - 1e-14;
         double pr, dpr;
         jacobi(n, a, b, xr, &pr, &dpr);
-        if ((pl < 0) != (pr < 0)) {
-            double lo = xl, hi = xr, r = 0.5 * (xl + xr);
-            for (int it = 0; it < 100; ++it) {
+        if (pr == 0.0) {
+            x.push_back(xr);  // grid point is a root
+        } else if (pl != 0.0 && (pl < 0) != (pr < 0)) {
+            // bisect the bracket down to 1e-6, then Newton to machine precision
+            double lo = xl, hi = xr, plo = pl;
+            while (hi - lo > 1e-6) {
+                const double m = 0.5 * (lo + hi);
+                double pm, dm;
+                jacobi(n, a, b, m, &pm, &dm);
+                if (pm == 0.0) { lo = hi = m; break; }
+                if ((pm < 0) == (plo < 0)) { lo = m; plo = pm; } else { hi = m; }
+            }
+            double r = 0.5 * (lo + hi);
+            for (int it = 0; it < 60; ++it) {
                 double pv, dv;
                 jacobi(n, a, b, r, &pv, &dv);
-                double rn = r - pv / dv;
-                if (!(rn > lo && rn < hi)) rn = 0.5 * (lo + hi);
-                double pn, dn;
-                jacobi(n, a, b, rn, &pn, &dn);
-                if ((pn < 0) == (pl < 0)) lo = rn; else hi = rn;
-                if (std::fabs(rn - r) < 1e-16) { r = rn; break; }
-                r = rn;
+                if (pv == 0.0) break;
+                const double dx = pv / dv;
+                r -= dx;
+                if (std::fabs(dx) <= 1e-17 * (1.0 + std::fabs(r))) break;
             }
             x.push_back(r);
         }
