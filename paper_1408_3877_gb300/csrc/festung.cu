@@ -921,7 +921,8 @@ int festung_set_coeff(festung_ctx *c, const double *d_samples, int loc) {
     }
     k_commit_coeff<<<small_grid(KN, c), 256, 0, c->stream>>>(KN, w.scratch64, c->dD, c->fD);
     FCK(cudaGetLastError());
-    c->symmetric = !(flags & 4);
+    // S is symmetric iff d_h is elementwise constant (always so for p = 0)
+    c->symmetric = (c->p == 0) || !(flags & 4);
     return FESTUNG_OK;
 }
 

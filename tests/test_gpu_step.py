@@ -48,7 +48,10 @@ def test_step_fp64_matches_oracle(p, mix):
     err = np.linalg.norm(C - Co) / np.linalg.norm(Co)
     assert err <= 1e-11, (err, info)
     assert info["rel_residual"] <= 1e-13
-    assert info["solver"] == F.SOLVER_BICGSTAB and info["symmetric"] == 0
+    if p == 0:  # d_h is elementwise constant for p = 0: S is symmetric, CG
+        assert info["solver"] == F.SOLVER_CG and info["symmetric"] == 1
+    else:
+        assert info["solver"] == F.SOLVER_BICGSTAB and info["symmetric"] == 0
     s.close()
 
 
