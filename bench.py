@@ -1,0 +1,369 @@
+"""Benchmark of the LDG implicit-Euler step on one GB300 (or N replicas).
+
+Workload (default): the 256 x 256 jittered square split into 131,072 triangles,
+p = 4 (N = 15, ~1.97M DOFs), triangle rule of degree 8 (25 points), Gauss rule with
+5 points, d(t, x, y) = 1 + 0.5 sin(2 pi x) cos(2 pi y) (1 + t), manufactured
+c = cos(7x) cos(7y) exp(-t) and its source, Dirichlet on x = 0, 1 and Neumann on
+y = 0, 1, dt = 1e-3, Krylov tolerance 1e-10 (FP32 inner iterations under FP64
+residual refinement).  One bench step = one implicit-Euler step: projection of the
+coefficient and the source, boundary data, right-hand side, the Krylov solve and the
+state update.  Inputs of every step are synthetic, seeded and resident in HBM
+before the timed region; all arrays exceed L2 only in part, so L2 is flushed
+between steps.
+
+Also measured: the operator apply alone (FP32 and FP64) on this workload and on the
+1024 x 1024 (2,097,152 triangles, p = 2) Gaussian-random-field workload, whose
+inputs exceed L2.
+
+`--impl reference` times the FP64 CPU oracle (sparse direct solve) instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "LDG apply DOF/s & HBM GB/s; sec per implicit step at 1e-10 rel. residual"
+CFG_NAME = "jitter256_p4"
+APPLY_CFG = "grf1024_p2"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def flops_per_element(N, R2, R1):
+    """Multiply-adds of the two operator kernels per interior triangle, times 2.
+
+    flux pass: 2 N^2 (volume, H^) + 9 R1 N (own and neighbour traces of x, test) + 6 N;
+    apply pass: 5 R2 N (d, z1, z2 at R2 points and the test) + 27 R1 N (own and
+    neighbour traces of x, d, z1, z2 and the test)."""
+    fma = 2 * N * N + 9 * R1 * N + 6 * N + 5 * R2 * N + 27 * R1 * N
+    return 2 * fma
+
+
+def bytes_per_element(N, s, geom_s):
+    """Algorithmic bytes of one apply per triangle: read x and D, write y (3 N s),
+    the 4 entries of B_k and the three neighbour words (12 B)."""
+    return 3 * N * s + 4 * geom_s + 12
+
+
+def make_problem(cfg_name, seed=11):
+    c = W.CONFIGS[cfg_name]
+    cV, V0T, side = W.square_mesh(c["n"], jitter=c["jitter"], seed=seed)
+    bdr = W.boundary_types(side, c["dirichlet"], c["neumann"])
+    return c, cV, V0T, bdr
+
+
+class Clocks:
+    """nvidia-smi sampler during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def timed_oracle_step(cfg, n_sample, p):
+    """Seconds of one oracle step (assembly + sparse direct solve) on an n_sample mesh of the workload."""
+    from oracle.solve import LDG
+    cV, V0T, side = W.square_mesh(n_sample, jitter=cfg["jitter"], seed=11)
+    bdr = W.boundary_types(side, cfg["dirichlet"], cfg["neumann"])
+    man = W.Manufactured(W.d_config2)
+    t0 = time.perf_counter()
+    L = LDG(cV, V0T, bdr, p)
+    C = L.project(lambda x, y: man.c(0.0, x, y))
+    t, tau = cfg["dt"], cfg["dt"]
+    C = L.step(C, L.project(lambda x, y: man.d(t, x, y)), L.project(lambda x, y: man.f(t, x, y)),
+               lambda x, y: man.c(t, x, y), lambda x, y: man.gN(t, x, y), tau)
+    return time.perf_counter() - t0, L.K * L.N
+
+
+def cpu_baseline(cfg, full_dofs, budget_s=15.0):
+    """The oracle as it stands, on a bounded sample: the largest mesh n_s x n_s whose
+    step fits the budget; seconds per step extrapolated linearly in DOFs."""
+    n_s, last = 8, None
+    while True:
+        sec, dofs = timed_oracle_step(cfg, n_s, cfg["p"])
+        last = (n_s, sec, dofs)
+        if sec * 4.5 > budget_s or n_s >= 64:
+            break
+        n_s *= 2
+    n_s, sec, dofs = last
+    return {"value": sec * full_dofs / dofs, "unit": "s/step", "cores": 1, "kind": "oracle",
+            "sample": "one implicit-Euler step of the same workload on a %dx%d jittered grid (%d DOFs, "
+                      "assembly + SuperLU) took %.3f s on 1 host core; scaled linearly to %d DOFs "
+                      "(optimistic for the oracle: the direct solve grows faster than linearly)"
+                      % (n_s, n_s, dofs, sec, full_dofs)}
+
+
+def step_inputs(s, cfg, man, t, to_dev):
+    xy, exy = s.quad_points()
+    X, Y = xy[..., 0], xy[..., 1]
+    EX, EY = exy[..., 0], exy[..., 1]
+    return (to_dev(man.d(t, X, Y)), to_dev(man.f(t, X, Y)), to_dev(man.c(t, EX, EY)), to_dev(man.gN(t, EX, EY)))
+
+
+def run_festung(args):
+    import torch
+    from paper_1408_3877_gb300 import festung as F
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    cfg, cV, V0T, bdr = make_problem(CFG_NAME, seed=11 + rank)
+    man = W.Manufactured(W.d_config2)
+    p, dt, tol = cfg["p"], cfg["dt"], cfg["tol"]
+    s = F.Solver(cV, V0T, bdr).setup(p)
+    stream = torch.cuda.current_stream()
+    s.set_stream(stream)
+    K, N = s.K, s.N
+    xy, exy = s.quad_points()
+    s.set_state(man.c(0.0, xy[..., 0], xy[..., 1]), is_samples=True)
+
+    nsteps = args.warmup + args.steps
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    inputs = [step_inputs(s, cfg, man, (i + 1) * dt, dev) for i in range(nsteps)]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def one_step(i):
+        d, f, cD, gN = inputs[i]
+        s.set_coeff(d)
+        s.set_source(f)
+        s.set_bc(cD, gN)
+        return s.step(dt, tol=tol, prec=F.MIXED, inner_tol=1e-4)
+
+    for i in range(args.warmup):
+        one_step(i)
+    infos, per_step = [], []
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    l0 = s.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_total = 0.0
+    for j in range(args.steps):
+        flush.zero_()
+        ev[j][0].record(stream)
+        infos.append(one_step(args.warmup + j))
+        ev[j][1].record(stream)
+    barrier()
+    clk = clocks.stop()
+    launches = s.launch_count() - l0
+    per_step = [a.elapsed_time(b) / 1e3 for a, b in ev]
+    t_total = float(sum(per_step))
+    if dist is not None:
+        tt = torch.tensor([t_total], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    sec_per_step = t_total / (args.steps * world)
+
+    # ---- end to end through host buffers (pinned), state read back every step ----
+    pin = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64).pin_memory()
+    host_inputs = [step_inputs(s, cfg, man, (nsteps + i + 1) * dt, pin) for i in range(args.steps)]
+    out = torch.empty((K, N), dtype=torch.float64).pin_memory()
+    h2d = sum(int(a.numel() * 8) for a in host_inputs[0])
+    d2h = K * N * 8
+    barrier()
+    t0 = time.perf_counter()
+    for j in range(args.steps):
+        d, f, cD, gN = host_inputs[j]
+        s._check(s.lib.festung_set_coeff(s.h, d.data_ptr(), F.HOST))
+        s._check(s.lib.festung_set_source(s.h, f.data_ptr(), F.HOST))
+        s._check(s.lib.festung_set_bc(s.h, cD.data_ptr(), gN.data_ptr(), F.HOST))
+        s.step(dt, tol=tol, prec=F.MIXED, inner_tol=1e-4)
+        s._check(s.lib.festung_get_state(s.h, out.data_ptr(), F.HOST))
+    barrier()
+    e2e = (time.perf_counter() - t0) / args.steps
+    if dist is not None:
+        tt = torch.tensor([e2e], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = float(tt.item())
+    e2e /= world
+
+    # ---- operator apply alone: this workload (L2 flushed between launches) ----
+    pk, pk_kind = peaks()
+
+    def time_apply(solver, prec, dtype, tau, reps, flush_l2):
+        x = torch.randn(solver.N, solver.K, dtype=dtype, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            solver.apply(x, y, tau, prec)
+        evs = []
+        for _ in range(reps):
+            if flush_l2:
+                flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            solver.apply(x, y, tau, prec)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in evs])) / 1e3
+
+    t_a32 = time_apply(s, F.FP32, torch.float32, dt, 20, True)
+    t_a64 = time_apply(s, F.FP64, torch.float64, dt, 5, True)
+    fl = flops_per_element(N, s.R2, s.R1) * K
+    clk_mhz = clk.get("sm_mhz") or 2070.0
+    fp32_peak = 152 * 128 * 2 * (clk.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12   # TFLOP/s at max clock
+    apply_main = {
+        "workload": CFG_NAME, "dofs": K * N,
+        "fp32": {"s": t_a32, "dof_per_s": K * N / t_a32, "tflops": fl / t_a32 / 1e12,
+                 "alg_gbs": bytes_per_element(N, 4, 4) * K / t_a32 / 1e9},
+        "fp64": {"s": t_a64, "dof_per_s": K * N / t_a64, "tflops": fl / t_a64 / 1e12,
+                 "alg_gbs": bytes_per_element(N, 8, 8) * K / t_a64 / 1e9},
+    }
+    s.close()
+
+    # ---- operator apply alone on the 2M-triangle GRF workload (inputs exceed L2) ----
+    apply_big = None
+    if not args.skip_big:
+        c3, cV3, V3, b3 = make_problem(APPLY_CFG, seed=12)
+        g = W.GaussianField(5, c3["grf_length"])
+        s3 = F.Solver(cV3, V3, b3).setup(c3["p"])
+        s3.set_stream(stream)
+        xy3, _ = s3.quad_points()
+        s3.set_coeff(np.exp(g(xy3[..., 0], xy3[..., 1])))
+        del xy3
+        K3, N3 = s3.K, s3.N
+        t3_32 = time_apply(s3, F.FP32, torch.float32, c3["dt"], 20, False)
+        t3_64 = time_apply(s3, F.FP64, torch.float64, c3["dt"], 5, False)
+        b32 = bytes_per_element(N3, 4, 4) * K3
+        b64 = bytes_per_element(N3, 8, 8) * K3
+        apply_big = {
+            "workload": APPLY_CFG, "dofs": K3 * N3,
+            "fp32": {"s": t3_32, "dof_per_s": K3 * N3 / t3_32, "alg_gbs": b32 / t3_32 / 1e9,
+                     "hbm_frac": b32 / t3_32 / 1e9 / pk["hbm_gbs"],
+                     "tflops": flops_per_element(N3, s3.R2, s3.R1) * K3 / t3_32 / 1e12},
+            "fp64": {"s": t3_64, "dof_per_s": K3 * N3 / t3_64, "alg_gbs": b64 / t3_64 / 1e9,
+                     "hbm_frac": b64 / t3_64 / 1e9 / pk["hbm_gbs"]},
+        }
+        s3.close()
+
+    if rank != 0:
+        return None
+    roof = {"bound": "alu", "kernel": "FP32 operator apply (k_flux + k_apply), %s" % CFG_NAME,
+            "achieved": apply_main["fp32"]["tflops"], "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": apply_main["fp32"]["tflops"] / fp32_peak, "traffic": None,
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock (derived; not in the measured peaks)"}
+    line = {
+        "metric": METRIC, "value": sec_per_step, "unit": "s/step", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sec_per_step * 1e3 * world, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (seeded manufactured solution on a seeded jittered mesh)",
+        "config": {"workload": CFG_NAME, "triangles": K, "p": p, "dofs": K * N, "dt": dt, "tol": tol,
+                   "precision": "FP32 inner Krylov, FP64 residual refinement", "l2": "flushed between steps",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "iterations_per_step": float(np.mean([i["iterations"] for i in infos])),
+        "outer_per_step": float(np.mean([i["outer"] for i in infos])),
+        "rel_residual_max": float(max(i["rel_residual"] for i in infos)),
+        "apply": apply_main, "apply_large": apply_big,
+        "roofline": roof,
+        "e2e": {"value": e2e, "unit": "s/step", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "peaks": pk_kind,
+    }
+    if not args.skip_cpu:
+        line["cpu_baseline"] = cpu_baseline(cfg, K * N)
+    return line
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    cfg = W.CONFIGS[CFG_NAME]
+    full = 2 * cfg["n"] ** 2 * 15
+    for _ in range(args.warmup):
+        timed_oracle_step(cfg, 16, cfg["p"])
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sec, dofs = timed_oracle_step(cfg, 32, cfg["p"])
+        vals.append(sec * full / dofs)
+    v = float(np.mean(vals))
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "s/step", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": CFG_NAME, "triangles": 2 * cfg["n"] ** 2, "p": cfg["p"], "dofs": full},
+            "cpu_baseline": {"value": v, "unit": "s/step", "cores": 1, "kind": "oracle",
+                             "sample": "each step: one oracle step (assembly + SuperLU) on a 32x32 jittered grid "
+                                       "of the workload, scaled linearly in DOFs to the full grid"},
+            "e2e": {"value": v, "unit": "s/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t0}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="festung", choices=["festung", "reference"])
+    ap.add_argument("--skip-big", action="store_true", help="skip the 2M-triangle apply measurement")
+    ap.add_argument("--skip-cpu", action="store_true", help="skip the oracle CPU baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    line = run_reference(args) if args.impl == "reference" else run_festung(args)
+    if line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

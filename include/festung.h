@@ -158,6 +158,11 @@ int festung_step(festung_ctx *ctx, double dt, const festung_step_opts *opts,
  * the triangle points (K x R2, host). */
 int festung_l2_error(const festung_ctx *ctx, const double *c_samples, double *err);
 
+/* Number of CUDA kernels this context has launched so far (kernels inside a replayed
+ * CUDA graph count one each per replay, including those that exit early because the
+ * Krylov iteration already converged).  For instrumentation; *count must not be NULL. */
+int festung_launch_count(const festung_ctx *ctx, int64_t *count);
+
 /* Use this CUDA stream (cudaStream_t) for all later work; NULL = legacy default. */
 int festung_set_stream(festung_ctx *ctx, void *stream);
 

@@ -46,6 +46,7 @@ struct Vecs {
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     int solver = 0, chunk = 0;
+    int64_t nodes = 0;
     double tau = 0.0;
     const void *x = nullptr, *b = nullptr;
 };
@@ -483,7 +484,7 @@ int alloc_vecs(festung_ctx *c, Vecs<T> &V, bool krylov) {
         T **ptrs[] = {&V.r, &V.r0, &V.p, &V.ph, &V.v, &V.s, &V.sh, &V.t, &V.x, &V.b};
         for (T **q : ptrs) FCK(cudaMalloc(q, n));
         FCK(cudaMalloc(&V.inv, (size_t)c->K * sizeof(T)));
-        k_inv_det<T><<<elem_grid(c), 256, 0, c->stream>>>(geomB<T>(c), V.inv, c->K);
+        k_inv_det<T><<<elem_grid(c), 256, 0, c->stream>>>(geomB<T>(c), V.inv, c->K); ++c->launches;
         FCK(cudaGetLastError());
         V.krylov = true;
     }
@@ -560,7 +561,7 @@ int upload_checked(festung_ctx *c, const double *src, int loc, double *dst, int6
     int rc = ensure_ws(c);
     if (rc) return rc;
     FCK(cudaMemsetAsync(c->ws->d_flags, 0, sizeof(int), c->stream));
-    k_check_finite<<<small_grid(n, c), 256, 0, c->stream>>>(dst, n, c->ws->d_flags);
+    k_check_finite<<<small_grid(n, c), 256, 0, c->stream>>>(dst, n, c->ws->d_flags); ++c->launches;
     FCK(cudaGetLastError());
     FCK(cudaMemcpyAsync(c->ws->h_flags, c->ws->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     FCK(cudaStreamSynchronize(c->stream));
@@ -585,7 +586,7 @@ int project_samples(festung_ctx *c, const double *samples, int loc, double *out,
     FCK(cudaMemsetAsync(c->ws->d_flags, 0, sizeof(int), c->stream));
     const TableOffsets o = table_offsets(c->N, c->R2, c->R1);
     k_project<<<elem_grid(c), 256, sizeof(double) * c->R2 * c->N, c->stream>>>(
-        src, out, out32, c->dTab + o.wphiQ, c->K, c->N, c->R2, check_pos, c->ws->d_flags);
+        src, out, out32, c->dTab + o.wphiQ, c->K, c->N, c->R2, check_pos, c->ws->d_flags); ++c->launches;
     FCK(cudaGetLastError());
     FCK(cudaMemcpyAsync(c->ws->h_flags, c->ws->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     FCK(cudaStreamSynchronize(c->stream));
@@ -662,15 +663,15 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
     for (int restart = 0; restart < 8; ++restart) {
         // r = b - S x
         if (x_zero && restart == 0) {
-            k_kr_init<T><<<g, RED_THREADS, 0, st>>>(K, N, V.b, nullptr, V.r, V.r0, V.p, V.v, w.part);
+            k_kr_init<T><<<g, RED_THREADS, 0, st>>>(K, N, V.b, nullptr, V.r, V.r0, V.p, V.v, w.part); ++c->launches;
         } else {
             launch_apply<T>(c, V.x, V.t, V.Z1, V.Z2, (T)tau, nullptr, st);
-            k_kr_init<T><<<g, RED_THREADS, 0, st>>>(K, N, V.b, V.t, V.r, V.r0, V.p, V.v, w.part);
+            k_kr_init<T><<<g, RED_THREADS, 0, st>>>(K, N, V.b, V.t, V.r, V.r0, V.p, V.v, w.part); ++c->launches;
         }
-        k_fin_init<<<1, 1024, 0, st>>>(w.scal, w.part, g, tol);
+        k_fin_init<<<1, 1024, 0, st>>>(w.scal, w.part, g, tol); ++c->launches;
         if (solver == FESTUNG_SOLVER_CG) {
-            k_cg_init<T><<<g, RED_THREADS, 0, st>>>(K, N, V.r, V.p, V.inv, w.part);
-            k_fin_cg_init<<<1, 1024, 0, st>>>(w.scal, w.part, g);
+            k_cg_init<T><<<g, RED_THREADS, 0, st>>>(K, N, V.r, V.p, V.inv, w.part); ++c->launches;
+            k_fin_cg_init<<<1, 1024, 0, st>>>(w.scal, w.part, g); ++c->launches;
         }
         FCK(cudaGetLastError());
         // capture (or reuse) a graph of CHUNK iterations
@@ -681,9 +682,14 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
             cudaStream_t cs;
             FCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
             cudaGraph_t graph;
+            const int64_t saved = c->launches;
             FCK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
             record_iterations<T>(c, solver, (T)tau, cs);
             FCK(cudaStreamEndCapture(cs, &graph));
+            c->launches = saved;
+            size_t nodes = 0;
+            FCK(cudaGraphGetNodes(graph, nullptr, &nodes));
+            gc.nodes = (int64_t)nodes;
             FCK(cudaGraphInstantiate(&gc.exec, graph, 0));
             cudaGraphDestroy(graph);
             cudaStreamDestroy(cs);
@@ -697,7 +703,7 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
             const KScal h = *w.h_scal;
             if (h.done) {
                 if (h.sconv) {
-                    k_axpy_alpha<T><<<g, RED_THREADS, 0, st>>>(K, N, V.x, V.ph, w.scal);
+                    k_axpy_alpha<T><<<g, RED_THREADS, 0, st>>>(K, N, V.x, V.ph, w.scal); ++c->launches;
                     FCK(cudaGetLastError());
                 }
                 total += h.iter;
@@ -718,6 +724,7 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
                 return FESTUNG_OK;
             }
             FCK(cudaGraphLaunch(gc.exec, st));
+            c->launches += gc.nodes;
         }
         if (!brk) break;
         // breakdown: restart from the current iterate
@@ -919,7 +926,7 @@ int festung_set_coeff(festung_ctx *c, const double *d_samples, int loc) {
         c->err = (flags & 1) ? "non-finite diffusion sample" : "diffusion sample <= 0";
         return FESTUNG_EDATA;
     }
-    k_commit_coeff<<<small_grid(KN, c), 256, 0, c->stream>>>(KN, w.scratch64, c->dD, c->fD);
+    k_commit_coeff<<<small_grid(KN, c), 256, 0, c->stream>>>(KN, w.scratch64, c->dD, c->fD); ++c->launches;
     FCK(cudaGetLastError());
     // S is symmetric iff d_h is elementwise constant (always so for p = 0)
     c->symmetric = (c->p == 0) || !(flags & 4);
@@ -991,7 +998,7 @@ int festung_set_state(festung_ctx *c, const double *C, int is_samples, int loc) 
         double *tmp = w.scratch64 + KN;
         rc = upload_checked(c, C, loc, tmp, KN);
         if (rc) return rc;
-        k_to_internal<<<small_grid(KN, c), 256, 0, c->stream>>>(tmp, c->dC, c->K, c->N);
+        k_to_internal<<<small_grid(KN, c), 256, 0, c->stream>>>(tmp, c->dC, c->K, c->N); ++c->launches;
         FCK(cudaGetLastError());
     }
     FCK(cudaStreamSynchronize(c->stream));
@@ -1011,7 +1018,7 @@ int festung_get_state(const festung_ctx *cc, double *C, int loc) {
     const int64_t KN = c->K * c->N;
     if (!w.scratch64) FCK(cudaMalloc(&w.scratch64, 2 * KN * sizeof(double)));
     double *dst = (loc == FESTUNG_DEVICE) ? C : w.scratch64;
-    k_to_public<<<small_grid(KN, c), 256, 0, c->stream>>>(c->dC, dst, c->K, c->N);
+    k_to_public<<<small_grid(KN, c), 256, 0, c->stream>>>(c->dC, dst, c->K, c->N); ++c->launches;
     FCK(cudaGetLastError());
     if (loc == FESTUNG_HOST)
         FCK(cudaMemcpyAsync(C, w.scratch64, KN * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -1082,9 +1089,9 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
             if (rc) return rc;
             iters += it;
             launch_apply<double>(c, V.x, V.t, V.Z1, V.Z2, dt, nullptr, st);
-            k_residual64<<<w.nblk, RED_THREADS, 0, st>>>(KN, V.b, V.t, V.r, w.part);
+            k_residual64<<<w.nblk, RED_THREADS, 0, st>>>(KN, V.b, V.t, V.r, w.part); ++c->launches;
             double h[2];
-            k_fin_sums<<<1, 1024, 0, st>>>(W1, w.part, w.nblk, 2);
+            k_fin_sums<<<1, 1024, 0, st>>>(W1, w.part, w.nblk, 2); ++c->launches;
             FCK(cudaMemcpyAsync(h, W1, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
             FCK(cudaStreamSynchronize(st));
             relres = h[1] > 0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
@@ -1100,8 +1107,8 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
         Vecs<float> &F = w.f;
         for (outer = 1; outer <= o.max_outer; ++outer) {
             launch_apply<double>(c, V.x, V.t, V.Z1, V.Z2, dt, nullptr, st);
-            k_residual64<<<w.nblk, RED_THREADS, 0, st>>>(KN, V.b, V.t, V.r, w.part);
-            k_fin_sums<<<1, 1024, 0, st>>>(W1, w.part, w.nblk, 2);
+            k_residual64<<<w.nblk, RED_THREADS, 0, st>>>(KN, V.b, V.t, V.r, w.part); ++c->launches;
+            k_fin_sums<<<1, 1024, 0, st>>>(W1, w.part, w.nblk, 2); ++c->launches;
             double h[2];
             FCK(cudaMemcpyAsync(h, W1, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
             FCK(cudaStreamSynchronize(st));
@@ -1112,15 +1119,15 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
                 break;
             }
             if (iters >= o.max_iter) break;
-            k_scale_to_f32<<<small_grid(KN, c), 256, 0, st>>>(KN, V.r, F.b, 1.0 / rn);
-            k_zero_f32<<<small_grid(KN, c), 256, 0, st>>>(KN, F.x);
+            k_scale_to_f32<<<small_grid(KN, c), 256, 0, st>>>(KN, V.r, F.b, 1.0 / rn); ++c->launches;
+            k_zero_f32<<<small_grid(KN, c), 256, 0, st>>>(KN, F.x); ++c->launches;
             int it = 0;
             bool cin = false;
             double ir2, ib2;
             rc = krylov_solve<float>(c, solver, dt, o.inner_tol, o.max_iter - iters, true, &it, &ir2, &ib2, &cin);
             if (rc) return rc;
             iters += it;
-            k_add_f32<<<small_grid(KN, c), 256, 0, st>>>(KN, V.x, F.x, rn);
+            k_add_f32<<<small_grid(KN, c), 256, 0, st>>>(KN, V.x, F.x, rn); ++c->launches;
             FCK(cudaGetLastError());
         }
         if (outer > o.max_outer) outer = o.max_outer;
@@ -1166,6 +1173,12 @@ int festung_l2_error(const festung_ctx *cc, const double *c_samples, double *err
         s += det * e;
     }
     *err = std::sqrt(s);
+    return FESTUNG_OK;
+}
+
+int festung_launch_count(const festung_ctx *c, int64_t *count) {
+    if (!c || !count) return FESTUNG_EINVAL;
+    *count = c->launches;
     return FESTUNG_OK;
 }
 

@@ -98,5 +98,6 @@ struct festung_ctx {
     festung::Workspace *ws = nullptr;
     cudaStream_t stream = nullptr;
     int num_sms = 0;
+    mutable int64_t launches = 0;  // kernels launched on behalf of this context (graph nodes counted)
     std::string err;
 };

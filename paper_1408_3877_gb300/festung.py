@@ -22,7 +22,7 @@ EXPORTS = [
     "festung_mesh_create", "festung_setup", "festung_sizes", "festung_quad_points",
     "festung_set_coeff", "festung_set_source", "festung_set_bc", "festung_set_state",
     "festung_get_state", "festung_apply", "festung_step", "festung_l2_error",
-    "festung_set_stream", "festung_last_error", "festung_destroy",
+    "festung_launch_count", "festung_set_stream", "festung_last_error", "festung_destroy",
 ]
 
 
@@ -69,6 +69,7 @@ def load(path=None):
     lib.festung_step.argtypes = [vp, dbl, ctypes.POINTER(StepOpts), ctypes.POINTER(StepInfo)]
     lib.festung_l2_error.argtypes = [vp, vp, ctypes.POINTER(dbl)]
     lib.festung_set_stream.argtypes = [vp, vp]
+    lib.festung_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
     lib.festung_last_error.argtypes = [vp]
     lib.festung_last_error.restype = ctypes.c_char_p
     lib.festung_destroy.argtypes = [vp]
@@ -183,6 +184,11 @@ class Solver:
         self._check(self.lib.festung_step(self.h, dt, ctypes.byref(o), ctypes.byref(info)))
         return {"iterations": info.iterations, "outer": info.outer, "rel_residual": info.rel_residual,
                 "solver": info.solver, "symmetric": info.symmetric}
+
+    def launch_count(self):
+        n = ctypes.c_int64()
+        self._check(self.lib.festung_launch_count(self.h, ctypes.byref(n)))
+        return n.value
 
     def l2_error(self, c_samples):
         s = np.ascontiguousarray(c_samples, dtype=np.float64)
