@@ -72,7 +72,7 @@ typedef struct festung_step_opts {
     double tol;          /* stop when ||b - S C||_2 <= tol ||b||_2 (unpreconditioned, over K x N) */
     int    max_iter;     /* bound on Krylov iterations (all inner iterations in FESTUNG_MIXED)  */
     int    prec;         /* FESTUNG_FP64 or FESTUNG_MIXED                                       */
-    double inner_tol;    /* FESTUNG_MIXED: relative reduction per inner FP32 solve (e.g. 1e-4)  */
+    double inner_tol;    /* FESTUNG_MIXED: relative reduction per inner FP32 solve (e.g. 1e-2)   */
     int    max_outer;    /* FESTUNG_MIXED: bound on refinement sweeps                          */
     int    solver;       /* 0: choose (CG iff S is symmetric); else FESTUNG_SOLVER_*            */
 } festung_step_opts;
@@ -149,7 +149,7 @@ int festung_apply(festung_ctx *ctx, const void *x, void *y, int prec, double dt)
 /* One implicit-Euler step of size dt (Sec. 2.5): forms b of (E2) from the current
  * C, D, f and boundary data, solves (E1) from the initial guess C^n and, only on
  * success, replaces C by C^{n+1}.  opts may be NULL (tol 1e-10, max_iter 20000,
- * FESTUNG_MIXED, inner_tol 1e-4, max_outer 50).  info may be NULL.  Synchronises
+ * FESTUNG_MIXED, inner_tol 1e-2, max_outer 50).  info may be NULL.  Synchronises
  * the context's stream.  Errors: ENOCONV (C unchanged), EINVAL, ESTATE, ECUDA. */
 int festung_step(festung_ctx *ctx, double dt, const festung_step_opts *opts,
                  festung_step_info *info);

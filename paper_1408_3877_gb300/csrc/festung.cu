@@ -45,7 +45,7 @@ struct Vecs {
 
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
-    int solver = 0, chunk = 0;
+    int solver = 0, chunk = 0, use_P = -1;
     int64_t nodes = 0;
     double tau = 0.0;
     const void *x = nullptr, *b = nullptr;
@@ -60,6 +60,8 @@ struct Workspace {
     int nblk = 0;
     double *scratch64 = nullptr;  // W^1, W^2 of the Dirichlet lift (2 x N x K)
     int *d_flags = nullptr, *h_flags = nullptr;
+    float *P = nullptr;        // block-Jacobi inverse blocks [(i N + j) K + k]
+    bool use_P = false;        // P is valid for the current step
     GraphCache g64, g32;
 };
 
@@ -199,12 +201,12 @@ __global__ void k_bicg_p(int64_t K, int N, const T *r, T *p, const T *v, T *ph, 
     if (sc->done) return;
     const T beta = (T)sc->beta, omega = (T)sc->omega;
     ELEM_LOOP(k) {
-        const T iv = inv[k];
+        const T iv = inv ? inv[k] : T(0);
         for (int j = 0; j < N; ++j) {
             const int64_t i = j * K + k;
             const T pi = r[i] + beta * (p[i] - omega * v[i]);
             p[i] = pi;
-            ph[i] = pi * iv;
+            if (inv) ph[i] = pi * iv;
         }
     }
 }
@@ -243,12 +245,12 @@ __global__ void k_bicg_s(int64_t K, int N, const T *r, const T *v, T *s, T *sh, 
     const T alpha = (T)sc->alpha;
     A acc[1] = {A(0)};
     ELEM_LOOP(k) {
-        const T iv = inv[k];
+        const T iv = inv ? inv[k] : T(0);
         for (int j = 0; j < N; ++j) {
             const int64_t i = j * K + k;
             const T si = r[i] - alpha * v[i];
             s[i] = si;
-            sh[i] = si * iv;
+            if (inv) sh[i] = si * iv;
             acc[0] += (A)si * (A)si;
         }
     }
@@ -388,15 +390,17 @@ __global__ void k_cg_xr(int64_t K, int N, T *x, const T *p, const T *q, T *r, T 
     const T alpha = (T)sc->alpha;
     A acc[2] = {A(0), A(0)};
     ELEM_LOOP(k) {
-        const T iv = inv[k];
+        const T iv = inv ? inv[k] : T(0);
         for (int j = 0; j < N; ++j) {
             const int64_t i = j * K + k;
             x[i] += alpha * p[i];
             const T ri = r[i] - alpha * q[i];
             r[i] = ri;
-            const T zi = ri * iv;
-            z[i] = zi;
-            acc[0] += (A)ri * (A)zi;
+            if (inv) {
+                const T zi = ri * iv;
+                z[i] = zi;
+                acc[0] += (A)ri * (A)zi;
+            }
             acc[1] += (A)ri * (A)ri;
         }
     }
@@ -535,6 +539,7 @@ void free_ctx_device(festung_ctx *c) {
         if (c->ws->h_scal) cudaFreeHost(c->ws->h_scal);
         if (c->ws->scratch64) cudaFree(c->ws->scratch64);
         if (c->ws->d_flags) cudaFree(c->ws->d_flags);
+        if (c->ws->P) cudaFree(c->ws->P);
         if (c->ws->h_flags) cudaFreeHost(c->ws->h_flags);
         delete c->ws;
         c->ws = nullptr;
@@ -616,14 +621,17 @@ void record_iterations(festung_ctx *c, int solver, T tau, cudaStream_t st) {
     const int64_t K = c->K;
     const int N = c->N, g = w.nblk;
     const int *skip = &w.scal->done;
+    const T *inv = w.use_P ? nullptr : V.inv;
     for (int it = 0; it < CHUNK; ++it) {
         if (solver == FESTUNG_SOLVER_BICGSTAB) {
-            k_bicg_p<T><<<g, RED_THREADS, 0, st>>>(K, N, V.r, V.p, V.v, V.ph, V.inv, w.scal);
+            k_bicg_p<T><<<g, RED_THREADS, 0, st>>>(K, N, V.r, V.p, V.v, V.ph, inv, w.scal);
+            if (w.use_P) launch_precond<T>(c, w.P, V.p, V.ph, nullptr, g, skip, st);
             launch_apply<T>(c, V.ph, V.v, V.Z1, V.Z2, tau, skip, st);
             k_dot1<T><<<g, RED_THREADS, 0, st>>>(K, N, V.r0, V.v, w.part, w.scal);
             k_fin_alpha<<<1, 1024, 0, st>>>(w.scal, w.part, g);
-            k_bicg_s<T><<<g, RED_THREADS, 0, st>>>(K, N, V.r, V.v, V.s, V.sh, V.inv, w.part, w.scal);
+            k_bicg_s<T><<<g, RED_THREADS, 0, st>>>(K, N, V.r, V.v, V.s, V.sh, inv, w.part, w.scal);
             k_fin_s<<<1, 1024, 0, st>>>(w.scal, w.part, g);
+            if (w.use_P) launch_precond<T>(c, w.P, V.s, V.sh, nullptr, g, skip, st);
             launch_apply<T>(c, V.sh, V.t, V.Z1, V.Z2, tau, skip, st);
             k_dot2<T><<<g, RED_THREADS, 0, st>>>(K, N, V.t, V.s, w.part, w.scal);
             k_fin_omega<<<1, 1024, 0, st>>>(w.scal, w.part, g);
@@ -634,7 +642,8 @@ void record_iterations(festung_ctx *c, int solver, T tau, cudaStream_t st) {
             launch_apply<T>(c, V.p, V.v, V.Z1, V.Z2, tau, skip, st);
             k_dot1<T><<<g, RED_THREADS, 0, st>>>(K, N, V.p, V.v, w.part, w.scal);
             k_fin_cg_alpha<<<1, 1024, 0, st>>>(w.scal, w.part, g);
-            k_cg_xr<T><<<g, RED_THREADS, 0, st>>>(K, N, V.x, V.p, V.v, V.r, V.s, V.inv, w.part, w.scal);
+            k_cg_xr<T><<<g, RED_THREADS, 0, st>>>(K, N, V.x, V.p, V.v, V.r, V.s, inv, w.part, w.scal);
+            if (w.use_P) launch_precond<T>(c, w.P, V.r, V.s, w.part, g, skip, st);
             k_fin_cg_iter<<<1, 1024, 0, st>>>(w.scal, w.part, g);
             k_cg_p<T><<<g, RED_THREADS, 0, st>>>(K, N, V.p, V.s, w.scal);
         }
@@ -670,13 +679,18 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
         }
         k_fin_init<<<1, 1024, 0, st>>>(w.scal, w.part, g, tol); ++c->launches;
         if (solver == FESTUNG_SOLVER_CG) {
-            k_cg_init<T><<<g, RED_THREADS, 0, st>>>(K, N, V.r, V.p, V.inv, w.part); ++c->launches;
+            if (w.use_P) {
+                launch_precond<T>(c, w.P, V.r, V.p, w.part, g, nullptr, st);
+            } else {
+                k_cg_init<T><<<g, RED_THREADS, 0, st>>>(K, N, V.r, V.p, V.inv, w.part);
+                ++c->launches;
+            }
             k_fin_cg_init<<<1, 1024, 0, st>>>(w.scal, w.part, g); ++c->launches;
         }
         FCK(cudaGetLastError());
         // capture (or reuse) a graph of CHUNK iterations
         GraphCache &gc = graph_of<T>(c);
-        if (!gc.exec || gc.solver != solver || gc.tau != tau) {
+        if (!gc.exec || gc.solver != solver || gc.tau != tau || gc.use_P != (int)w.use_P) {
             if (gc.exec) cudaGraphExecDestroy(gc.exec);
             gc.exec = nullptr;
             cudaStream_t cs;
@@ -695,6 +709,7 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
             cudaStreamDestroy(cs);
             gc.solver = solver;
             gc.tau = tau;
+            gc.use_P = (int)w.use_P;
         }
         bool brk = false;
         while (true) {
@@ -1052,13 +1067,14 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
     o.tol = 1e-10;
     o.max_iter = 20000;
     o.prec = FESTUNG_MIXED;
-    o.inner_tol = 1e-4;
+    o.inner_tol = 1e-2;
     o.max_outer = 50;
     o.solver = 0;
     if (opts) o = *opts;
     if (!(dt > 0.0) || !(o.tol > 0.0) || o.max_iter < 1 ||
         (o.prec != FESTUNG_FP64 && o.prec != FESTUNG_MIXED) || o.max_outer < 1 ||
-        !(o.inner_tol > 0.0 && o.inner_tol < 1.0)) {
+        !(o.inner_tol > 0.0 && o.inner_tol < 1.0) ||
+        (o.solver != 0 && o.solver != FESTUNG_SOLVER_CG && o.solver != FESTUNG_SOLVER_BICGSTAB)) {
         c->err = "bad step arguments";
         return FESTUNG_EINVAL;
     }
@@ -1068,7 +1084,7 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
     if ((rc = alloc_vecs<double>(c, w.d, true))) return rc;
     if (o.prec == FESTUNG_MIXED && (rc = alloc_vecs<float>(c, w.f, true))) return rc;
     const int solver = o.solver ? o.solver : (c->symmetric ? FESTUNG_SOLVER_CG : FESTUNG_SOLVER_BICGSTAB);
-    const int64_t K = c->K, KN = K * c->N;
+    const int64_t KN = c->K * c->N;
     cudaStream_t st = c->stream;
     Vecs<double> &V = w.d;
     if (!w.scratch64) FCK(cudaMalloc(&w.scratch64, 2 * KN * sizeof(double)));
@@ -1076,49 +1092,54 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
     double *W1 = w.scratch64, *W2 = w.scratch64 + KN;
     launch_rhs(c, W1, W2, V.b, dt, st);
     FCK(cudaGetLastError());
+    // block-Jacobi preconditioner: inverse diagonal blocks of S for this D and dt
+    if (!w.P) FCK(cudaMalloc(&w.P, (size_t)c->N * c->N * c->K * sizeof(float)));
+    FCK(cudaMemsetAsync(w.d_flags, 0, sizeof(int), st));
+    launch_blockjacobi(c, w.P, dt, w.d_flags, st);
+    FCK(cudaGetLastError());
     FCK(cudaMemcpyAsync(V.x, c->dC, KN * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    FCK(cudaMemcpyAsync(w.h_flags, w.d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FCK(cudaStreamSynchronize(st));
+    w.use_P = (w.h_flags[0] == 0);
     int iters = 0, outer = 0;
     double r2 = 0, b2 = 0;
     bool conv = false;
     double relres = 0.0;
-    if (o.prec == FESTUNG_FP64) {
-        // FP64 Krylov; verify with the true residual and restart if the recursion drifted
-        for (outer = 1; outer <= o.max_outer; ++outer) {
-            int it = 0;
-            rc = krylov_solve<double>(c, solver, dt, o.tol, o.max_iter - iters, false, &it, &r2, &b2, &conv);
-            if (rc) return rc;
-            iters += it;
-            launch_apply<double>(c, V.x, V.t, V.Z1, V.Z2, dt, nullptr, st);
-            k_residual64<<<w.nblk, RED_THREADS, 0, st>>>(KN, V.b, V.t, V.r, w.part); ++c->launches;
-            double h[2];
-            k_fin_sums<<<1, 1024, 0, st>>>(W1, w.part, w.nblk, 2); ++c->launches;
-            FCK(cudaMemcpyAsync(h, W1, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-            FCK(cudaStreamSynchronize(st));
-            relres = h[1] > 0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
-            if (relres <= o.tol) {
-                conv = true;
-                break;
-            }
-            conv = false;
-            if (iters >= o.max_iter) break;
-        }
-    } else {
-        // mixed precision: FP64 residual, FP32 inner solve of S d = r / ||r||, C += ||r|| d
+    // FP64 residual r = b - S x and its norms (rn, bn)
+    auto residual64 = [&](double *rn, double *bn) -> int {
+        launch_apply<double>(c, V.x, V.t, V.Z1, V.Z2, dt, nullptr, st);
+        k_residual64<<<w.nblk, RED_THREADS, 0, st>>>(KN, V.b, V.t, V.r, w.part);
+        k_fin_sums<<<1, 1024, 0, st>>>(W1, w.part, w.nblk, 2);
+        c->launches += 2;
+        double h[2];
+        FCK(cudaMemcpyAsync(h, W1, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        FCK(cudaStreamSynchronize(st));
+        *rn = std::sqrt(h[0]);
+        *bn = std::sqrt(h[1]);
+        return FESTUNG_OK;
+    };
+    bool fp64 = (o.prec == FESTUNG_FP64);
+    if (!fp64) {
+        // mixed precision: FP64 residual, FP32 inner solve of S d = r / ||r||, C += ||r|| d.
+        // An inner solve that does not lower the FP64 residual is undone and the step
+        // finishes in FP64.
         Vecs<float> &F = w.f;
+        double prev_rn = -1.0, last_scale = 0.0;
         for (outer = 1; outer <= o.max_outer; ++outer) {
-            launch_apply<double>(c, V.x, V.t, V.Z1, V.Z2, dt, nullptr, st);
-            k_residual64<<<w.nblk, RED_THREADS, 0, st>>>(KN, V.b, V.t, V.r, w.part); ++c->launches;
-            k_fin_sums<<<1, 1024, 0, st>>>(W1, w.part, w.nblk, 2); ++c->launches;
-            double h[2];
-            FCK(cudaMemcpyAsync(h, W1, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-            FCK(cudaStreamSynchronize(st));
-            const double rn = std::sqrt(h[0]), bn = std::sqrt(h[1]);
+            double rn, bn;
+            if ((rc = residual64(&rn, &bn))) return rc;
             relres = bn > 0 ? rn / bn : rn;
             if (relres <= o.tol || rn == 0.0) {
                 conv = true;
                 break;
             }
+            if (prev_rn >= 0.0 && !(rn < 0.9 * prev_rn)) {
+                k_add_f32<<<small_grid(KN, c), 256, 0, st>>>(KN, V.x, F.x, -last_scale); ++c->launches;
+                fp64 = true;
+                break;
+            }
             if (iters >= o.max_iter) break;
+            prev_rn = rn;
             k_scale_to_f32<<<small_grid(KN, c), 256, 0, st>>>(KN, V.r, F.b, 1.0 / rn); ++c->launches;
             k_zero_f32<<<small_grid(KN, c), 256, 0, st>>>(KN, F.x); ++c->launches;
             int it = 0;
@@ -1127,10 +1148,27 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
             rc = krylov_solve<float>(c, solver, dt, o.inner_tol, o.max_iter - iters, true, &it, &ir2, &ib2, &cin);
             if (rc) return rc;
             iters += it;
+            last_scale = rn;
             k_add_f32<<<small_grid(KN, c), 256, 0, st>>>(KN, V.x, F.x, rn); ++c->launches;
             FCK(cudaGetLastError());
         }
         if (outer > o.max_outer) outer = o.max_outer;
+    }
+    if (fp64) {
+        // FP64 Krylov; verified with the true residual and restarted if the recursion drifted
+        for (int sweep = 1; sweep <= o.max_outer; ++sweep, ++outer) {
+            int it = 0;
+            rc = krylov_solve<double>(c, solver, dt, o.tol, std::max(1, o.max_iter - iters), false, &it, &r2, &b2,
+                                      &conv);
+            if (rc) return rc;
+            iters += it;
+            double rn, bn;
+            if ((rc = residual64(&rn, &bn))) return rc;
+            relres = bn > 0 ? rn / bn : rn;
+            conv = relres <= o.tol;
+            if (conv || iters >= o.max_iter) break;
+        }
+        if (outer < 1) outer = 1;
     }
     if (info) {
         info->iterations = iters;

@@ -12,7 +12,10 @@
 
 #include <cstdint>
 
+#include <type_traits>
+
 #include "internal.h"
+#include "krylov.cuh"
 
 namespace festung {
 
@@ -317,6 +320,241 @@ __global__ void __launch_bounds__(256) k_dirichlet_lift(T *__restrict__ W1, T *_
             W2[i * K + k] = a2[i] * inv;
         }
     }
+}
+
+}  // namespace festung
+
+namespace festung {
+
+// ---------------------------------------------------------------------------
+// Diagonal blocks of the step operator, S_kk = M_k + tau (eta S_t,kk - sum_m sum_k'
+// A_m,kk' M_k'^{-1} B_m,k'k), one column per unit coefficient vector e_j of triangle
+// k.  A unit vector on k alone produces flux unknowns on k (through B_m,kk) and on
+// each interior neighbour k' (through the central flux of eq. globQ:offdiag); S_kk e_j
+// collects their contributions back on k.  Written to P[(i N + j) K + k] in FP32.
+// ---------------------------------------------------------------------------
+template <typename T, int N, int R2, int R1>
+__global__ void __launch_bounds__(128) k_blockdiag(float *__restrict__ P, const T *__restrict__ Bg,
+                                                   const int32_t *__restrict__ nbr, const T *__restrict__ Dc,
+                                                   int64_t K, T tau, T eta, const T *__restrict__ tabg) {
+    __shared__ SmemTab<T, N, R2, R1> s;
+    load_tables(s, tabg);
+    __syncthreads();
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const T b11 = Bg[k], b12 = Bg[K + k], b21 = Bg[2 * K + k], b22 = Bg[3 * K + k];
+        const T det = b11 * b22 - b12 * b21;
+        T d[N];
+#pragma unroll
+        for (int l = 0; l < N; ++l) d[l] = Dc[l * K + k];
+        int code[3];
+        T nx[3], ny[3], inv2[3];
+        T dm[3][R1], dp[3][R1];
+#pragma unroll
+        for (int n = 0; n < 3; ++n) {
+            code[n] = nbr[n * K + k];
+            edge_normal(n, b11, b12, b21, b22, nx[n], ny[n]);
+            trace_own<T, N, R1>(s.phiE, n, d, dm[n]);
+            inv2[n] = T(0);
+#pragma unroll
+            for (int r = 0; r < R1; ++r) dp[n][r] = T(0);
+            if (code[n] >= 0) {
+                const int64_t k2 = code[n] >> 2;
+                trace_nbr<T, N, R1>(s.phiE, Dc, K, k2, code[n] & 3, dp[n]);
+                inv2[n] = T(1) / (Bg[k2] * Bg[3 * K + k2] - Bg[K + k2] * Bg[2 * K + k2]);
+            }
+        }
+        T dq[R2];
+#pragma unroll 1
+        for (int r = 0; r < R2; ++r) {
+            T v = T(0);
+#pragma unroll
+            for (int l = 0; l < N; ++l) v += s.phiQ[r * N + l] * d[l];
+            dq[r] = v;
+        }
+#pragma unroll 1
+        for (int j = 0; j < N; ++j) {
+            // Z_k = -M_k^{-1} B_m,kk e_j
+            T z1[N], z2[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const T h1 = s.H1[i * N + j], h2 = s.H2[i * N + j];
+                z1[i] = -(b22 * h1 - b21 * h2);
+                z2[i] = -(b11 * h2 - b12 * h1);
+            }
+#pragma unroll
+            for (int n = 0; n < 3; ++n) {
+                if (code[n] == NBR_DIRICHLET) continue;
+                const T fac = code[n] >= 0 ? T(0.5) : T(1);
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    T t = T(0);
+#pragma unroll
+                    for (int r = 0; r < R1; ++r) t += s.wphiE[(n * R1 + r) * N + i] * s.phiE[(n * R1 + r) * N + j];
+                    z1[i] += fac * nx[n] * t;
+                    z2[i] += fac * ny[n] * t;
+                }
+            }
+            const T idet = T(1) / det;
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                z1[i] *= -idet;
+                z2[i] *= -idet;
+            }
+            T acc[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i) acc[i] = T(0);
+            // volume term -sum_m G^m Z^m
+#pragma unroll 1
+            for (int r = 0; r < R2; ++r) {
+                T w1 = T(0), w2 = T(0);
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    w1 += s.phiQ[r * N + i] * z1[i];
+                    w2 += s.phiQ[r * N + i] * z2[i];
+                }
+                const T u = dq[r] * (b22 * w1 - b12 * w2);
+                const T v = dq[r] * (b11 * w2 - b21 * w1);
+#pragma unroll
+                for (int i = 0; i < N; ++i) acc[i] -= s.gw1[r * N + i] * u + s.gw2[r * N + i] * v;
+            }
+#pragma unroll 1
+            for (int n = 0; n < 3; ++n) {
+                if (code[n] == NBR_NEUMANN) continue;
+                T zm1[R1], zm2[R1], g[R1];
+                trace_own<T, N, R1>(s.phiE, n, z1, zm1);
+                trace_own<T, N, R1>(s.phiE, n, z2, zm2);
+                if (code[n] >= 0) {
+                    const int n2 = code[n] & 3;
+                    // neighbour's flux unknown from the trace of e_j: Z_k' = -M_k'^{-1} (1/2) nu_k'n' |E| S^(n', n) e_j,
+                    // with nu_k'n' |E| = -nu_kn |E|
+                    T q[N];
+#pragma unroll
+                    for (int i = 0; i < N; ++i) {
+                        T t = T(0);
+#pragma unroll
+                        for (int r = 0; r < R1; ++r)
+                            t += s.wphiE[(n2 * R1 + r) * N + i] * s.phiE[(n * R1 + (R1 - 1 - r)) * N + j];
+                        q[i] = t;
+                    }
+                    T qt[R1];
+#pragma unroll
+                    for (int r = 0; r < R1; ++r) {
+                        T t = T(0);
+#pragma unroll
+                        for (int i = 0; i < N; ++i) t += s.phiE[(n2 * R1 + (R1 - 1 - r)) * N + i] * q[i];
+                        qt[r] = t;
+                    }
+                    const T c2 = T(0.5) * inv2[n];  // -M^{-1} * 1/2 * (-nu |E|) = +1/2 nu |E| / det'
+#pragma unroll
+                    for (int r = 0; r < R1; ++r) {
+                        const T zp1 = c2 * nx[n] * qt[r], zp2 = c2 * ny[n] * qt[r];
+                        const T cm = s.phiE[(n * R1 + r) * N + j];
+                        g[r] = T(0.5) * (nx[n] * (dm[n][r] * zm1[r] + dp[n][r] * zp1) +
+                                         ny[n] * (dm[n][r] * zm2[r] + dp[n][r] * zp2)) +
+                               eta * cm;
+                    }
+                } else {  // Dirichlet
+#pragma unroll
+                    for (int r = 0; r < R1; ++r)
+                        g[r] = dm[n][r] * (nx[n] * zm1[r] + ny[n] * zm2[r]) + eta * s.phiE[(n * R1 + r) * N + j];
+                }
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    T t = T(0);
+#pragma unroll
+                    for (int r = 0; r < R1; ++r) t += s.wphiE[(n * R1 + r) * N + i] * g[r];
+                    acc[i] += t;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < N; ++i)
+                P[(int64_t)(i * N + j) * K + k] = (float)((i == j ? det : T(0)) + tau * acc[i]);
+        }
+    }
+}
+
+// In-place inverse of every N x N block of P (layout [(i N + j) K + k]) by Gauss-Jordan
+// elimination with partial pivoting in FP64.  flags |= 1 if a block is singular.
+template <int N>
+__global__ void __launch_bounds__(128) k_blockinv(float *__restrict__ P, int64_t K, int *__restrict__ flags) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        double A[N][N], X[N][N];
+        for (int i = 0; i < N; ++i)
+            for (int j = 0; j < N; ++j) {
+                A[i][j] = (double)P[(int64_t)(i * N + j) * K + k];
+                X[i][j] = (i == j) ? 1.0 : 0.0;
+            }
+        bool bad = false;
+        for (int c = 0; c < N; ++c) {
+            int piv = c;
+            double best = fabs(A[c][c]);
+            for (int i = c + 1; i < N; ++i)
+                if (fabs(A[i][c]) > best) {
+                    best = fabs(A[i][c]);
+                    piv = i;
+                }
+            if (!(best > 0.0)) {
+                bad = true;
+                break;
+            }
+            if (piv != c)
+                for (int j = 0; j < N; ++j) {
+                    double t = A[c][j];
+                    A[c][j] = A[piv][j];
+                    A[piv][j] = t;
+                    t = X[c][j];
+                    X[c][j] = X[piv][j];
+                    X[piv][j] = t;
+                }
+            const double ip = 1.0 / A[c][c];
+            for (int j = 0; j < N; ++j) {
+                A[c][j] *= ip;
+                X[c][j] *= ip;
+            }
+            for (int i = 0; i < N; ++i) {
+                if (i == c) continue;
+                const double f = A[i][c];
+                if (f == 0.0) continue;
+                for (int j = 0; j < N; ++j) {
+                    A[i][j] -= f * A[c][j];
+                    X[i][j] -= f * X[c][j];
+                }
+            }
+        }
+        if (bad) {
+            atomicOr(flags, 1);
+            continue;
+        }
+        for (int i = 0; i < N; ++i)
+            for (int j = 0; j < N; ++j) P[(int64_t)(i * N + j) * K + k] = (float)X[i][j];
+    }
+}
+
+// y_k = P_k x_k for every triangle (block-Jacobi preconditioner); optionally the
+// partial dot product (r, y) with r = x.
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_precond(const float *__restrict__ P, const T *__restrict__ X,
+                                                 T *__restrict__ Y, int64_t K, double *part, const int *skip) {
+    if (skip && *skip) return;
+    using A = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
+    A acc[1] = {A(0)};
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        T x[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) x[j] = X[j * K + k];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            T y = T(0);
+#pragma unroll
+            for (int j = 0; j < N; ++j) y += (T)P[(int64_t)(i * N + j) * K + k] * x[j];
+            Y[i * K + k] = y;
+            if (part) acc[0] += (A)y * (A)x[i];
+        }
+    }
+    if (part) block_partials<1>(acc, part);
 }
 
 }  // namespace festung

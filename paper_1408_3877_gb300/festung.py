@@ -178,7 +178,7 @@ class Solver:
         self._check(self.lib.festung_apply(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                                            prec, dt))
 
-    def step(self, dt, tol=1e-10, prec=MIXED, max_iter=20000, inner_tol=1e-4, max_outer=50, solver=0):
+    def step(self, dt, tol=1e-10, prec=MIXED, max_iter=20000, inner_tol=1e-2, max_outer=50, solver=0):
         o = StepOpts(tol, max_iter, prec, inner_tol, max_outer, solver)
         info = StepInfo()
         self._check(self.lib.festung_step(self.h, dt, ctypes.byref(o), ctypes.byref(info)))
