@@ -349,6 +349,30 @@ def run_reference(args):
             "wall_s": time.perf_counter() - t0}
 
 
+def profile_apply(args):
+    """Operator apply alone on one workload, `reps` launches after 2 warm-up launches."""
+    import torch
+    from paper_1408_3877_gb300 import festung as F
+    c, cV, V0T, bdr = make_problem(args.profile_apply, seed=12)
+    s = F.Solver(cV, V0T, bdr).setup(c["p"])
+    xy, _ = s.quad_points()
+    if c["coeff"] == "grf":
+        g = W.GaussianField(5, c["grf_length"])
+        s.set_coeff(np.exp(g(xy[..., 0], xy[..., 1])))
+    else:
+        s.set_coeff(W.d_config2(0.5, xy[..., 0], xy[..., 1])[0])
+    prec, dt = (F.FP32, torch.float32) if args.prec == "fp32" else (F.FP64, torch.float64)
+    x = torch.randn(s.N, s.K, dtype=dt, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(2 + args.reps):
+        s.apply(x, y, c["dt"], prec)
+    torch.cuda.synchronize()
+    out = {"profile_apply": args.profile_apply, "prec": args.prec, "triangles": s.K, "N": s.N,
+           "checksum": float(y.double().abs().sum().item())}
+    s.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -357,10 +381,19 @@ def main():
     ap.add_argument("--impl", default="festung", choices=["festung", "reference"])
     ap.add_argument("--skip-big", action="store_true", help="skip the 2M-triangle apply measurement")
     ap.add_argument("--skip-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--profile-apply", default=None, metavar="WORKLOAD",
+                    help="only run the operator apply on WORKLOAD (for ncu captures); prints one line")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    line = run_reference(args) if args.impl == "reference" else run_festung(args)
+    if args.profile_apply:
+        line = profile_apply(args)
+    elif args.impl == "reference":
+        line = run_reference(args)
+    else:
+        line = run_festung(args)
     if line is not None:
         print(json.dumps(line))
 
