@@ -146,6 +146,22 @@ int festung_get_state(const festung_ctx *ctx, double *C, int loc);
  * context's stream and returns without synchronising. */
 int festung_apply(festung_ctx *ctx, const void *x, void *y, int prec, double dt);
 
+/* Same result as festung_apply(), for callers that cannot allocate device memory:
+ * code running under an external memory manager that owns the device's memory (a
+ * framework pool or a fixed budget, where an extra cudaMalloc fails or escapes the
+ * accounting) and latency-critical loops where cudaMalloc/cudaFree would synchronise
+ * the device.  The paper has no counterpart; it is a deployment variant of the apply.
+ * The flux unknowns go to a fixed 32 MiB array inside the library instead of
+ * context scratch, so the call allocates and frees nothing.  Limit: 2 x N x K values
+ * of the chosen precision must fit in 32 MiB (N*K <= 2,097,152 for FP64, 4,194,304
+ * for FP32); larger meshes get FESTUNG_EINVAL.  The array exists once per device
+ * for the life of the process and is shared by all contexts and calls: calls whose
+ * kernels overlap on the GPU (other streams or threads) race on it and must be
+ * ordered by the caller.  The first call on a device looks up the array's device
+ * address; make that first call before any stream capture.  Arguments, layout and
+ * errors as festung_apply(). */
+int festung_apply_noalloc(festung_ctx *ctx, const void *x, void *y, int prec, double dt);
+
 /* One implicit-Euler step of size dt (Sec. 2.5): forms b of (E2) from the current
  * C, D, f and boundary data, solves (E1) from the initial guess C^n and, only on
  * success, replaces C by C^{n+1}.  opts may be NULL (tol 1e-10, max_iter 20000,

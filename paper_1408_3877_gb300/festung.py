@@ -21,7 +21,7 @@ BDR_INTERIOR, BDR_DIRICHLET, BDR_NEUMANN = 0, 1, 2
 EXPORTS = [
     "festung_mesh_create", "festung_setup", "festung_sizes", "festung_quad_points",
     "festung_set_coeff", "festung_set_source", "festung_set_bc", "festung_set_state",
-    "festung_get_state", "festung_apply", "festung_step", "festung_l2_error",
+    "festung_get_state", "festung_apply", "festung_apply_noalloc", "festung_step", "festung_l2_error",
     "festung_launch_count", "festung_set_stream", "festung_last_error", "festung_destroy",
 ]
 
@@ -66,6 +66,7 @@ def load(path=None):
     lib.festung_set_state.argtypes = [vp, vp, cint, cint]
     lib.festung_get_state.argtypes = [vp, vp, cint]
     lib.festung_apply.argtypes = [vp, vp, vp, cint, dbl]
+    lib.festung_apply_noalloc.argtypes = [vp, vp, vp, cint, dbl]
     lib.festung_step.argtypes = [vp, dbl, ctypes.POINTER(StepOpts), ctypes.POINTER(StepInfo)]
     lib.festung_l2_error.argtypes = [vp, vp, ctypes.POINTER(dbl)]
     lib.festung_set_stream.argtypes = [vp, vp]
