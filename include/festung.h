@@ -29,9 +29,11 @@
  *  - "Samples" are values of a function at the physical quadrature points that
  *    festung_quad_points() returns, in the same order.
  *  - Coefficient arrays of the public state are K x N row-major (element-major,
- *    the paper's global ordering (k-1)N + i).  Vectors handed to festung_apply()
- *    use the library's device layout N x K (row j holds coefficient j of all
- *    elements), which is the K x N array stored column-major.
+ *    the paper's global ordering (k-1)N + i) in the caller's triangle order.
+ *  - Internally triangles are renumbered along a Morton curve of their centroids, so
+ *    that neighbours sit close in memory.  Vectors handed to festung_apply() use the
+ *    library's device layout: N x K (row j holds coefficient j of all triangles) with
+ *    the triangles in this internal order; festung_element_order() returns it.
  *  - All calls on one context must come from one host thread at a time.
  */
 #ifndef FESTUNG_H
@@ -173,6 +175,10 @@ int festung_step(festung_ctx *ctx, double dt, const festung_step_opts *opts,
 /* Discretisation error ||c_h - c||_{L2} (Sec. 3.5) from samples of the exact c at
  * the triangle points (K x R2, host). */
 int festung_l2_error(const festung_ctx *ctx, const double *c_samples, double *err);
+
+/* The internal triangle order of the device layout: order[i] is the caller's index of
+ * the triangle stored at position i (order holds K entries, host memory). */
+int festung_element_order(const festung_ctx *ctx, int64_t *order);
 
 /* Number of CUDA kernels this context has launched so far (kernels inside a replayed
  * CUDA graph count one each per replay, including those that exit early because the

@@ -2,22 +2,29 @@
 #include <algorithm>
 
 #include "dispatch.h"
-#include "ldg_kernels.cuh"
+#include "ldg_fused.cuh"
 #include "ops.h"
 
 namespace festung {
 
 template <>
 void launch_apply<float>(const festung_ctx *c, const float *x, float *y, float *Z1, float *Z2, float tau,
-                         const int *skip, cudaStream_t st) {
-    const int grid = elem_grid(c);
-    c->launches += 2;
+                          const int *skip, cudaStream_t st) {
+    (void)Z1;
+    (void)Z2;
+    const int tiles = (int)((c->K + c->TE - 1) / c->TE);
+    c->launches += 1;
     dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
         constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
-        k_flux<float, N, R2, R1><<<grid, 256, 0, st>>>(x, Z1, Z2, c->fB, c->dNbr, c->K, c->fTab, skip);
-        k_apply<float, N, R2, R1, MODE_APPLY><<<grid, 256, 0, st>>>(x, Z1, Z2, c->fD, y, c->fB, c->dNbr, c->K, tau,
-                                                                    (float)c->eta, c->fTab, nullptr, nullptr,
-                                                                    nullptr, skip);
+        const size_t smem = (size_t)4 * 3 * R1 * c->nslot * sizeof(float);
+        static size_t configured = 0;
+        if (smem > configured) {
+            cudaFuncSetAttribute(k_apply_fused<float, N, R2, R1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            configured = smem;
+        }
+        k_apply_fused<float, N, R2, R1><<<tiles, 256, smem, st>>>(x, y, c->fD, c->fB, c->dNbr, c->dSlot, c->dHaloPtr,
+                                                                c->dHalo, c->K, c->TE, c->nslot, tau, (float)c->eta,
+                                                                c->fTab, skip);
     });
 }
 
@@ -41,6 +48,50 @@ void launch_precond<float>(const festung_ctx *c, const float *P, const float *x,
         constexpr int N = decltype(n_)::value;
         k_precond<float, N><<<part ? nblk : elem_grid(c), 256, 0, st>>>(P, x, y, c->K, part, skip);
     });
+}
+
+template <>
+void launch_apply_twopass<float>(const festung_ctx *c, const float *x, float *y, float *Z1, float *Z2, float tau,
+                                  const int *skip, cudaStream_t st) {
+    const int grid = elem_grid(c);
+    c->launches += 2;
+    dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
+        constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
+        k_flux<float, N, R2, R1><<<grid, 256, 0, st>>>(x, Z1, Z2, c->fB, c->dNbr, c->K, c->fTab, skip);
+        k_apply<float, N, R2, R1, MODE_APPLY><<<grid, 256, 0, st>>>(x, Z1, Z2, c->fD, y, c->fB, c->dNbr, c->K, tau,
+                                                                  (float)c->eta, c->fTab, nullptr, nullptr, nullptr,
+                                                                  nullptr, skip);
+    });
+}
+
+// Copy the reference tables of the context's (N, R2, R1) into the constant bank.  The
+// tables depend only on p and the quadrature, so every context of the same shape
+// writes identical values; the copy is done once per process and shape.
+cudaError_t upload_tables_f32(const festung_ctx *c) {
+    cudaError_t err = cudaSuccess;
+    dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
+        constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
+        static bool done = false;
+        if (done) return;
+        CTab<float, N, R2, R1> h;
+        const HostTables &t = c->tab;
+        for (int i = 0; i < R2 * N; ++i) {
+            h.phiQ[i] = (float)t.phiQ[i];
+            h.gw1[i] = (float)t.gw1[i];
+            h.gw2[i] = (float)t.gw2[i];
+        }
+        for (int i = 0; i < N * N; ++i) {
+            h.H1[i] = (float)t.H1[i];
+            h.H2[i] = (float)t.H2[i];
+        }
+        for (int i = 0; i < 3 * R1 * N; ++i) {
+            h.phiE[i] = (float)t.phiE[i];
+            h.wphiE[i] = (float)t.wphiE[i];
+        }
+        err = cudaMemcpyToSymbol(c_tab<float, N, R2, R1>, &h, sizeof(h));
+        if (err == cudaSuccess) done = true;
+    });
+    return err;
 }
 
 }  // namespace festung

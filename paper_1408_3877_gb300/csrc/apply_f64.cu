@@ -1,6 +1,6 @@
 // FP64 instantiations of the operator kernels and the right-hand side.
 #include "dispatch.h"
-#include "ldg_kernels.cuh"
+#include "ldg_fused.cuh"
 #include "ops.h"
 
 namespace festung {
@@ -8,14 +8,21 @@ namespace festung {
 template <>
 void launch_apply<double>(const festung_ctx *c, const double *x, double *y, double *Z1, double *Z2, double tau,
                           const int *skip, cudaStream_t st) {
-    const int grid = elem_grid(c);
-    c->launches += 2;
+    (void)Z1;
+    (void)Z2;
+    const int tiles = (int)((c->K + c->TE - 1) / c->TE);
+    c->launches += 1;
     dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
         constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
-        k_flux<double, N, R2, R1><<<grid, 256, 0, st>>>(x, Z1, Z2, c->dB, c->dNbr, c->K, c->dTab, skip);
-        k_apply<double, N, R2, R1, MODE_APPLY><<<grid, 256, 0, st>>>(x, Z1, Z2, c->dD, y, c->dB, c->dNbr, c->K, tau,
-                                                                     c->eta, c->dTab, nullptr, nullptr, nullptr,
-                                                                     skip);
+        const size_t smem = (size_t)4 * 3 * R1 * c->nslot * sizeof(double);
+        static size_t configured = 0;
+        if (smem > configured) {
+            cudaFuncSetAttribute(k_apply_fused<double, N, R2, R1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            configured = smem;
+        }
+        k_apply_fused<double, N, R2, R1><<<tiles, 256, smem, st>>>(x, y, c->dD, c->dB, c->dNbr, c->dSlot, c->dHaloPtr,
+                                                                c->dHalo, c->K, c->TE, c->nslot, tau, (double)c->eta,
+                                                                c->dTab, skip);
     });
 }
 
@@ -24,10 +31,11 @@ void launch_rhs(const festung_ctx *c, double *W1, double *W2, double *b, double 
     c->launches += 2;
     dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
         constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
-        k_dirichlet_lift<double, N, R2, R1><<<grid, 256, 0, st>>>(W1, W2, c->dB, c->dNbr, c->K, c->dTab, c->dCD);
+        k_dirichlet_lift<double, N, R2, R1><<<grid, 256, 0, st>>>(W1, W2, c->dB, c->dNbr, c->K, c->dTab, c->dCD,
+                                                                  c->dPerm);
         k_apply<double, N, R2, R1, MODE_RHS><<<grid, 256, 0, st>>>(c->dC, W1, W2, c->dD, b, c->dB, c->dNbr, c->K,
                                                                    tau, c->eta, c->dTab, c->dF, c->dCD, c->dGN,
-                                                                   nullptr);
+                                                                   c->dPerm, nullptr);
     });
 }
 
@@ -39,6 +47,50 @@ void launch_precond<double>(const festung_ctx *c, const float *P, const double *
         constexpr int N = decltype(n_)::value;
         k_precond<double, N><<<part ? nblk : elem_grid(c), 256, 0, st>>>(P, x, y, c->K, part, skip);
     });
+}
+
+template <>
+void launch_apply_twopass<double>(const festung_ctx *c, const double *x, double *y, double *Z1, double *Z2, double tau,
+                                  const int *skip, cudaStream_t st) {
+    const int grid = elem_grid(c);
+    c->launches += 2;
+    dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
+        constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
+        k_flux<double, N, R2, R1><<<grid, 256, 0, st>>>(x, Z1, Z2, c->dB, c->dNbr, c->K, c->dTab, skip);
+        k_apply<double, N, R2, R1, MODE_APPLY><<<grid, 256, 0, st>>>(x, Z1, Z2, c->dD, y, c->dB, c->dNbr, c->K, tau,
+                                                                  (double)c->eta, c->dTab, nullptr, nullptr, nullptr,
+                                                                  nullptr, skip);
+    });
+}
+
+// Copy the reference tables of the context's (N, R2, R1) into the constant bank.  The
+// tables depend only on p and the quadrature, so every context of the same shape
+// writes identical values; the copy is done once per process and shape.
+cudaError_t upload_tables_f64(const festung_ctx *c) {
+    cudaError_t err = cudaSuccess;
+    dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
+        constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
+        static bool done = false;
+        if (done) return;
+        CTab<double, N, R2, R1> h;
+        const HostTables &t = c->tab;
+        for (int i = 0; i < R2 * N; ++i) {
+            h.phiQ[i] = (double)t.phiQ[i];
+            h.gw1[i] = (double)t.gw1[i];
+            h.gw2[i] = (double)t.gw2[i];
+        }
+        for (int i = 0; i < N * N; ++i) {
+            h.H1[i] = (double)t.H1[i];
+            h.H2[i] = (double)t.H2[i];
+        }
+        for (int i = 0; i < 3 * R1 * N; ++i) {
+            h.phiE[i] = (double)t.phiE[i];
+            h.wphiE[i] = (double)t.wphiE[i];
+        }
+        err = cudaMemcpyToSymbol(c_tab<double, N, R2, R1>, &h, sizeof(h));
+        if (err == cudaSuccess) done = true;
+    });
+    return err;
 }
 
 }  // namespace festung

@@ -97,7 +97,7 @@ template <> Vecs<float> &vecs<float>(festung_ctx *c) { return c->ws->f; }
 // ---------------------------------------------------------------------------
 __global__ void k_project(const double *__restrict__ samp, double *__restrict__ out, float *__restrict__ out32,
                           const double *__restrict__ wphiQ, int64_t K, int N, int R2, int check_positive,
-                          int *__restrict__ flags) {
+                          const int32_t *__restrict__ perm, int *__restrict__ flags) {
     extern __shared__ double sw[];
     for (int i = threadIdx.x; i < R2 * N; i += blockDim.x) sw[i] = wphiQ[i];
     __syncthreads();
@@ -105,9 +105,10 @@ __global__ void k_project(const double *__restrict__ samp, double *__restrict__ 
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x) {
         double acc[NMAX];
         for (int j = 0; j < N; ++j) acc[j] = 0.0;
-        const double first = samp[k * R2];
+        const int64_t u = perm[k];  // samples arrive in the caller's triangle order
+        const double first = samp[u * R2];
         for (int r = 0; r < R2; ++r) {
-            const double v = samp[k * R2 + r];
+            const double v = samp[u * R2 + r];
             if (!isfinite(v)) fl |= 1;
             if (check_positive && !(v > 0.0)) fl |= 2;
             if (v != first) fl |= 4;
@@ -128,19 +129,21 @@ __global__ void k_check_finite(const double *__restrict__ a, int64_t n, int *__r
     if (fl) atomicOr(flags, 1);
 }
 
-// K x N (row-major) <-> N x K
-__global__ void k_to_internal(const double *__restrict__ a, double *__restrict__ b, int64_t K, int N) {
+// public K x N (caller's triangle order, row-major) <-> internal N x K (internal order)
+__global__ void k_to_internal(const double *__restrict__ a, double *__restrict__ b, int64_t K, int N,
+                              const int32_t *__restrict__ perm) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < K * N; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = i / N;
-        const int j = (int)(i - k * N);
-        b[j * K + k] = a[i];
+        const int64_t j = i / K;
+        const int64_t k = i - j * K;
+        b[i] = a[(int64_t)perm[k] * N + j];
     }
 }
-__global__ void k_to_public(const double *__restrict__ b, double *__restrict__ a, int64_t K, int N) {
+__global__ void k_to_public(const double *__restrict__ b, double *__restrict__ a, int64_t K, int N,
+                            const int32_t *__restrict__ perm) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < K * N; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = i / N;
-        const int j = (int)(i - k * N);
-        a[i] = b[j * K + k];
+        const int64_t j = i / K;
+        const int64_t k = i - j * K;
+        a[(int64_t)perm[k] * N + j] = b[i];
     }
 }
 
@@ -591,7 +594,7 @@ int project_samples(festung_ctx *c, const double *samples, int loc, double *out,
     FCK(cudaMemsetAsync(c->ws->d_flags, 0, sizeof(int), c->stream));
     const TableOffsets o = table_offsets(c->N, c->R2, c->R1);
     k_project<<<elem_grid(c), 256, sizeof(double) * c->R2 * c->N, c->stream>>>(
-        src, out, out32, c->dTab + o.wphiQ, c->K, c->N, c->R2, check_pos, c->ws->d_flags); ++c->launches;
+        src, out, out32, c->dTab + o.wphiQ, c->K, c->N, c->R2, check_pos, c->dPerm, c->ws->d_flags); ++c->launches;
     FCK(cudaGetLastError());
     FCK(cudaMemcpyAsync(c->ws->h_flags, c->ws->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     FCK(cudaStreamSynchronize(c->stream));
@@ -785,13 +788,16 @@ int festung_mesh_create(const double *coordV, int64_t numV, const int32_t *V0T, 
         if (bdr_type[i] == FESTUNG_BDR_DIRICHLET) c->has_dirichlet = true;
         if (bdr_type[i] == FESTUNG_BDR_NEUMANN) c->has_neumann = true;
     }
+    // internal order: Morton order of centroids, in tiles of 256 triangles
+    MeshOrder mo;
+    order_and_tile(coordV, V0T, numT, c->hB, nbr, 256, mo);
+    c->perm = mo.perm;
+    c->TE = mo.TE;
+    c->max_halo = mo.max_halo;
+    c->nslot = mo.TE + mo.max_halo;
     auto fail = [&](cudaError_t e) {
         g_create_err = std::string("CUDA: ") + cudaGetErrorString(e);
-        free_ctx_device(c);
-        if (c->dB) cudaFree(c->dB);
-        if (c->fB) cudaFree(c->fB);
-        if (c->dNbr) cudaFree(c->dNbr);
-        delete c;
+        festung_destroy(c);
         return e == cudaErrorMemoryAllocation ? FESTUNG_ENOMEM : FESTUNG_ECUDA;
     };
     int dev = 0;
@@ -803,13 +809,27 @@ int festung_mesh_create(const double *coordV, int64_t numV, const int32_t *V0T, 
     if ((e = cudaMalloc(&c->dB, 4 * K * sizeof(double))) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&c->fB, 4 * K * sizeof(float))) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&c->dNbr, 3 * K * sizeof(int32_t))) != cudaSuccess) return fail(e);
-    std::vector<float> fB(c->hB.begin(), c->hB.end());
-    if ((e = cudaMemcpy(c->dB, c->hB.data(), 4 * K * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+    std::vector<float> fB(mo.B.begin(), mo.B.end());
+    std::vector<int16_t> slot16(mo.slot.begin(), mo.slot.end());
+    const int64_t T = (K + mo.TE - 1) / mo.TE;
+    if ((e = cudaMalloc(&c->dPerm, K * sizeof(int32_t))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&c->dSlot, 3 * K * sizeof(int16_t))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&c->dHaloPtr, (T + 1) * sizeof(int32_t))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&c->dHalo, std::max<size_t>(1, mo.halo.size()) * sizeof(int32_t))) != cudaSuccess)
         return fail(e);
-    if ((e = cudaMemcpy(c->fB, fB.data(), 4 * K * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
-        return fail(e);
-    if ((e = cudaMemcpy(c->dNbr, nbr.data(), 3 * K * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess)
-        return fail(e);
+    const struct {
+        void *dst;
+        const void *src;
+        size_t bytes;
+    } up[] = {{c->dB, mo.B.data(), 4 * K * sizeof(double)},
+              {c->fB, fB.data(), 4 * K * sizeof(float)},
+              {c->dNbr, mo.nbr.data(), 3 * K * sizeof(int32_t)},
+              {c->dPerm, mo.perm.data(), K * sizeof(int32_t)},
+              {c->dSlot, slot16.data(), 3 * K * sizeof(int16_t)},
+              {c->dHaloPtr, mo.halo_ptr.data(), (T + 1) * sizeof(int32_t)},
+              {c->dHalo, mo.halo.data(), mo.halo.size() * sizeof(int32_t)}};
+    for (const auto &u : up)
+        if (u.bytes && (e = cudaMemcpy(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
     *out = c;
     return FESTUNG_OK;
 }
@@ -860,6 +880,8 @@ int festung_setup(festung_ctx *c, int p, int quad_order, double eta) {
     FCK(cudaMalloc(&c->fTab, o.total * sizeof(float)));
     FCK(cudaMemcpy(c->dTab, h.data(), o.total * sizeof(double), cudaMemcpyHostToDevice));
     FCK(cudaMemcpy(c->fTab, hf.data(), o.total * sizeof(float), cudaMemcpyHostToDevice));
+    FCK(upload_tables_f64(c));
+    FCK(upload_tables_f32(c));
     FCK(cudaMalloc(&c->dC, K * N * sizeof(double)));
     FCK(cudaMalloc(&c->dD, K * N * sizeof(double)));
     FCK(cudaMalloc(&c->fD, K * N * sizeof(float)));
@@ -1013,7 +1035,7 @@ int festung_set_state(festung_ctx *c, const double *C, int is_samples, int loc) 
         double *tmp = w.scratch64 + KN;
         rc = upload_checked(c, C, loc, tmp, KN);
         if (rc) return rc;
-        k_to_internal<<<small_grid(KN, c), 256, 0, c->stream>>>(tmp, c->dC, c->K, c->N); ++c->launches;
+        k_to_internal<<<small_grid(KN, c), 256, 0, c->stream>>>(tmp, c->dC, c->K, c->N, c->dPerm); ++c->launches;
         FCK(cudaGetLastError());
     }
     FCK(cudaStreamSynchronize(c->stream));
@@ -1033,7 +1055,7 @@ int festung_get_state(const festung_ctx *cc, double *C, int loc) {
     const int64_t KN = c->K * c->N;
     if (!w.scratch64) FCK(cudaMalloc(&w.scratch64, 2 * KN * sizeof(double)));
     double *dst = (loc == FESTUNG_DEVICE) ? C : w.scratch64;
-    k_to_public<<<small_grid(KN, c), 256, 0, c->stream>>>(c->dC, dst, c->K, c->N); ++c->launches;
+    k_to_public<<<small_grid(KN, c), 256, 0, c->stream>>>(c->dC, dst, c->K, c->N, c->dPerm); ++c->launches;
     FCK(cudaGetLastError());
     if (loc == FESTUNG_HOST)
         FCK(cudaMemcpyAsync(C, w.scratch64, KN * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -1214,6 +1236,12 @@ int festung_l2_error(const festung_ctx *cc, const double *c_samples, double *err
     return FESTUNG_OK;
 }
 
+int festung_element_order(const festung_ctx *c, int64_t *order) {
+    if (!c || !order) return FESTUNG_EINVAL;
+    for (int64_t k = 0; k < c->K; ++k) order[k] = c->perm[k];
+    return FESTUNG_OK;
+}
+
 int festung_launch_count(const festung_ctx *c, int64_t *count) {
     if (!c || !count) return FESTUNG_EINVAL;
     *count = c->launches;
@@ -1235,9 +1263,9 @@ void festung_destroy(festung_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_ctx_device(c);
-    if (c->dB) cudaFree(c->dB);
-    if (c->fB) cudaFree(c->fB);
-    if (c->dNbr) cudaFree(c->dNbr);
+    void *mesh_ptrs[] = {c->dB, c->fB, c->dNbr, c->dPerm, c->dSlot, c->dHaloPtr, c->dHalo};
+    for (void *q : mesh_ptrs)
+        if (q) cudaFree(q);
     delete c;
 }
 

@@ -51,6 +51,21 @@ int build_mesh(const double *coordV, int64_t numV, const int32_t *V0T, int64_t n
                const int8_t *bdr, std::vector<double> &B /*4 x K*/, std::vector<int32_t> &nbr /*3 x K*/,
                std::string &err);
 
+// Internal element order and tiling (see order_and_tile in mesh.cpp).
+struct MeshOrder {
+    std::vector<int32_t> perm;      // internal index -> caller's triangle index
+    std::vector<int32_t> inv;       // caller's index -> internal index
+    std::vector<double> B;          // 4 x K geometry, internal order
+    std::vector<int32_t> nbr;       // 3 x K neighbour codes with internal indices
+    int TE = 0;                     // triangles per tile
+    int max_halo = 0;               // largest halo of any tile
+    std::vector<int32_t> halo_ptr;  // tile t's halo is halo[halo_ptr[t] .. halo_ptr[t+1])
+    std::vector<int32_t> halo;      // internal indices
+    std::vector<int32_t> slot;      // 3 x K: shared-memory slot of the neighbour across edge n (-1: boundary)
+};
+void order_and_tile(const double *coordV, const int32_t *V0T, int64_t K, const std::vector<double> &B_usr,
+                    const std::vector<int32_t> &nbr_usr, int TE, MeshOrder &o);
+
 // Device-side view passed to kernels.
 template <typename T>
 struct DevMesh {
@@ -74,7 +89,12 @@ struct festung_ctx {
     std::vector<double> coordV;
     std::vector<int32_t> V0T;
     std::vector<int8_t> bdr;
-    std::vector<double> hB;  // 4 x K
+    std::vector<double> hB;  // 4 x K geometry in the caller's triangle order
+    std::vector<int32_t> perm;  // internal index -> caller's triangle index
+    int32_t *dPerm = nullptr;   // device copy of perm
+    int TE = 0, max_halo = 0, nslot = 0;
+    int32_t *dHaloPtr = nullptr, *dHalo = nullptr;
+    int16_t *dSlot = nullptr;   // 3 x K
     bool has_dirichlet = false, has_neumann = false;
     // device mesh
     double *dB = nullptr;

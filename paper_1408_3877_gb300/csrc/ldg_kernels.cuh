@@ -5,6 +5,9 @@
 // transaction.  Geometry is 4 x K (B11, B12, B21, B22) and the neighbour relation
 // 3 x K codes: (k+ << 2) | n+ for an interior edge, -1 Dirichlet, -2 Neumann.
 //
+// Boundary samples (c_D, g_N) arrive in the caller's triangle order; perm maps the
+// internal index to it.
+//
 // Reference tables (basis values and weighted gradients at the quadrature points)
 // are staged once per block in shared memory; every table read is warp-uniform
 // except the neighbour's edge trace, whose local edge n+ varies per thread.
@@ -183,7 +186,7 @@ __global__ void __launch_bounds__(256) k_apply(const T *__restrict__ X, const T 
                                                const int32_t *__restrict__ nbr, int64_t K, T tau, T eta,
                                                const T *__restrict__ tabg, const T *__restrict__ F,
                                                const T *__restrict__ cD, const T *__restrict__ gN,
-                                               const int *__restrict__ skip) {
+                                               const int32_t *__restrict__ perm, const int *__restrict__ skip) {
     __shared__ SmemTab<T, N, R2, R1> s;
     if (skip && *skip) return;
     load_tables(s, tabg);
@@ -229,7 +232,7 @@ __global__ void __launch_bounds__(256) k_apply(const T *__restrict__ X, const T 
                 // -K_N: -|E| sum_r w_r phi_i d^- g_N
                 const T len = sqrt(nx * nx + ny * ny);
 #pragma unroll
-                for (int r = 0; r < R1; ++r) g[r] = -len * dm[r] * gN[(k * 3 + n) * R1 + r];
+                for (int r = 0; r < R1; ++r) g[r] = -len * dm[r] * gN[((int64_t)perm[k] * 3 + n) * R1 + r];
             } else {
                 T zm1[R1], zm2[R1];
                 trace_own<T, N, R1>(s.phiE, n, z1, zm1);
@@ -262,7 +265,7 @@ __global__ void __launch_bounds__(256) k_apply(const T *__restrict__ X, const T 
                         for (int r = 0; r < R1; ++r) g[r] += eta * cm[r];
                     } else {
 #pragma unroll
-                        for (int r = 0; r < R1; ++r) g[r] += eta * cD[(k * 3 + n) * R1 + r];
+                        for (int r = 0; r < R1; ++r) g[r] += eta * cD[((int64_t)perm[k] * 3 + n) * R1 + r];
                     }
                 }
             }
@@ -289,7 +292,8 @@ template <typename T, int N, int R2, int R1>
 __global__ void __launch_bounds__(256) k_dirichlet_lift(T *__restrict__ W1, T *__restrict__ W2,
                                                         const T *__restrict__ Bg,
                                                         const int32_t *__restrict__ nbr, int64_t K,
-                                                        const T *__restrict__ tabg, const T *__restrict__ cD) {
+                                                        const T *__restrict__ tabg, const T *__restrict__ cD,
+                                                        const int32_t *__restrict__ perm) {
     __shared__ SmemTab<T, N, R2, R1> s;
     load_tables(s, tabg);
     __syncthreads();
@@ -308,7 +312,8 @@ __global__ void __launch_bounds__(256) k_dirichlet_lift(T *__restrict__ W1, T *_
             for (int i = 0; i < N; ++i) {
                 T t = T(0);
 #pragma unroll
-                for (int r = 0; r < R1; ++r) t += s.wphiE[(n * R1 + r) * N + i] * cD[(k * 3 + n) * R1 + r];
+                for (int r = 0; r < R1; ++r)
+                    t += s.wphiE[(n * R1 + r) * N + i] * cD[((int64_t)perm[k] * 3 + n) * R1 + r];
                 a1[i] += nx * t;
                 a2[i] += ny * t;
             }

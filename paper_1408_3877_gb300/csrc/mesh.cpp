@@ -106,3 +106,102 @@ int build_mesh(const double *coordV, int64_t numV, const int32_t *V0T, int64_t K
 }
 
 }  // namespace festung
+
+namespace festung {
+
+namespace {
+
+// spread the low 21 bits of v to the even bit positions (one axis of a 2-D Morton key)
+uint64_t spread2(uint64_t v) {
+    v &= 0x1fffffULL;
+    v = (v | (v << 16)) & 0x0000ffff0000ffffULL;
+    v = (v | (v << 8)) & 0x00ff00ff00ff00ffULL;
+    v = (v | (v << 4)) & 0x0f0f0f0f0f0f0f0fULL;
+    v = (v | (v << 2)) & 0x3333333333333333ULL;
+    v = (v | (v << 1)) & 0x5555555555555555ULL;
+    return v;
+}
+
+}  // namespace
+
+void order_and_tile(const double *coordV, const int32_t *V0T, int64_t K, const std::vector<double> &B_usr,
+                    const std::vector<int32_t> &nbr_usr, int TE, MeshOrder &o) {
+    // Morton order of the triangle centroids: nearby triangles get nearby indices, so a
+    // tile of TE consecutive triangles is a compact patch with a short boundary.
+    std::vector<double> cx(K), cy(K);
+    double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+    for (int64_t k = 0; k < K; ++k) {
+        double sx = 0, sy = 0;
+        for (int v = 0; v < 3; ++v) {
+            sx += coordV[2 * int64_t(V0T[3 * k + v])];
+            sy += coordV[2 * int64_t(V0T[3 * k + v]) + 1];
+        }
+        cx[k] = sx / 3.0;
+        cy[k] = sy / 3.0;
+        x0 = std::min(x0, cx[k]);
+        x1 = std::max(x1, cx[k]);
+        y0 = std::min(y0, cy[k]);
+        y1 = std::max(y1, cy[k]);
+    }
+    const double span = std::max(std::max(x1 - x0, y1 - y0), 1e-300);
+    const double scale = double((1 << 21) - 1) / span;
+    std::vector<uint64_t> key(K);
+    for (int64_t k = 0; k < K; ++k) {
+        const uint64_t qx = (uint64_t)((cx[k] - x0) * scale), qy = (uint64_t)((cy[k] - y0) * scale);
+        key[k] = spread2(qx) | (spread2(qy) << 1);
+    }
+    o.perm.resize(K);
+    for (int64_t k = 0; k < K; ++k) o.perm[k] = (int32_t)k;
+    std::stable_sort(o.perm.begin(), o.perm.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+    o.inv.assign(K, 0);
+    for (int64_t i = 0; i < K; ++i) o.inv[o.perm[i]] = (int32_t)i;
+    // geometry and neighbour codes in internal order
+    o.B.assign(4 * K, 0.0);
+    o.nbr.assign(3 * K, 0);
+    for (int64_t i = 0; i < K; ++i) {
+        const int64_t u = o.perm[i];
+        for (int c = 0; c < 4; ++c) o.B[c * K + i] = B_usr[c * K + u];
+        for (int n = 0; n < 3; ++n) {
+            const int32_t code = nbr_usr[n * K + u];
+            o.nbr[n * K + i] = code >= 0 ? (int32_t)((int64_t(o.inv[code >> 2]) << 2) | (code & 3)) : code;
+        }
+    }
+    // tiles of TE consecutive triangles; halo = interior neighbours outside the tile
+    o.TE = TE;
+    const int64_t T = (K + TE - 1) / TE;
+    o.halo_ptr.assign(T + 1, 0);
+    o.halo.clear();
+    o.slot.assign(3 * K, -1);
+    o.max_halo = 0;
+    std::vector<int32_t> h;
+    for (int64_t t = 0; t < T; ++t) {
+        const int64_t s0 = t * TE, s1 = std::min(K, s0 + TE);
+        h.clear();
+        for (int64_t i = s0; i < s1; ++i)
+            for (int n = 0; n < 3; ++n) {
+                const int32_t code = o.nbr[n * K + i];
+                if (code < 0) continue;
+                const int64_t k2 = code >> 2;
+                if (k2 < s0 || k2 >= s1) h.push_back((int32_t)k2);
+            }
+        std::sort(h.begin(), h.end());
+        h.erase(std::unique(h.begin(), h.end()), h.end());
+        for (int64_t i = s0; i < s1; ++i)
+            for (int n = 0; n < 3; ++n) {
+                const int32_t code = o.nbr[n * K + i];
+                if (code < 0) continue;
+                const int64_t k2 = code >> 2;
+                if (k2 >= s0 && k2 < s1) {
+                    o.slot[n * K + i] = (int32_t)(k2 - s0);
+                } else {
+                    const int64_t pos = std::lower_bound(h.begin(), h.end(), (int32_t)k2) - h.begin();
+                    o.slot[n * K + i] = (int32_t)(TE + pos);
+                }
+            }
+        o.halo.insert(o.halo.end(), h.begin(), h.end());
+        o.halo_ptr[t + 1] = (int32_t)o.halo.size();
+        o.max_halo = std::max<int>(o.max_halo, (int)h.size());
+    }
+}
+
+}  // namespace festung

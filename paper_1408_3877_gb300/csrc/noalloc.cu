@@ -1,9 +1,9 @@
 // Operator apply for callers that cannot allocate device memory.
 //
-// festung_apply() keeps the eliminated flux unknowns Z^1, Z^2 (2 x N x K values) in
-// context scratch that it allocates on first use.  This variant instead keeps them in
+// This variant evaluates y = S x with the two-pass kernels, whose eliminated flux
+// unknowns Z^1, Z^2 (2 x N x K values) travel through global scratch.  The scratch is
 // one fixed array that is part of the library image, so the call itself never
-// allocates or frees.
+// allocates or frees (festung_apply allocates its context workspace on first use).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -68,11 +68,11 @@ extern "C" int festung_apply_noalloc(festung_ctx *c, const void *x, void *y, int
     // them, so nothing has to be cleared between calls.
     if (prec == FESTUNG_FP64) {
         double *Z1 = static_cast<double *>(base);
-        festung::launch_apply<double>(c, static_cast<const double *>(x), static_cast<double *>(y), Z1,
+        festung::launch_apply_twopass<double>(c, static_cast<const double *>(x), static_cast<double *>(y), Z1,
                                       Z1 + c->N * c->K, dt, nullptr, c->stream);
     } else {
         float *Z1 = static_cast<float *>(base);
-        festung::launch_apply<float>(c, static_cast<const float *>(x), static_cast<float *>(y), Z1, Z1 + c->N * c->K,
+        festung::launch_apply_twopass<float>(c, static_cast<const float *>(x), static_cast<float *>(y), Z1, Z1 + c->N * c->K,
                                      (float)dt, nullptr, c->stream);
     }
     e = cudaGetLastError();

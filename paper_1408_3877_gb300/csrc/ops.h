@@ -7,18 +7,29 @@
 
 namespace festung {
 
-// y = S x of the step operator (E1) with time step tau; Z1, Z2: N x K scratch for the
-// eliminated flux unknowns.  skip: optional device flag; when it is non-zero at
+// y = S x of the step operator (E1) with time step tau, one fused pass per tile (the
+// flux unknowns stay in shared memory; Z1, Z2 are not used).  skip: optional device flag; when it is non-zero at
 // launch the kernels return immediately (early exit inside captured graphs).
 template <typename T>
 void launch_apply(const festung_ctx *c, const T *x, T *y, T *Z1, T *Z2, T tau, const int *skip,
                   cudaStream_t st);
+
+// The same y = S x in two passes: k_flux writes Z^1, Z^2 to the N x K scratch arrays
+// Z1, Z2 in global memory, k_apply reads them back.
+template <typename T>
+void launch_apply_twopass(const festung_ctx *c, const T *x, T *y, T *Z1, T *Z2, T tau, const int *skip,
+                          cudaStream_t st);
 
 // b of (E2) in FP64 from C^n, F, the boundary data and D; W1, W2: N x K scratch
 // (the Dirichlet lift M^{-1} J_D^m).
 void launch_rhs(const festung_ctx *c, double *W1, double *W2, double *b, double tau, cudaStream_t st);
 
 int elem_grid(const festung_ctx *c);
+
+// Reference tables of the context's (p, quadrature) into the constant bank of the
+// fused apply kernels (FP64 and FP32 copies).
+cudaError_t upload_tables_f64(const festung_ctx *c);
+cudaError_t upload_tables_f32(const festung_ctx *c);
 
 // Block-Jacobi preconditioner: P <- inverse of the N x N diagonal blocks of S (E1),
 // built in FP32 from the FP32 copies of geometry, tables and D; layout [(i N + j) K + k].

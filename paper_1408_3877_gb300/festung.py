@@ -22,7 +22,7 @@ EXPORTS = [
     "festung_mesh_create", "festung_setup", "festung_sizes", "festung_quad_points",
     "festung_set_coeff", "festung_set_source", "festung_set_bc", "festung_set_state",
     "festung_get_state", "festung_apply", "festung_apply_noalloc", "festung_step", "festung_l2_error",
-    "festung_launch_count", "festung_set_stream", "festung_last_error", "festung_destroy",
+    "festung_element_order", "festung_launch_count", "festung_set_stream", "festung_last_error", "festung_destroy",
 ]
 
 
@@ -71,6 +71,7 @@ def load(path=None):
     lib.festung_l2_error.argtypes = [vp, vp, ctypes.POINTER(dbl)]
     lib.festung_set_stream.argtypes = [vp, vp]
     lib.festung_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
+    lib.festung_element_order.argtypes = [vp, vp]
     lib.festung_last_error.argtypes = [vp]
     lib.festung_last_error.restype = ctypes.c_char_p
     lib.festung_destroy.argtypes = [vp]
@@ -175,7 +176,7 @@ class Solver:
         return out
 
     def apply(self, x, y, dt, prec=FP64):
-        """y = S x on device tensors of shape (N, K) (FP64 or FP32 by prec)."""
+        """y = S x on device tensors of shape (N, K) in the internal triangle order (FP64 or FP32 by prec)."""
         self._check(self.lib.festung_apply(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                                            prec, dt))
 
@@ -185,6 +186,12 @@ class Solver:
         self._check(self.lib.festung_step(self.h, dt, ctypes.byref(o), ctypes.byref(info)))
         return {"iterations": info.iterations, "outer": info.outer, "rel_residual": info.rel_residual,
                 "solver": info.solver, "symmetric": info.symmetric}
+
+    def element_order(self):
+        """order[i] = caller's index of the triangle at position i of the device layout."""
+        o = np.zeros(self.K, dtype=np.int64)
+        self._check(self.lib.festung_element_order(self.h, o.ctypes.data))
+        return o
 
     def launch_count(self):
         n = ctypes.c_int64()

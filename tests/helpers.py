@@ -36,13 +36,19 @@ def rounding_bound(S_abs, x, eps):
     return eps * np.linalg.norm(S_abs @ np.abs(x))
 
 
-def to_gpu_layout(x, K, N, dtype):
+def to_gpu_layout(x, K, N, dtype, order):
+    """Caller-order K x N coefficients -> device layout N x K in the library's internal order."""
     import torch
-    return torch.tensor(np.ascontiguousarray(np.asarray(x).reshape(K, N).T), dtype=dtype, device="cuda")
+    xi = np.asarray(x).reshape(K, N)[np.asarray(order)]
+    return torch.tensor(np.ascontiguousarray(xi.T), dtype=dtype, device="cuda")
 
 
-def from_gpu_layout(y):
-    return y.double().cpu().numpy().T.copy()
+def from_gpu_layout(y, order):
+    """Device layout N x K (internal order) -> caller-order K x N."""
+    yi = y.double().cpu().numpy().T
+    out = np.empty_like(yi)
+    out[np.asarray(order)] = yi
+    return out
 
 
 def patch_oracle_rows(cV, V0T, bdr, p, dfun, x, tau, ks, quad_order=None, eta=1.0):

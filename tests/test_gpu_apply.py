@@ -36,12 +36,13 @@ def _case(n, p, mix, tau, quad_order=None, seed=1, jitter=0.2):
     x = np.random.default_rng(seed + 7).standard_normal(L.K * L.N)
     y_or = S @ x
     out = {}
+    order = s.element_order()
     for prec, dt in ((F.FP64, torch.float64), (F.FP32, torch.float32)):
-        xg = to_gpu_layout(x, L.K, L.N, dt)
+        xg = to_gpu_layout(x, L.K, L.N, dt, order)
         yg = torch.empty_like(xg)
         s.apply(xg, yg, tau, prec)
         torch.cuda.synchronize()
-        out[prec] = from_gpu_layout(yg).ravel()
+        out[prec] = from_gpu_layout(yg, order).ravel()
     s.close()
     return S, x, y_or, out
 
@@ -85,11 +86,12 @@ def test_apply_dt_zero_is_mass_and_two_triangles():
         x = np.random.default_rng(p).standard_normal(2 * L.N)
         for tau in (0.0, 0.3):
             y = L.operator(L.project(smooth_d), tau) @ x
-            xg = to_gpu_layout(x, 2, L.N, torch.float64)
+            order = s.element_order()
+            xg = to_gpu_layout(x, 2, L.N, torch.float64, order)
             yg = torch.empty_like(xg)
             s.apply(xg, yg, tau, F.FP64)
             torch.cuda.synchronize()
-            assert np.allclose(from_gpu_layout(yg).ravel(), y, rtol=1e-12, atol=1e-12 * np.abs(y).max())
+            assert np.allclose(from_gpu_layout(yg, order).ravel(), y, rtol=1e-12, atol=1e-12 * np.abs(y).max())
         s.close()
 
 
@@ -132,16 +134,17 @@ def test_apply_full_size_sampled(cfg):
     x = rng.standard_normal((K, N))
     ks = rng.choice(K, 24, replace=False)
     rows, scale = patch_oracle_rows(cV, V0T, bdr, p, dfun, x, tau, ks)
+    order = s.element_order()
     for prec, dt, eps in ((F.FP64, torch.float64, EPS64), (F.FP32, torch.float32, EPS32)):
-        xg = to_gpu_layout(x, K, N, dt)
+        xg = to_gpu_layout(x, K, N, dt, order)
         yg = torch.empty_like(xg)
         s.apply(xg, yg, tau, prec)
         torch.cuda.synchronize()
-        y = from_gpu_layout(yg)
+        y = from_gpu_layout(yg, order)
         err = np.abs(y[ks] - rows)
         assert np.all(err <= 256 * eps * scale), (prec, (err / scale).max())
     if not c["dirichlet"]:
-        xs = to_gpu_layout(x, K, N, torch.float64)
+        xs = to_gpu_layout(x, K, N, torch.float64, order)
         y0, y1 = torch.empty_like(xs), torch.empty_like(xs)
         s.apply(xs, y0, 0.0, F.FP64)
         s.apply(xs, y1, tau, F.FP64)
