@@ -16,14 +16,14 @@ void launch_apply<float>(const festung_ctx *c, const float *x, float *y, float *
     c->launches += 1;
     dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
         constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
-        const size_t smem = (size_t)4 * 3 * R1 * c->nslot * sizeof(float);
+        const size_t smem = (size_t)4 * 3 * TraceLayout<float, R1>::RP * c->nslot * sizeof(float);
         static size_t configured = 0;
         if (smem > configured) {
             cudaFuncSetAttribute(k_apply_fused<float, N, R2, R1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             configured = smem;
         }
-        k_apply_fused<float, N, R2, R1><<<tiles, 256, smem, st>>>(x, y, c->fD, c->fB, c->dNbr, c->dSlot, c->dHaloPtr,
-                                                                c->dHalo, c->K, c->TE, c->nslot, tau, (float)c->eta,
+        k_apply_fused<float, N, R2, R1><<<tiles, FUSED_THREADS, smem, st>>>(x, y, c->fD, c->fB, c->dNbr, c->dSlot, c->dHaloPtr,
+                                                                c->dHalo, c->dHaloSlot, c->K, c->TE, c->nslot, tau, (float)c->eta,
                                                                 c->fTab, skip);
     });
 }

@@ -14,14 +14,14 @@ void launch_apply<double>(const festung_ctx *c, const double *x, double *y, doub
     c->launches += 1;
     dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
         constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
-        const size_t smem = (size_t)4 * 3 * R1 * c->nslot * sizeof(double);
+        const size_t smem = (size_t)4 * 3 * TraceLayout<double, R1>::RP * c->nslot * sizeof(double);
         static size_t configured = 0;
         if (smem > configured) {
             cudaFuncSetAttribute(k_apply_fused<double, N, R2, R1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             configured = smem;
         }
-        k_apply_fused<double, N, R2, R1><<<tiles, 256, smem, st>>>(x, y, c->dD, c->dB, c->dNbr, c->dSlot, c->dHaloPtr,
-                                                                c->dHalo, c->K, c->TE, c->nslot, tau, (double)c->eta,
+        k_apply_fused<double, N, R2, R1><<<tiles, FUSED_THREADS, smem, st>>>(x, y, c->dD, c->dB, c->dNbr, c->dSlot, c->dHaloPtr,
+                                                                c->dHalo, c->dHaloSlot, c->K, c->TE, c->nslot, tau, (double)c->eta,
                                                                 c->dTab, skip);
     });
 }

@@ -811,11 +811,14 @@ int festung_mesh_create(const double *coordV, int64_t numV, const int32_t *V0T, 
     if ((e = cudaMalloc(&c->dNbr, 3 * K * sizeof(int32_t))) != cudaSuccess) return fail(e);
     std::vector<float> fB(mo.B.begin(), mo.B.end());
     std::vector<int16_t> slot16(mo.slot.begin(), mo.slot.end());
+    std::vector<int16_t> hslot16(mo.halo_slot.begin(), mo.halo_slot.end());
     const int64_t T = (K + mo.TE - 1) / mo.TE;
     if ((e = cudaMalloc(&c->dPerm, K * sizeof(int32_t))) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&c->dSlot, 3 * K * sizeof(int16_t))) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&c->dHaloPtr, (T + 1) * sizeof(int32_t))) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&c->dHalo, std::max<size_t>(1, mo.halo.size()) * sizeof(int32_t))) != cudaSuccess)
+        return fail(e);
+    if ((e = cudaMalloc(&c->dHaloSlot, std::max<size_t>(1, hslot16.size()) * sizeof(int16_t))) != cudaSuccess)
         return fail(e);
     const struct {
         void *dst;
@@ -827,7 +830,8 @@ int festung_mesh_create(const double *coordV, int64_t numV, const int32_t *V0T, 
               {c->dPerm, mo.perm.data(), K * sizeof(int32_t)},
               {c->dSlot, slot16.data(), 3 * K * sizeof(int16_t)},
               {c->dHaloPtr, mo.halo_ptr.data(), (T + 1) * sizeof(int32_t)},
-              {c->dHalo, mo.halo.data(), mo.halo.size() * sizeof(int32_t)}};
+              {c->dHalo, mo.halo.data(), mo.halo.size() * sizeof(int32_t)},
+              {c->dHaloSlot, hslot16.data(), hslot16.size() * sizeof(int16_t)}};
     for (const auto &u : up)
         if (u.bytes && (e = cudaMemcpy(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
     *out = c;
@@ -847,6 +851,10 @@ int festung_setup(festung_ctx *c, int p, int quad_order, double eta) {
     int qT = quad_order == 0 ? std::max(1, 2 * p) : quad_order;
     if (quad_order != 0 && !(quad_order == 2 * p || quad_order == 2 * p + 1 || (p == 0 && quad_order == 1))) {
         c->err = "quad_order must be 0, 2p or 2p+1";
+        return FESTUNG_EINVAL;
+    }
+    if (c->K * (int64_t)num_dofs(p) >= (int64_t(1) << 31)) {
+        c->err = "K * N must stay below 2^31";
         return FESTUNG_EINVAL;
     }
     HostTables T;
@@ -1263,7 +1271,7 @@ void festung_destroy(festung_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_ctx_device(c);
-    void *mesh_ptrs[] = {c->dB, c->fB, c->dNbr, c->dPerm, c->dSlot, c->dHaloPtr, c->dHalo};
+    void *mesh_ptrs[] = {c->dB, c->fB, c->dNbr, c->dPerm, c->dSlot, c->dHaloPtr, c->dHalo, c->dHaloSlot};
     for (void *q : mesh_ptrs)
         if (q) cudaFree(q);
     delete c;

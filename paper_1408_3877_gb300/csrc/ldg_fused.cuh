@@ -1,13 +1,14 @@
 // Single-pass operator apply y = S x (E1) over tiles of nearby triangles.
 //
 // Triangles are stored in Morton order of their centroids, so TE consecutive
-// triangles form a compact patch ("tile").  One thread block handles one tile.  Phase A
-// evaluates, for every triangle of the tile and of its halo (interior neighbours
-// outside the tile), the flux unknowns Z^m = -M^{-1} B_m x (block rows 1-2 of eq.
-// timeDepSystem) and the traces of x, d_h, z^1, z^2 on its three edges at the Gauss
-// points; the traces go to shared memory.  Phase B adds, for every tile triangle, the
-// volume term -sum_m G^m Z^m and the edge terms R^m, R_D^m, S, S_D, reading its
-// neighbours' traces from shared memory.  The flux unknowns never leave the chip.
+// triangles form a compact patch ("tile").  One thread block handles one tile and its
+// halo (the interior neighbours outside the tile), one triangle ("slot") per thread:
+//   A1  traces of x and d_h on the three edges of every slot -> shared memory;
+//   A2  flux unknowns Z^m = -M^{-1} B_m x (block rows 1-2 of eq. timeDepSystem) from
+//       the slot's own and its neighbours' x traces, and their traces -> shared memory;
+//   B   for every tile triangle, the volume term -sum_m G^m Z^m and the edge terms
+//       R^m, R_D^m, S, S_D from its own and its neighbours' traces.
+// The flux unknowns never leave the chip, and every trace is evaluated once per slot.
 #pragma once
 
 #include "ldg_kernels.cuh"
@@ -46,42 +47,100 @@ __device__ __forceinline__ void ctrace(const T (&c)[N], T (&out)[R1]) {
     }
 }
 
-// Shared-memory trace of field f (0: x, 1: d_h, 2: z^1, 3: z^2) on edge n at point r.
-template <int R1>
-__device__ __forceinline__ int tr_index(int f, int n, int r, int slot, int NS) {
-    return ((f * 3 + n) * R1 + r) * NS + slot;
+// Shared-memory traces: field f (0: x, 1: d_h, 2: z^1, 3: z^2) on edge n of slot s
+// occupy RP consecutive values (R1 Gauss points padded to a multiple of 16 bytes), so
+// one thread moves a whole trace with 128-bit accesses.
+template <typename T, int R1>
+struct TraceLayout {
+    static constexpr int per16 = 16 / sizeof(T);
+    static constexpr int RP = ((R1 + per16 - 1) / per16) * per16;
+    static constexpr int nvec = RP / per16;
+};
+
+template <typename T, int R1>
+__device__ __forceinline__ T *tr_ptr(T *tr, int f, int n, int slot, int NS) {
+    return tr + ((size_t)(f * 3 + n) * NS + slot) * TraceLayout<T, R1>::RP;
 }
 
-// Phase A, edge n of triangle e: traces of x and d_h to shared memory, and the edge's
-// contribution nu_en |E_en| int phi_i {c} to B_m x (central flux, eq. globQ; interior
-// value on Neumann edges, eq. globQm:N; nothing on Dirichlet edges).
+template <typename T, int R1>
+__device__ __forceinline__ void tr_store(T *tr, int f, int n, int slot, int NS, const T (&v)[R1]) {
+    using L = TraceLayout<T, R1>;
+    T buf[L::RP];
+#pragma unroll
+    for (int r = 0; r < L::RP; ++r) buf[r] = r < R1 ? v[r] : T(0);
+    float4 *dst = reinterpret_cast<float4 *>(tr_ptr<T, R1>(tr, f, n, slot, NS));
+#pragma unroll
+    for (int q = 0; q < L::nvec; ++q) dst[q] = reinterpret_cast<const float4 *>(buf)[q];
+}
+
+template <typename T, int R1>
+__device__ __forceinline__ void tr_load(const T *tr, int f, int n, int slot, int NS, T (&v)[R1]) {
+    using L = TraceLayout<T, R1>;
+    T buf[L::RP];
+    const float4 *src = reinterpret_cast<const float4 *>(tr_ptr<T, R1>(const_cast<T *>(tr), f, n, slot, NS));
+#pragma unroll
+    for (int q = 0; q < L::nvec; ++q) reinterpret_cast<float4 *>(buf)[q] = src[q];
+#pragma unroll
+    for (int r = 0; r < R1; ++r) v[r] = buf[r];
+}
+
+// Phase A1 for triangle e at shared-memory slot `slot`: loads x and d_h of e and stores
+// their traces on the three edges.
 template <typename T, int N, int R2, int R1, int n>
-__device__ __forceinline__ void slot_edge(const T *phiE_s, const T *__restrict__ X, int64_t K, int code,
-                                          const T (&x)[N], const T (&d)[N], T b11, T b12, T b21, T b22,
-                                          T *tr, int NS, int slot, T (&a1)[N], T (&a2)[N]) {
-    const CTab<T, N, R2, R1> &t = c_tab<T, N, R2, R1>;
+__device__ __forceinline__ void a1_edge(const T (&x)[N], const T (&d)[N], T *tr, int NS, int slot) {
     T xt[R1], dt[R1];
     ctrace<T, N, R2, R1, n>(x, xt);
     ctrace<T, N, R2, R1, n>(d, dt);
+    tr_store<T, R1>(tr, 0, n, slot, NS, xt);
+    tr_store<T, R1>(tr, 1, n, slot, NS, dt);
+}
+
+template <typename T, int N, int R2, int R1>
+__device__ __forceinline__ void slot_a1(const T *__restrict__ X, const T *__restrict__ Dc, int Ki, int e, T *tr,
+                                        int NS, int slot, T (&d)[N]) {
+    T x[N];
 #pragma unroll
-    for (int r = 0; r < R1; ++r) {
-        tr[tr_index<R1>(0, n, r, slot, NS)] = xt[r];
-        tr[tr_index<R1>(1, n, r, slot, NS)] = dt[r];
+    for (int j = 0; j < N; ++j) {
+        x[j] = X[j * Ki + e];
+        d[j] = Dc[j * Ki + e];
     }
+    a1_edge<T, N, R2, R1, 0>(x, d, tr, NS, slot);
+    a1_edge<T, N, R2, R1, 1>(x, d, tr, NS, slot);
+    a1_edge<T, N, R2, R1, 2>(x, d, tr, NS, slot);
+}
+
+// Phase A2, edge n: the edge's contribution nu_en |E_en| int phi_i {c} to B_m x (central
+// flux, eq. globQ; interior value on Neumann edges, eq. globQm:N; nothing on Dirichlet
+// edges).  The neighbour's trace comes from its slot, or from global memory when the
+// neighbour of a halo triangle lies outside the tile's slots (nsl == -2).
+template <typename T, int N, int R2, int R1, int n>
+__device__ __forceinline__ void a2_edge(const T *phiE_s, const T *__restrict__ X, int Ki, int code, int nsl,
+                                        const T *tr, int NS, int slot, T b11, T b12, T b21, T b22, T (&a1)[N],
+                                        T (&a2)[N]) {
     if (code == NBR_DIRICHLET) return;  // c_D enters the right-hand side only
-    T nx, ny;
-    edge_normal(n, b11, b12, b21, b22, nx, ny);
+    const CTab<T, N, R2, R1> &t = c_tab<T, N, R2, R1>;
+    T f[R1];
+    tr_load<T, R1>(tr, 0, n, slot, NS, f);
     if (code >= 0) {
         T cp[R1];
-        trace_nbr<T, N, R1>(phiE_s, X, K, code >> 2, code & 3, cp);
+        if (nsl >= 0) {
+            T nb[R1];
+            tr_load<T, R1>(tr, 0, code & 3, nsl, NS, nb);
 #pragma unroll
-        for (int r = 0; r < R1; ++r) xt[r] = T(0.5) * (xt[r] + cp[r]);
+            for (int r = 0; r < R1; ++r) cp[r] = nb[R1 - 1 - r];  // the maps of eq. mapEE reverse the edge
+        } else {
+            trace_nbr<T, N, R1>(phiE_s, X, (int64_t)Ki, code >> 2, code & 3, cp);
+        }
+#pragma unroll
+        for (int r = 0; r < R1; ++r) f[r] = T(0.5) * (f[r] + cp[r]);
     }
+    T nx, ny;
+    edge_normal(n, b11, b12, b21, b22, nx, ny);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         T v = T(0);
 #pragma unroll
-        for (int r = 0; r < R1; ++r) v += t.wphiE[(n * R1 + r) * N + i] * xt[r];
+        for (int r = 0; r < R1; ++r) v += t.wphiE[(n * R1 + r) * N + i] * f[r];
         a1[i] += nx * v;
         a2[i] += ny * v;
     }
@@ -92,28 +151,21 @@ __device__ __forceinline__ void slot_ztrace(const T (&z1)[N], const T (&z2)[N], 
     T t1[R1], t2[R1];
     ctrace<T, N, R2, R1, n>(z1, t1);
     ctrace<T, N, R2, R1, n>(z2, t2);
-#pragma unroll
-    for (int r = 0; r < R1; ++r) {
-        tr[tr_index<R1>(2, n, r, slot, NS)] = t1[r];
-        tr[tr_index<R1>(3, n, r, slot, NS)] = t2[r];
-    }
+    tr_store<T, R1>(tr, 2, n, slot, NS, t1);
+    tr_store<T, R1>(tr, 3, n, slot, NS, t2);
 }
 
-// Phase A for triangle e stored at shared-memory slot `slot`: Z^m = -M^{-1} B_m x and
-// the traces of x, d_h, z^1, z^2.  Returns Z^1, Z^2 and d_h of e in z1, z2, d.
+// Phase A2 for triangle e at slot `slot`: Z^m = -M^{-1} B_m x, and the traces of z^1,
+// z^2.  nsl[n]: slot of the neighbour across edge n (see a2_edge).
 template <typename T, int N, int R2, int R1>
-__device__ __forceinline__ void slot_traces(const T *phiE_s, const T *__restrict__ X, const T *__restrict__ Dc,
-                                            const T *__restrict__ Bg, const int32_t *__restrict__ nbr, int64_t K,
-                                            int64_t e, T *tr, int NS, int slot, T (&z1)[N], T (&z2)[N],
-                                            T (&d)[N]) {
+__device__ __forceinline__ void slot_a2(const T *phiE_s, const T *__restrict__ X, const T *__restrict__ Bg,
+                                        const int32_t *__restrict__ nbr, int Ki, int e, const int (&nsl)[3],
+                                        T *tr, int NS, int slot, T (&z1)[N], T (&z2)[N]) {
     const CTab<T, N, R2, R1> &t = c_tab<T, N, R2, R1>;
     T x[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-        x[j] = X[j * K + e];
-        d[j] = Dc[j * K + e];
-    }
-    const T b11 = Bg[e], b12 = Bg[K + e], b21 = Bg[2 * K + e], b22 = Bg[3 * K + e];
+    for (int j = 0; j < N; ++j) x[j] = X[j * Ki + e];
+    const T b11 = Bg[e], b12 = Bg[Ki + e], b21 = Bg[2 * Ki + e], b22 = Bg[3 * Ki + e];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         T h1 = T(0), h2 = T(0);
@@ -126,10 +178,10 @@ __device__ __forceinline__ void slot_traces(const T *phiE_s, const T *__restrict
         z1[i] = -(b22 * h1 - b21 * h2);
         z2[i] = -(b11 * h2 - b12 * h1);
     }
-    const int c0 = nbr[e], c1 = nbr[K + e], c2 = nbr[2 * K + e];
-    slot_edge<T, N, R2, R1, 0>(phiE_s, X, K, c0, x, d, b11, b12, b21, b22, tr, NS, slot, z1, z2);
-    slot_edge<T, N, R2, R1, 1>(phiE_s, X, K, c1, x, d, b11, b12, b21, b22, tr, NS, slot, z1, z2);
-    slot_edge<T, N, R2, R1, 2>(phiE_s, X, K, c2, x, d, b11, b12, b21, b22, tr, NS, slot, z1, z2);
+    const int c0 = nbr[e], c1 = nbr[Ki + e], c2 = nbr[2 * Ki + e];
+    a2_edge<T, N, R2, R1, 0>(phiE_s, X, Ki, c0, nsl[0], tr, NS, slot, b11, b12, b21, b22, z1, z2);
+    a2_edge<T, N, R2, R1, 1>(phiE_s, X, Ki, c1, nsl[1], tr, NS, slot, b11, b12, b21, b22, z1, z2);
+    a2_edge<T, N, R2, R1, 2>(phiE_s, X, Ki, c2, nsl[2], tr, NS, slot, b11, b12, b21, b22, z1, z2);
     const T inv = T(-1) / (b11 * b22 - b12 * b21);  // Z = -M^{-1} (B_m x), M = 2|T_e| I
 #pragma unroll
     for (int i = 0; i < N; ++i) {
@@ -150,27 +202,27 @@ __device__ __forceinline__ void tile_edge(int code, int sl, const T *tr, int NS,
     const CTab<T, N, R2, R1> &t = c_tab<T, N, R2, R1>;
     T nx, ny;
     edge_normal(n, b11, b12, b21, b22, nx, ny);
-    T g[R1];
+    T g[R1], xm[R1], dm[R1], am[R1], bm[R1];
+    tr_load<T, R1>(tr, 0, n, i, NS, xm);
+    tr_load<T, R1>(tr, 1, n, i, NS, dm);
+    tr_load<T, R1>(tr, 2, n, i, NS, am);
+    tr_load<T, R1>(tr, 3, n, i, NS, bm);
     if (code >= 0) {
         const int n2 = code & 3;
+        T xp[R1], dp[R1], ap[R1], bp[R1];
+        tr_load<T, R1>(tr, 0, n2, sl, NS, xp);
+        tr_load<T, R1>(tr, 1, n2, sl, NS, dp);
+        tr_load<T, R1>(tr, 2, n2, sl, NS, ap);
+        tr_load<T, R1>(tr, 3, n2, sl, NS, bp);
 #pragma unroll
         for (int r = 0; r < R1; ++r) {
             const int rp = R1 - 1 - r;  // the neighbour's Gauss point at our point r (eq. mapEE)
-            const T xm = tr[tr_index<R1>(0, n, r, i, NS)], xp = tr[tr_index<R1>(0, n2, rp, sl, NS)];
-            const T dm = tr[tr_index<R1>(1, n, r, i, NS)], dp = tr[tr_index<R1>(1, n2, rp, sl, NS)];
-            const T am = tr[tr_index<R1>(2, n, r, i, NS)], ap = tr[tr_index<R1>(2, n2, rp, sl, NS)];
-            const T bm = tr[tr_index<R1>(3, n, r, i, NS)], bp = tr[tr_index<R1>(3, n2, rp, sl, NS)];
-            g[r] = T(0.5) * (nx * (dm * am + dp * ap) + ny * (dm * bm + dp * bp)) + eta * (xm - xp);
+            g[r] = T(0.5) * (nx * (dm[r] * am[r] + dp[rp] * ap[rp]) + ny * (dm[r] * bm[r] + dp[rp] * bp[rp])) +
+                   eta * (xm[r] - xp[rp]);
         }
     } else {  // Dirichlet
 #pragma unroll
-        for (int r = 0; r < R1; ++r) {
-            const T xm = tr[tr_index<R1>(0, n, r, i, NS)];
-            const T dm = tr[tr_index<R1>(1, n, r, i, NS)];
-            const T am = tr[tr_index<R1>(2, n, r, i, NS)];
-            const T bm = tr[tr_index<R1>(3, n, r, i, NS)];
-            g[r] = dm * (nx * am + ny * bm) + eta * xm;
-        }
+        for (int r = 0; r < R1; ++r) g[r] = dm[r] * (nx * am[r] + ny * bm[r]) + eta * xm[r];
     }
 #pragma unroll
     for (int j = 0; j < N; ++j) {
@@ -181,43 +233,13 @@ __device__ __forceinline__ void tile_edge(int code, int sl, const T *tr, int NS,
     }
 }
 
+constexpr int FUSED_THREADS = 320;  // a tile of 256 triangles plus up to 64 halo triangles per round
+
+// volume term -sum_m G^m Z^m at the triangle points (Sec. 3.6.3), tables in the constant bank
 template <typename T, int N, int R2, int R1>
-__global__ void __launch_bounds__(256) k_apply_fused(const T *__restrict__ X, T *__restrict__ Y,
-                                                     const T *__restrict__ Dc, const T *__restrict__ Bg,
-                                                     const int32_t *__restrict__ nbr, const int16_t *__restrict__ slotg,
-                                                     const int32_t *__restrict__ halo_ptr,
-                                                     const int32_t *__restrict__ halo, int64_t K, int TE, int NS,
-                                                     T tau, T eta, const T *__restrict__ tabg,
-                                                     const int *__restrict__ skip) {
-    __shared__ T phiE_s[3 * R1 * N];
-    extern __shared__ __align__(16) unsigned char dyn_smem[];
-    T *tr = reinterpret_cast<T *>(dyn_smem);
-    if (skip && *skip) return;
-    {
-        const int o_phiE = 4 * R2 * N + 2 * N * N;  // table layout of table_offsets()
-        for (int j = threadIdx.x; j < 3 * R1 * N; j += blockDim.x) phiE_s[j] = tabg[o_phiE + j];
-    }
-    const int64_t start = (int64_t)blockIdx.x * TE;
-    const int cnt = (int)((K - start) < TE ? (K - start) : TE);
-    const int h0 = halo_ptr[blockIdx.x], nh = halo_ptr[blockIdx.x + 1] - h0;
-    __syncthreads();
-    for (int j = threadIdx.x; j < nh; j += blockDim.x) {
-        T z1[N], z2[N], d[N];
-        slot_traces<T, N, R2, R1>(phiE_s, X, Dc, Bg, nbr, K, halo[h0 + j], tr, NS, TE + j, z1, z2, d);
-    }
-    const int i = threadIdx.x;
-    const bool own = i < cnt;
-    const int64_t k = start + i;
-    T z1[N], z2[N], d[N];
-    if (own) slot_traces<T, N, R2, R1>(phiE_s, X, Dc, Bg, nbr, K, k, tr, NS, i, z1, z2, d);
-    __syncthreads();
-    if (!own) return;
+__device__ __forceinline__ void volume_const(const T (&d)[N], const T (&z1)[N], const T (&z2)[N], T b11, T b12,
+                                             T b21, T b22, T (&acc)[N]) {
     const CTab<T, N, R2, R1> &t = c_tab<T, N, R2, R1>;
-    const T b11 = Bg[k], b12 = Bg[K + k], b21 = Bg[2 * K + k], b22 = Bg[3 * K + k];
-    T acc[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) acc[j] = T(0);
-    // volume term -sum_m G^m Z^m at the triangle points (Sec. 3.6.3)
 #pragma unroll
     for (int r = 0; r < R2; ++r) {
         T dv = T(0), w1 = T(0), w2 = T(0);
@@ -233,13 +255,116 @@ __global__ void __launch_bounds__(256) k_apply_fused(const T *__restrict__ X, T 
 #pragma unroll
         for (int j = 0; j < N; ++j) acc[j] -= t.gw1[r * N + j] * u + t.gw2[r * N + j] * v;
     }
-    const int c0 = nbr[k], c1 = nbr[K + k], c2 = nbr[2 * K + k];
+}
+
+// the same with the point loop rolled and the tables read from shared memory in
+// 16-byte vectors (row stride NP = N rounded up to 16 bytes); keeps the code of the
+// high orders small
+template <typename T, int N, int R2, int NP>
+__device__ __forceinline__ void volume_smem(const T *phiQ_s, const T *gw1_s, const T *gw2_s, const T (&d)[N],
+                                            const T (&z1)[N], const T (&z2)[N], T b11, T b12, T b21, T b22,
+                                            T (&acc)[N]) {
+#pragma unroll 1
+    for (int r = 0; r < R2; ++r) {
+        T ph[NP], g1[NP], g2[NP];
+#pragma unroll
+        for (int q = 0; q < NP * (int)sizeof(T) / 16; ++q) {
+            reinterpret_cast<float4 *>(ph)[q] = reinterpret_cast<const float4 *>(phiQ_s + r * NP)[q];
+            reinterpret_cast<float4 *>(g1)[q] = reinterpret_cast<const float4 *>(gw1_s + r * NP)[q];
+            reinterpret_cast<float4 *>(g2)[q] = reinterpret_cast<const float4 *>(gw2_s + r * NP)[q];
+        }
+        T dv = T(0), w1 = T(0), w2 = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            dv += ph[j] * d[j];
+            w1 += ph[j] * z1[j];
+            w2 += ph[j] * z2[j];
+        }
+        const T u = dv * (b22 * w1 - b12 * w2);
+        const T v = dv * (b11 * w2 - b21 * w1);
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc[j] -= g1[j] * u + g2[j] * v;
+    }
+}
+
+template <typename T, int N, int R2, int R1>
+__global__ void __launch_bounds__(FUSED_THREADS) k_apply_fused(
+    const T *__restrict__ X, T *__restrict__ Y, const T *__restrict__ Dc, const T *__restrict__ Bg,
+    const int32_t *__restrict__ nbr, const int16_t *__restrict__ slotg, const int32_t *__restrict__ halo_ptr,
+    const int32_t *__restrict__ halo, const int16_t *__restrict__ halo_slot, int64_t K, int TE, int NS, T tau,
+    T eta, const T *__restrict__ tabg, const int *__restrict__ skip) {
+    constexpr bool kBigVolume = R2 * N > 150;
+    constexpr int NP = ((N * (int)sizeof(T) + 15) / 16) * 16 / (int)sizeof(T);
+    constexpr int VOL = kBigVolume ? 3 * R2 * NP : 4;
+    __shared__ __align__(16) T phiE_s[3 * R1 * N];
+    __shared__ __align__(16) T vol_s[VOL];
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    T *tr = reinterpret_cast<T *>(dyn_smem);
+    if (skip && *skip) return;
+    const int Ki = (int)K;  // K * N < 2^31 (checked at setup): 32-bit offsets
+    {
+        const int o_phiE = 4 * R2 * N + 2 * N * N;  // table layout of table_offsets()
+        for (int j = threadIdx.x; j < 3 * R1 * N; j += blockDim.x) phiE_s[j] = tabg[o_phiE + j];
+        if (kBigVolume) {
+            const int o_phiQ = 0, o_gw1 = 2 * R2 * N, o_gw2 = 3 * R2 * N;
+            for (int j = threadIdx.x; j < R2 * NP; j += blockDim.x) {
+                const int r = j / NP, c = j - r * NP;
+                vol_s[j] = c < N ? tabg[o_phiQ + r * N + c] : T(0);
+                vol_s[R2 * NP + j] = c < N ? tabg[o_gw1 + r * N + c] : T(0);
+                vol_s[2 * R2 * NP + j] = c < N ? tabg[o_gw2 + r * N + c] : T(0);
+            }
+        }
+    }
+    const int start = blockIdx.x * TE;
+    const int cnt = (Ki - start) < TE ? (Ki - start) : TE;
+    const int h0 = halo_ptr[blockIdx.x], nh = halo_ptr[blockIdx.x + 1] - h0;
+    const int i = threadIdx.x;
+    const int hstride = blockDim.x - TE;
+    T z1[N], z2[N], d[N];
+    // A1: traces of x and d_h of every slot (tile triangles keep d_h in registers)
+    if (i < TE) {
+        if (i < cnt) slot_a1<T, N, R2, R1>(X, Dc, Ki, start + i, tr, NS, i, d);
+    } else {
+        for (int j = i - TE; j < nh; j += hstride) {
+            T hd[N];
+            slot_a1<T, N, R2, R1>(X, Dc, Ki, halo[h0 + j], tr, NS, TE + j, hd);
+        }
+    }
+    __syncthreads();
+    // A2: flux unknowns and their traces
+    if (i < TE) {
+        if (i < cnt) {
+            const int k = start + i;
+            const int nsl[3] = {slotg[k], slotg[Ki + k], slotg[2 * Ki + k]};
+            slot_a2<T, N, R2, R1>(phiE_s, X, Bg, nbr, Ki, k, nsl, tr, NS, i, z1, z2);
+        }
+    } else {
+        for (int j = i - TE; j < nh; j += hstride) {
+            const int q = 3 * (h0 + j);
+            const int nsl[3] = {halo_slot[q], halo_slot[q + 1], halo_slot[q + 2]};
+            T hz1[N], hz2[N];
+            slot_a2<T, N, R2, R1>(phiE_s, X, Bg, nbr, Ki, halo[h0 + j], nsl, tr, NS, TE + j, hz1, hz2);
+        }
+    }
+    __syncthreads();
+    if (i >= cnt) return;
+    // B: volume and edge terms of the tile triangles
+    const int k = start + i;
+    const T b11 = Bg[k], b12 = Bg[Ki + k], b21 = Bg[2 * Ki + k], b22 = Bg[3 * Ki + k];
+    T acc[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) acc[j] = T(0);
+    if (kBigVolume)
+        volume_smem<T, N, R2, NP>(vol_s, vol_s + R2 * NP, vol_s + 2 * R2 * NP, d, z1, z2, b11, b12, b21, b22, acc);
+    else
+        volume_const<T, N, R2, R1>(d, z1, z2, b11, b12, b21, b22, acc);
+    const int c0 = nbr[k], c1 = nbr[Ki + k], c2 = nbr[2 * Ki + k];
     tile_edge<T, N, R2, R1, 0>(c0, c0 >= 0 ? slotg[k] : 0, tr, NS, i, b11, b12, b21, b22, eta, acc);
-    tile_edge<T, N, R2, R1, 1>(c1, c1 >= 0 ? slotg[K + k] : 0, tr, NS, i, b11, b12, b21, b22, eta, acc);
-    tile_edge<T, N, R2, R1, 2>(c2, c2 >= 0 ? slotg[2 * K + k] : 0, tr, NS, i, b11, b12, b21, b22, eta, acc);
+    tile_edge<T, N, R2, R1, 1>(c1, c1 >= 0 ? slotg[Ki + k] : 0, tr, NS, i, b11, b12, b21, b22, eta, acc);
+    tile_edge<T, N, R2, R1, 2>(c2, c2 >= 0 ? slotg[2 * Ki + k] : 0, tr, NS, i, b11, b12, b21, b22, eta, acc);
     const T det = b11 * b22 - b12 * b21;
 #pragma unroll
-    for (int j = 0; j < N; ++j) Y[j * K + k] = det * X[j * K + k] + tau * acc[j];
+    for (int j = 0; j < N; ++j) Y[j * Ki + k] = det * X[j * Ki + k] + tau * acc[j];
 }
 
 }  // namespace festung

@@ -171,6 +171,7 @@ void order_and_tile(const double *coordV, const int32_t *V0T, int64_t K, const s
     const int64_t T = (K + TE - 1) / TE;
     o.halo_ptr.assign(T + 1, 0);
     o.halo.clear();
+    o.halo_slot.clear();
     o.slot.assign(3 * K, -1);
     o.max_halo = 0;
     std::vector<int32_t> h;
@@ -197,6 +198,23 @@ void order_and_tile(const double *coordV, const int32_t *V0T, int64_t K, const s
                     const int64_t pos = std::lower_bound(h.begin(), h.end(), (int32_t)k2) - h.begin();
                     o.slot[n * K + i] = (int32_t)(TE + pos);
                 }
+            }
+        // neighbours of the halo triangles: their slot if they are resident (tile or
+        // halo), -1 on the boundary, -2 if they lie outside the tile's slots
+        for (int32_t e : h)
+            for (int n = 0; n < 3; ++n) {
+                const int32_t code = o.nbr[n * K + e];
+                int32_t sl = -1;
+                if (code >= 0) {
+                    const int64_t k2 = code >> 2;
+                    if (k2 >= s0 && k2 < s1) {
+                        sl = (int32_t)(k2 - s0);
+                    } else {
+                        auto it = std::lower_bound(h.begin(), h.end(), (int32_t)k2);
+                        sl = (it != h.end() && *it == k2) ? (int32_t)(TE + (it - h.begin())) : -2;
+                    }
+                }
+                o.halo_slot.push_back(sl);
             }
         o.halo.insert(o.halo.end(), h.begin(), h.end());
         o.halo_ptr[t + 1] = (int32_t)o.halo.size();
