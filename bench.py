@@ -297,7 +297,7 @@ def run_festung(args):
 
     if rank != 0:
         return None
-    roof = {"bound": "alu", "kernel": "FP32 operator apply (k_flux + k_apply), %s" % CFG_NAME,
+    roof = {"bound": "alu", "kernel": "FP32 fused operator apply (k_apply_fused), %s" % CFG_NAME,
             "achieved": apply_main["fp32"]["tflops"], "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": apply_main["fp32"]["tflops"] / fp32_peak, "traffic": None,
             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock (derived; not in the measured peaks)"}

@@ -85,6 +85,8 @@ typedef struct festung_step_info {
     double rel_residual; /* final ||b - S C||_2 / ||b||_2, evaluated in FP64                    */
     int    solver;       /* FESTUNG_SOLVER_CG or FESTUNG_SOLVER_BICGSTAB                        */
     int    symmetric;    /* 1 if d_h is elementwise constant (S symmetric, Sec. 2.4.3-2.4.4)   */
+    int    fp64_iterations; /* FESTUNG_MIXED: iterations of the FP64 solve that finished the step
+                               after an FP32 sweep failed to lower the residual (else 0)            */
 } festung_step_info;
 
 /* Build the grid lists of Tab. 1 (Sec. 3.1, routine generateGridData): edges,
@@ -165,8 +167,10 @@ int festung_apply(festung_ctx *ctx, const void *x, void *y, int prec, double dt)
 int festung_apply_noalloc(festung_ctx *ctx, const void *x, void *y, int prec, double dt);
 
 /* One implicit-Euler step of size dt (Sec. 2.5): forms b of (E2) from the current
- * C, D, f and boundary data, solves (E1) from the initial guess C^n and, only on
- * success, replaces C by C^{n+1}.  opts may be NULL (tol 1e-10, max_iter 20000,
+ * C, D, f and boundary data, solves (E1) and, only on success, replaces C by C^{n+1}.
+ * The initial guess is C^n + dt/dt_prev (C^n - C^{n-1}) after a successful step of
+ * size dt_prev (linear extrapolation in time), else C^n; festung_set_state and
+ * festung_setup reset this history.  Preconditioner: inverse N x N diagonal blocks of S.  opts may be NULL (tol 1e-10, max_iter 20000,
  * FESTUNG_MIXED, inner_tol 1e-2, max_outer 50).  info may be NULL.  Synchronises
  * the context's stream.  Errors: ENOCONV (C unchanged), EINVAL, ESTATE, ECUDA. */
 int festung_step(festung_ctx *ctx, double dt, const festung_step_opts *opts,

@@ -61,6 +61,7 @@ struct Workspace {
     double *scratch64 = nullptr;  // W^1, W^2 of the Dirichlet lift (2 x N x K)
     int *d_flags = nullptr, *h_flags = nullptr;
     float *P = nullptr;        // block-Jacobi inverse blocks [(i N + j) K + k]
+    double *res = nullptr, *h_res = nullptr;  // device / pinned host pair for residual norms
     bool use_P = false;        // P is valid for the current step
     GraphCache g64, g32;
 };
@@ -158,9 +159,12 @@ __global__ void k_inv_det(const T *__restrict__ B, T *__restrict__ inv, int64_t 
 // ---------------------------------------------------------------------------
 #define ELEM_LOOP(k) for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x)
 
-// r = b - y (y = S x, or y = null for x = 0); r0 = r; p = v = 0; partials (r,r), (b,b)
+// r = b - y (y = S x, or y = null for x = 0); shadow r0 = r (or, after a restart, r
+// with a fixed pseudo-random reweighting so that the new Krylov process differs);
+// p = v = 0; partials (r,r), (b,b)
 template <typename T>
-__global__ void k_kr_init(int64_t K, int N, const T *b, const T *y, T *r, T *r0, T *p, T *v, double *part) {
+__global__ void k_kr_init(int64_t K, int N, const T *b, const T *y, T *r, T *r0, T *p, T *v, double *part,
+                          int reweight) {
     using A = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
     A acc[2] = {A(0), A(0)};
     ELEM_LOOP(k) {
@@ -169,7 +173,12 @@ __global__ void k_kr_init(int64_t K, int N, const T *b, const T *y, T *r, T *r0,
             const T bi = b[i];
             const T ri = y ? bi - y[i] : bi;
             r[i] = ri;
-            r0[i] = ri;
+            T wgt = T(1);
+            if (reweight) {
+                const uint32_t h = (uint32_t)(i * 2654435761ull) >> 8;
+                wgt = T(0.5) + T(h & 0xffff) / T(65536);
+            }
+            r0[i] = ri * wgt;
             if (p) p[i] = T(0);
             if (v) v[i] = T(0);
             acc[0] += (A)ri * (A)ri;
@@ -435,6 +444,21 @@ __global__ void k_cg_p(int64_t K, int N, T *p, const T *z, const KScal *sc) {
     }
 }
 
+// partials of ||b - y||^2 and ||b||^2 in precision T
+template <typename T>
+__global__ void k_residual(int64_t K, int N, const T *b, const T *y, double *part) {
+    using A = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
+    A acc[2] = {A(0), A(0)};
+    ELEM_LOOP(k) {
+        for (int j = 0; j < N; ++j) {
+            const A bi = (A)b[j * K + k], ri = bi - (A)y[j * K + k];
+            acc[0] += ri * ri;
+            acc[1] += bi * bi;
+        }
+    }
+    block_partials<2>(acc, part);
+}
+
 // refinement helpers
 __global__ void k_residual64(int64_t n, const double *b, const double *y, double *r, double *part) {
     double acc[2] = {0.0, 0.0};
@@ -470,6 +494,12 @@ __global__ void k_commit_coeff(int64_t n, const double *src, double *d, float *f
         d[i] = v;
         f[i] = (float)v;
     }
+}
+
+// x = C + a (C - C_prev)
+__global__ void k_extrapolate(int64_t n, const double *C, const double *Cp, double *x, double a) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = C[i] + a * (C[i] - Cp[i]);
 }
 
 __global__ void k_zero_f32(int64_t n, float *a) {
@@ -519,6 +549,8 @@ int ensure_ws(festung_ctx *c) {
         FCK(cudaMalloc(&w.scal, sizeof(KScal)));
         FCK(cudaMallocHost(&w.h_scal, sizeof(KScal)));
         FCK(cudaMalloc(&w.d_flags, sizeof(int) * 4));
+        FCK(cudaMalloc(&w.res, sizeof(double) * 2));
+        FCK(cudaMallocHost(&w.h_res, sizeof(double) * 2));
         FCK(cudaMallocHost(&w.h_flags, sizeof(int) * 4));
     }
     return FESTUNG_OK;
@@ -543,16 +575,19 @@ void free_ctx_device(festung_ctx *c) {
         if (c->ws->scratch64) cudaFree(c->ws->scratch64);
         if (c->ws->d_flags) cudaFree(c->ws->d_flags);
         if (c->ws->P) cudaFree(c->ws->P);
+        if (c->ws->res) cudaFree(c->ws->res);
+        if (c->ws->h_res) cudaFreeHost(c->ws->h_res);
         if (c->ws->h_flags) cudaFreeHost(c->ws->h_flags);
         delete c->ws;
         c->ws = nullptr;
     }
-    void *ptrs[] = {c->dTab, c->fTab, c->dC, c->dD, c->dF, c->fD, c->dCD, c->dGN, c->dSamp};
+    void *ptrs[] = {c->dTab, c->fTab, c->dC, c->dD, c->dF, c->fD, c->dCD, c->dGN, c->dSamp, c->dCprev};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     c->dTab = nullptr;
     c->fTab = nullptr;
-    c->dC = c->dD = c->dF = c->dCD = c->dGN = c->dSamp = nullptr;
+    c->dC = c->dD = c->dF = c->dCD = c->dGN = c->dSamp = c->dCprev = nullptr;
+    c->hist_valid = false;
     c->fD = nullptr;
 }
 
@@ -614,7 +649,7 @@ bool ready(festung_ctx *c) {
 // ---------------------------------------------------------------------------
 // Krylov drivers
 // ---------------------------------------------------------------------------
-constexpr int CHUNK = 8;  // iterations per captured graph
+constexpr int CHUNK = 16;  // iterations per captured graph
 
 // record `CHUNK` iterations of the solver on stream st
 template <typename T>
@@ -675,10 +710,10 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
     for (int restart = 0; restart < 8; ++restart) {
         // r = b - S x
         if (x_zero && restart == 0) {
-            k_kr_init<T><<<g, RED_THREADS, 0, st>>>(K, N, V.b, nullptr, V.r, V.r0, V.p, V.v, w.part); ++c->launches;
+            k_kr_init<T><<<g, RED_THREADS, 0, st>>>(K, N, V.b, nullptr, V.r, V.r0, V.p, V.v, w.part, 0); ++c->launches;
         } else {
             launch_apply<T>(c, V.x, V.t, V.Z1, V.Z2, (T)tau, nullptr, st);
-            k_kr_init<T><<<g, RED_THREADS, 0, st>>>(K, N, V.b, V.t, V.r, V.r0, V.p, V.v, w.part); ++c->launches;
+            k_kr_init<T><<<g, RED_THREADS, 0, st>>>(K, N, V.b, V.t, V.r, V.r0, V.p, V.v, w.part, restart > 0); ++c->launches;
         }
         k_fin_init<<<1, 1024, 0, st>>>(w.scal, w.part, g, tol); ++c->launches;
         if (solver == FESTUNG_SOLVER_CG) {
@@ -714,7 +749,7 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
             gc.tau = tau;
             gc.use_P = (int)w.use_P;
         }
-        bool brk = false;
+        bool brk = false, drift = false;
         while (true) {
             FCK(cudaMemcpyAsync(w.h_scal, w.scal, sizeof(KScal), cudaMemcpyDeviceToHost, st));
             FCK(cudaStreamSynchronize(st));
@@ -730,7 +765,20 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
                 if (h.breakdown) {
                     brk = true;
                 } else {
-                    *conv = true;
+                    // the recursively updated residual can drift from b - S x in low
+                    // precision: check the true residual and restart if it is off by > 10x
+                    launch_apply<T>(c, V.x, V.t, V.Z1, V.Z2, (T)tau, nullptr, st);
+                    k_residual<T><<<g, RED_THREADS, 0, st>>>(K, N, V.b, V.t, w.part); ++c->launches;
+                    k_fin_sums<<<1, 1024, 0, st>>>(w.res, w.part, g, 2); ++c->launches;
+                    FCK(cudaMemcpyAsync(w.h_res, w.res, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+                    FCK(cudaStreamSynchronize(st));
+                    const double tr2 = w.h_res[0], tb2 = w.h_res[1];
+                    if (tr2 <= 100.0 * tol * tol * tb2 || restart >= 3) {
+                        *conv = tr2 <= 100.0 * tol * tol * tb2;
+                        *r2 = tr2;
+                    } else {
+                        drift = true;
+                    }
                 }
                 break;
             }
@@ -744,8 +792,8 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
             FCK(cudaGraphLaunch(gc.exec, st));
             c->launches += gc.nodes;
         }
-        if (!brk) break;
-        // breakdown: restart from the current iterate
+        if (!brk && !drift) break;
+        // breakdown or drift: restart from the current iterate
     }
     *iters = total;
     return FESTUNG_OK;
@@ -1046,6 +1094,7 @@ int festung_set_state(festung_ctx *c, const double *C, int is_samples, int loc) 
         k_to_internal<<<small_grid(KN, c), 256, 0, c->stream>>>(tmp, c->dC, c->K, c->N, c->dPerm); ++c->launches;
         FCK(cudaGetLastError());
     }
+    c->hist_valid = false;
     FCK(cudaStreamSynchronize(c->stream));
     return FESTUNG_OK;
 }
@@ -1127,11 +1176,17 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
     FCK(cudaMemsetAsync(w.d_flags, 0, sizeof(int), st));
     launch_blockjacobi(c, w.P, dt, w.d_flags, st);
     FCK(cudaGetLastError());
-    FCK(cudaMemcpyAsync(V.x, c->dC, KN * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    // initial guess: linear extrapolation in time from the two previous states when the
+    // previous step exists, else C^n (the result does not depend on it beyond the tolerance)
+    if (c->hist_valid && c->dt_prev > 0.0) {
+        k_extrapolate<<<small_grid(KN, c), 256, 0, st>>>(KN, c->dC, c->dCprev, V.x, dt / c->dt_prev); ++c->launches;
+    } else {
+        FCK(cudaMemcpyAsync(V.x, c->dC, KN * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
     FCK(cudaMemcpyAsync(w.h_flags, w.d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     FCK(cudaStreamSynchronize(st));
     w.use_P = (w.h_flags[0] == 0);
-    int iters = 0, outer = 0;
+    int iters = 0, outer = 0, iters64 = 0;
     double r2 = 0, b2 = 0;
     bool conv = false;
     double relres = 0.0;
@@ -1155,6 +1210,7 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
         // finishes in FP64.
         Vecs<float> &F = w.f;
         double prev_rn = -1.0, last_scale = 0.0;
+        int failures = 0;
         for (outer = 1; outer <= o.max_outer; ++outer) {
             double rn, bn;
             if ((rc = residual64(&rn, &bn))) return rc;
@@ -1163,10 +1219,17 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
                 conv = true;
                 break;
             }
-            if (prev_rn >= 0.0 && !(rn < 0.9 * prev_rn)) {
+            if (prev_rn >= 0.0 && !(rn < prev_rn)) {
+                // the sweep did not lower the residual: undo it; retry once in FP32
+                // (fresh shadow residual), then finish in FP64
                 k_add_f32<<<small_grid(KN, c), 256, 0, st>>>(KN, V.x, F.x, -last_scale); ++c->launches;
-                fp64 = true;
-                break;
+                if (++failures >= 2) {
+                    fp64 = true;
+                    break;
+                }
+                if ((rc = residual64(&rn, &bn))) return rc;
+            } else {
+                failures = 0;
             }
             if (iters >= o.max_iter) break;
             prev_rn = rn;
@@ -1192,6 +1255,7 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
                                       &conv);
             if (rc) return rc;
             iters += it;
+            if (o.prec == FESTUNG_MIXED) iters64 += it;
             double rn, bn;
             if ((rc = residual64(&rn, &bn))) return rc;
             relres = bn > 0 ? rn / bn : rn;
@@ -1206,13 +1270,18 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
         info->rel_residual = relres;
         info->solver = solver;
         info->symmetric = c->symmetric ? 1 : 0;
+        info->fp64_iterations = iters64;
     }
     if (!conv) {
         c->err = "Krylov solve did not converge (relative residual " + std::to_string(relres) + ")";
         return FESTUNG_ENOCONV;
     }
+    if (!c->dCprev) FCK(cudaMalloc(&c->dCprev, KN * sizeof(double)));
+    FCK(cudaMemcpyAsync(c->dCprev, c->dC, KN * sizeof(double), cudaMemcpyDeviceToDevice, st));
     FCK(cudaMemcpyAsync(c->dC, V.x, KN * sizeof(double), cudaMemcpyDeviceToDevice, st));
     FCK(cudaStreamSynchronize(st));
+    c->hist_valid = true;
+    c->dt_prev = dt;
     return FESTUNG_OK;
 }
 

@@ -33,7 +33,7 @@ class StepOpts(ctypes.Structure):
 
 class StepInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("outer", ctypes.c_int), ("rel_residual", ctypes.c_double),
-                ("solver", ctypes.c_int), ("symmetric", ctypes.c_int)]
+                ("solver", ctypes.c_int), ("symmetric", ctypes.c_int), ("fp64_iterations", ctypes.c_int)]
 
 
 class FestungError(RuntimeError):
@@ -185,7 +185,7 @@ class Solver:
         info = StepInfo()
         self._check(self.lib.festung_step(self.h, dt, ctypes.byref(o), ctypes.byref(info)))
         return {"iterations": info.iterations, "outer": info.outer, "rel_residual": info.rel_residual,
-                "solver": info.solver, "symmetric": info.symmetric}
+                "solver": info.solver, "symmetric": info.symmetric, "fp64_iterations": info.fp64_iterations}
 
     def element_order(self):
         """order[i] = caller's index of the triangle at position i of the device layout."""
