@@ -40,16 +40,6 @@ void launch_rhs(const festung_ctx *c, double *W1, double *W2, double *b, double 
 }
 
 template <>
-void launch_precond<double>(const festung_ctx *c, const float *P, const double *x, double *y, double *part, int nblk,
-                            const int *skip, cudaStream_t st) {
-    c->launches += 1;
-    dispatch(c->N, c->R2, c->R1, [&](auto n_, auto, auto) {
-        constexpr int N = decltype(n_)::value;
-        k_precond<double, N><<<part ? nblk : elem_grid(c), 256, 0, st>>>(P, x, y, c->K, part, skip);
-    });
-}
-
-template <>
 void launch_apply_twopass<double>(const festung_ctx *c, const double *x, double *y, double *Z1, double *Z2, double tau,
                                   const int *skip, cudaStream_t st) {
     const int grid = elem_grid(c);

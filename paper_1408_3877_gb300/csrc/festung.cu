@@ -13,6 +13,7 @@
 
 #include "internal.h"
 #include "krylov.cuh"
+#include "krylov_kernels.cuh"
 #include "dispatch.h"
 #include "ops.h"
 
@@ -60,7 +61,10 @@ struct Workspace {
     int nblk = 0;
     double *scratch64 = nullptr;  // W^1, W^2 of the Dirichlet lift (2 x N x K)
     int *d_flags = nullptr, *h_flags = nullptr;
-    float *P = nullptr;        // block-Jacobi inverse blocks [(i N + j) K + k]
+    float *P = nullptr;            // block-Jacobi diagonal blocks (FP32 scratch of the build)
+    __nv_bfloat16 *Pb = nullptr;   // their inverses in BF16, [(i N + j) K + k]
+    unsigned int *counter = nullptr;  // last-block counter of the reducing Krylov kernels
+    double *part2 = nullptr;          // second partials buffer (CG: (r, r))
     double *res = nullptr, *h_res = nullptr;  // device / pinned host pair for residual norms
     bool use_P = false;        // P is valid for the current step
     GraphCache g64, g32;
@@ -207,240 +211,12 @@ __global__ void k_fin_init(KScal *sc, const double *part, int nblk, double tol) 
     }
 }
 
-// BiCGStab (right preconditioner P^{-1} = M^{-1}): p = r + beta (p - omega v); ph = P^{-1} p
-template <typename T>
-__global__ void k_bicg_p(int64_t K, int N, const T *r, T *p, const T *v, T *ph, const T *inv, const KScal *sc) {
-    if (sc->done) return;
-    const T beta = (T)sc->beta, omega = (T)sc->omega;
-    ELEM_LOOP(k) {
-        const T iv = inv ? inv[k] : T(0);
-        for (int j = 0; j < N; ++j) {
-            const int64_t i = j * K + k;
-            const T pi = r[i] + beta * (p[i] - omega * v[i]);
-            p[i] = pi;
-            if (inv) ph[i] = pi * iv;
-        }
-    }
-}
-
-template <typename T>
-__global__ void k_dot1(int64_t K, int N, const T *a, const T *b, double *part, const KScal *sc) {
-    if (sc->done) return;
-    using A = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
-    A acc[1] = {A(0)};
-    ELEM_LOOP(k) {
-        for (int j = 0; j < N; ++j) acc[0] += (A)a[j * K + k] * (A)b[j * K + k];
-    }
-    block_partials<1>(acc, part);
-}
-
-__global__ void k_fin_alpha(KScal *sc, const double *part, int nblk) {
-    if (sc->done) return;
-    const double den = sum_partials(part, 0, nblk);
-    if (threadIdx.x == 0) {
-        sc->den = den;
-        if (!(fabs(den) > 1e-300) || !isfinite(den)) {
-            sc->breakdown = 1;
-            sc->done = 1;
-        } else {
-            sc->alpha = sc->rho / den;
-        }
-    }
-}
-
-// s = r - alpha v; sh = P^{-1} s; partial (s, s)
-template <typename T>
-__global__ void k_bicg_s(int64_t K, int N, const T *r, const T *v, T *s, T *sh, const T *inv, double *part,
-                         const KScal *sc) {
-    if (sc->done) return;
-    using A = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
-    const T alpha = (T)sc->alpha;
-    A acc[1] = {A(0)};
-    ELEM_LOOP(k) {
-        const T iv = inv ? inv[k] : T(0);
-        for (int j = 0; j < N; ++j) {
-            const int64_t i = j * K + k;
-            const T si = r[i] - alpha * v[i];
-            s[i] = si;
-            if (inv) sh[i] = si * iv;
-            acc[0] += (A)si * (A)si;
-        }
-    }
-    block_partials<1>(acc, part);
-}
-
-__global__ void k_fin_s(KScal *sc, const double *part, int nblk) {
-    if (sc->done) return;
-    const double s2 = sum_partials(part, 0, nblk);
-    if (threadIdx.x == 0 && s2 <= sc->tol2 * sc->b2) {
-        sc->sconv = 1;
-        sc->r2 = s2;
-        sc->iter += 1;
-        sc->done = 1;
-    }
-}
-
-template <typename T>
-__global__ void k_dot2(int64_t K, int N, const T *t, const T *s, double *part, const KScal *sc) {
-    if (sc->done) return;
-    using A = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
-    A acc[2] = {A(0), A(0)};
-    ELEM_LOOP(k) {
-        for (int j = 0; j < N; ++j) {
-            const A ti = (A)t[j * K + k];
-            acc[0] += ti * (A)s[j * K + k];
-            acc[1] += ti * ti;
-        }
-    }
-    block_partials<2>(acc, part);
-}
-
-__global__ void k_fin_omega(KScal *sc, const double *part, int nblk) {
-    if (sc->done) return;
-    const double ts = sum_partials(part, 0, nblk);
-    const double tt = sum_partials(part, 1, nblk);
-    if (threadIdx.x == 0) {
-        if (!(tt > 0.0) || !isfinite(ts) || ts == 0.0) {
-            sc->breakdown = 1;
-            sc->done = 1;
-        } else {
-            sc->omega = ts / tt;
-        }
-    }
-}
-
-// x += alpha ph + omega sh; r = s - omega t; partials (r0, r), (r, r)
-template <typename T>
-__global__ void k_bicg_xr(int64_t K, int N, T *x, const T *ph, const T *sh, const T *s, const T *t, T *r,
-                          const T *r0, double *part, const KScal *sc) {
-    if (sc->done) return;
-    using A = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
-    const T alpha = (T)sc->alpha, omega = (T)sc->omega;
-    A acc[2] = {A(0), A(0)};
-    ELEM_LOOP(k) {
-        for (int j = 0; j < N; ++j) {
-            const int64_t i = j * K + k;
-            x[i] += alpha * ph[i] + omega * sh[i];
-            const T ri = s[i] - omega * t[i];
-            r[i] = ri;
-            acc[0] += (A)r0[i] * (A)ri;
-            acc[1] += (A)ri * (A)ri;
-        }
-    }
-    block_partials<2>(acc, part);
-}
-
-__global__ void k_fin_iter(KScal *sc, const double *part, int nblk) {
-    if (sc->done) return;
-    const double rho_new = sum_partials(part, 0, nblk);
-    const double r2 = sum_partials(part, 1, nblk);
-    if (threadIdx.x == 0) {
-        sc->iter += 1;
-        sc->r2 = r2;
-        if (r2 <= sc->tol2 * sc->b2) {
-            sc->done = 1;
-        } else if (!(fabs(rho_new) > 1e-300) || !isfinite(rho_new)) {
-            sc->breakdown = 1;
-            sc->done = 1;
-        } else {
-            sc->beta = (rho_new / sc->rho) * (sc->alpha / sc->omega);
-            sc->rho = rho_new;
-        }
-    }
-}
-
 // x += alpha ph (used when BiCGStab converged on s)
 template <typename T>
 __global__ void k_axpy_alpha(int64_t K, int N, T *x, const T *ph, const KScal *sc) {
     const T alpha = (T)sc->alpha;
     ELEM_LOOP(k) {
         for (int j = 0; j < N; ++j) x[j * K + k] += alpha * ph[j * K + k];
-    }
-}
-
-// CG (SPD case, preconditioner M^{-1}): init z = P^{-1} r, p = z; partial (r, z)
-template <typename T>
-__global__ void k_cg_init(int64_t K, int N, const T *r, T *p, const T *inv, double *part) {
-    using A = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
-    A acc[1] = {A(0)};
-    ELEM_LOOP(k) {
-        const T iv = inv[k];
-        for (int j = 0; j < N; ++j) {
-            const int64_t i = j * K + k;
-            const T zi = r[i] * iv;
-            p[i] = zi;
-            acc[0] += (A)r[i] * (A)zi;
-        }
-    }
-    block_partials<1>(acc, part);
-}
-
-__global__ void k_fin_cg_init(KScal *sc, const double *part, int nblk) {
-    const double rz = sum_partials(part, 0, nblk);
-    if (threadIdx.x == 0) sc->rho = rz;
-}
-
-__global__ void k_fin_cg_alpha(KScal *sc, const double *part, int nblk) {
-    if (sc->done) return;
-    const double pq = sum_partials(part, 0, nblk);
-    if (threadIdx.x == 0) {
-        if (!(pq > 0.0) || !isfinite(pq)) {
-            sc->breakdown = 1;
-            sc->done = 1;
-        } else {
-            sc->alpha = sc->rho / pq;
-        }
-    }
-}
-
-// x += alpha p; r -= alpha q; z = P^{-1} r; partials (r, z), (r, r)
-template <typename T>
-__global__ void k_cg_xr(int64_t K, int N, T *x, const T *p, const T *q, T *r, T *z, const T *inv, double *part,
-                        const KScal *sc) {
-    if (sc->done) return;
-    using A = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
-    const T alpha = (T)sc->alpha;
-    A acc[2] = {A(0), A(0)};
-    ELEM_LOOP(k) {
-        const T iv = inv ? inv[k] : T(0);
-        for (int j = 0; j < N; ++j) {
-            const int64_t i = j * K + k;
-            x[i] += alpha * p[i];
-            const T ri = r[i] - alpha * q[i];
-            r[i] = ri;
-            if (inv) {
-                const T zi = ri * iv;
-                z[i] = zi;
-                acc[0] += (A)ri * (A)zi;
-            }
-            acc[1] += (A)ri * (A)ri;
-        }
-    }
-    block_partials<2>(acc, part);
-}
-
-__global__ void k_fin_cg_iter(KScal *sc, const double *part, int nblk) {
-    if (sc->done) return;
-    const double rz = sum_partials(part, 0, nblk);
-    const double r2 = sum_partials(part, 1, nblk);
-    if (threadIdx.x == 0) {
-        sc->iter += 1;
-        sc->r2 = r2;
-        if (r2 <= sc->tol2 * sc->b2) {
-            sc->done = 1;
-        } else {
-            sc->beta = rz / sc->rho;
-            sc->rho = rz;
-        }
-    }
-}
-
-template <typename T>
-__global__ void k_cg_p(int64_t K, int N, T *p, const T *z, const KScal *sc) {
-    if (sc->done) return;
-    const T beta = (T)sc->beta;
-    ELEM_LOOP(k) {
-        for (int j = 0; j < N; ++j) p[j * K + k] = z[j * K + k] + beta * p[j * K + k];
     }
 }
 
@@ -550,6 +326,9 @@ int ensure_ws(festung_ctx *c) {
         FCK(cudaMallocHost(&w.h_scal, sizeof(KScal)));
         FCK(cudaMalloc(&w.d_flags, sizeof(int) * 4));
         FCK(cudaMalloc(&w.res, sizeof(double) * 2));
+        FCK(cudaMalloc(&w.counter, sizeof(unsigned int)));
+        FCK(cudaMemset(w.counter, 0, sizeof(unsigned int)));
+        FCK(cudaMalloc(&w.part2, sizeof(double) * 4 * w.nblk));
         FCK(cudaMallocHost(&w.h_res, sizeof(double) * 2));
         FCK(cudaMallocHost(&w.h_flags, sizeof(int) * 4));
     }
@@ -575,6 +354,9 @@ void free_ctx_device(festung_ctx *c) {
         if (c->ws->scratch64) cudaFree(c->ws->scratch64);
         if (c->ws->d_flags) cudaFree(c->ws->d_flags);
         if (c->ws->P) cudaFree(c->ws->P);
+        if (c->ws->Pb) cudaFree(c->ws->Pb);
+        if (c->ws->counter) cudaFree(c->ws->counter);
+        if (c->ws->part2) cudaFree(c->ws->part2);
         if (c->ws->res) cudaFree(c->ws->res);
         if (c->ws->h_res) cudaFreeHost(c->ws->h_res);
         if (c->ws->h_flags) cudaFreeHost(c->ws->h_flags);
@@ -651,39 +433,60 @@ bool ready(festung_ctx *c) {
 // ---------------------------------------------------------------------------
 constexpr int CHUNK = 16;  // iterations per captured graph
 
+// preconditioned update kernels (templated on N)
+template <typename T>
+void launch_bicg_prec(festung_ctx *c, int mode, const T *r, T *pv, const T *v, T *out, cudaStream_t st) {
+    Workspace &w = *c->ws;
+    const __nv_bfloat16 *P = w.use_P ? w.Pb : nullptr;
+    const T *inv = vecs<T>(c).inv;
+    dispatch(c->N, c->R2, c->R1, [&](auto n_, auto, auto) {
+        constexpr int N = decltype(n_)::value;
+        if (mode == 0)
+            k_bicg_prec<T, N, 0><<<w.nblk, RED_THREADS, 0, st>>>((int)c->K, r, pv, v, out, P, inv, w.part, w.scal,
+                                                                 w.counter);
+        else
+            k_bicg_prec<T, N, 1><<<w.nblk, RED_THREADS, 0, st>>>((int)c->K, r, pv, v, out, P, inv, w.part, w.scal,
+                                                                 w.counter);
+    });
+}
+
+template <typename T>
+void launch_cg_prec(festung_ctx *c, const T *r, T *z, int init, cudaStream_t st) {
+    Workspace &w = *c->ws;
+    const __nv_bfloat16 *P = w.use_P ? w.Pb : nullptr;
+    const T *inv = vecs<T>(c).inv;
+    dispatch(c->N, c->R2, c->R1, [&](auto n_, auto, auto) {
+        constexpr int N = decltype(n_)::value;
+        k_cg_prec<T, N><<<w.nblk, RED_THREADS, 0, st>>>((int)c->K, r, z, P, inv, w.part, w.part2, w.nblk, w.scal,
+                                                        w.counter, init);
+    });
+}
+
 // record `CHUNK` iterations of the solver on stream st
 template <typename T>
 void record_iterations(festung_ctx *c, int solver, T tau, cudaStream_t st) {
     Workspace &w = *c->ws;
     Vecs<T> &V = vecs<T>(c);
-    const int64_t K = c->K;
-    const int N = c->N, g = w.nblk;
+    const int64_t n = c->K * c->N;
+    const int g = w.nblk;
     const int *skip = &w.scal->done;
-    const T *inv = w.use_P ? nullptr : V.inv;
     for (int it = 0; it < CHUNK; ++it) {
         if (solver == FESTUNG_SOLVER_BICGSTAB) {
-            k_bicg_p<T><<<g, RED_THREADS, 0, st>>>(K, N, V.r, V.p, V.v, V.ph, inv, w.scal);
-            if (w.use_P) launch_precond<T>(c, w.P, V.p, V.ph, nullptr, g, skip, st);
-            launch_apply<T>(c, V.ph, V.v, V.Z1, V.Z2, tau, skip, st);
-            k_dot1<T><<<g, RED_THREADS, 0, st>>>(K, N, V.r0, V.v, w.part, w.scal);
-            k_fin_alpha<<<1, 1024, 0, st>>>(w.scal, w.part, g);
-            k_bicg_s<T><<<g, RED_THREADS, 0, st>>>(K, N, V.r, V.v, V.s, V.sh, inv, w.part, w.scal);
-            k_fin_s<<<1, 1024, 0, st>>>(w.scal, w.part, g);
-            if (w.use_P) launch_precond<T>(c, w.P, V.s, V.sh, nullptr, g, skip, st);
-            launch_apply<T>(c, V.sh, V.t, V.Z1, V.Z2, tau, skip, st);
-            k_dot2<T><<<g, RED_THREADS, 0, st>>>(K, N, V.t, V.s, w.part, w.scal);
-            k_fin_omega<<<1, 1024, 0, st>>>(w.scal, w.part, g);
-            k_bicg_xr<T><<<g, RED_THREADS, 0, st>>>(K, N, V.x, V.ph, V.sh, V.s, V.t, V.r, V.r0, w.part, w.scal);
-            k_fin_iter<<<1, 1024, 0, st>>>(w.scal, w.part, g);
+            launch_bicg_prec<T>(c, 0, V.r, V.p, V.v, V.ph, st);                 // p, ph = P^{-1} p
+            launch_apply<T>(c, V.ph, V.v, V.Z1, V.Z2, tau, skip, st);           // v = S ph
+            k_bicg_alpha<T><<<g, RED_THREADS, 0, st>>>(n, V.r0, V.v, w.part, w.scal, w.counter);
+            launch_bicg_prec<T>(c, 1, V.r, V.s, V.v, V.sh, st);                 // s, sh = P^{-1} s
+            launch_apply<T>(c, V.sh, V.t, V.Z1, V.Z2, tau, skip, st);           // t = S sh
+            k_bicg_omega<T><<<g, RED_THREADS, 0, st>>>(n, V.t, V.s, w.part, w.scal, w.counter);
+            k_bicg_xr<T><<<g, RED_THREADS, 0, st>>>(n, V.x, V.ph, V.sh, V.s, V.t, V.r, V.r0, w.part, w.scal,
+                                                    w.counter);
         } else {
             // CG: p (search), v = S p, s = z
             launch_apply<T>(c, V.p, V.v, V.Z1, V.Z2, tau, skip, st);
-            k_dot1<T><<<g, RED_THREADS, 0, st>>>(K, N, V.p, V.v, w.part, w.scal);
-            k_fin_cg_alpha<<<1, 1024, 0, st>>>(w.scal, w.part, g);
-            k_cg_xr<T><<<g, RED_THREADS, 0, st>>>(K, N, V.x, V.p, V.v, V.r, V.s, inv, w.part, w.scal);
-            if (w.use_P) launch_precond<T>(c, w.P, V.r, V.s, w.part, g, skip, st);
-            k_fin_cg_iter<<<1, 1024, 0, st>>>(w.scal, w.part, g);
-            k_cg_p<T><<<g, RED_THREADS, 0, st>>>(K, N, V.p, V.s, w.scal);
+            k_cg_alpha<T><<<g, RED_THREADS, 0, st>>>(n, V.p, V.v, w.part, w.scal, w.counter);
+            k_cg_xr<T><<<g, RED_THREADS, 0, st>>>(n, V.x, V.p, V.v, V.r, w.part2, w.scal);
+            launch_cg_prec<T>(c, V.r, V.s, 0, st);
+            k_cg_p<T><<<g, RED_THREADS, 0, st>>>(n, V.p, V.s, w.scal, 0);
         }
     }
 }
@@ -717,13 +520,9 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
         }
         k_fin_init<<<1, 1024, 0, st>>>(w.scal, w.part, g, tol); ++c->launches;
         if (solver == FESTUNG_SOLVER_CG) {
-            if (w.use_P) {
-                launch_precond<T>(c, w.P, V.r, V.p, w.part, g, nullptr, st);
-            } else {
-                k_cg_init<T><<<g, RED_THREADS, 0, st>>>(K, N, V.r, V.p, V.inv, w.part);
-                ++c->launches;
-            }
-            k_fin_cg_init<<<1, 1024, 0, st>>>(w.scal, w.part, g); ++c->launches;
+            launch_cg_prec<T>(c, V.r, V.s, 1, st);                    // z = P^{-1} r, rho = (r, z)
+            k_cg_p<T><<<g, RED_THREADS, 0, st>>>(K * N, V.p, V.s, w.scal, 1);  // p = z
+            c->launches += 2;
         }
         FCK(cudaGetLastError());
         // capture (or reuse) a graph of CHUNK iterations
@@ -1173,8 +972,9 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
     FCK(cudaGetLastError());
     // block-Jacobi preconditioner: inverse diagonal blocks of S for this D and dt
     if (!w.P) FCK(cudaMalloc(&w.P, (size_t)c->N * c->N * c->K * sizeof(float)));
+    if (!w.Pb) FCK(cudaMalloc(&w.Pb, (size_t)c->N * c->N * c->K * sizeof(__nv_bfloat16)));
     FCK(cudaMemsetAsync(w.d_flags, 0, sizeof(int), st));
-    launch_blockjacobi(c, w.P, dt, w.d_flags, st);
+    launch_blockjacobi(c, w.P, w.Pb, dt, w.d_flags, st);
     FCK(cudaGetLastError());
     // initial guess: linear extrapolation in time from the two previous states when the
     // previous step exists, else C^n (the result does not depend on it beyond the tolerance)

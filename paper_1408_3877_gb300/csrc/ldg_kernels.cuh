@@ -15,6 +15,8 @@
 
 #include <cstdint>
 
+#include <cuda_bf16.h>
+
 #include <type_traits>
 
 #include "internal.h"
@@ -479,10 +481,13 @@ __global__ void __launch_bounds__(128) k_blockdiag(float *__restrict__ P, const 
     }
 }
 
-// In-place inverse of every N x N block of P (layout [(i N + j) K + k]) by Gauss-Jordan
-// elimination with partial pivoting in FP64.  flags |= 1 if a block is singular.
+// Inverse of every N x N block of P (layout [(i N + j) K + k]) by Gauss-Jordan
+// elimination with partial pivoting in FP64, stored in BF16 in Pinv (the preconditioner
+// only steers convergence; its rounding does not enter the solution).  flags |= 1 if a
+// block is singular.
 template <int N>
-__global__ void __launch_bounds__(128) k_blockinv(float *__restrict__ P, int64_t K, int *__restrict__ flags) {
+__global__ void __launch_bounds__(128) k_blockinv(const float *__restrict__ P, __nv_bfloat16 *__restrict__ Pinv,
+                                                  int64_t K, int *__restrict__ flags) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
          k += (int64_t)gridDim.x * blockDim.x) {
         double A[N][N], X[N][N];
@@ -533,33 +538,8 @@ __global__ void __launch_bounds__(128) k_blockinv(float *__restrict__ P, int64_t
             continue;
         }
         for (int i = 0; i < N; ++i)
-            for (int j = 0; j < N; ++j) P[(int64_t)(i * N + j) * K + k] = (float)X[i][j];
+            for (int j = 0; j < N; ++j) Pinv[(int64_t)(i * N + j) * K + k] = __float2bfloat16((float)X[i][j]);
     }
-}
-
-// y_k = P_k x_k for every triangle (block-Jacobi preconditioner); optionally the
-// partial dot product (r, y) with r = x.
-template <typename T, int N>
-__global__ void __launch_bounds__(256) k_precond(const float *__restrict__ P, const T *__restrict__ X,
-                                                 T *__restrict__ Y, int64_t K, double *part, const int *skip) {
-    if (skip && *skip) return;
-    using A = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
-    A acc[1] = {A(0)};
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        T x[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) x[j] = X[j * K + k];
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-            T y = T(0);
-#pragma unroll
-            for (int j = 0; j < N; ++j) y += (T)P[(int64_t)(i * N + j) * K + k] * x[j];
-            Y[i * K + k] = y;
-            if (part) acc[0] += (A)y * (A)x[i];
-        }
-    }
-    if (part) block_partials<1>(acc, part);
 }
 
 }  // namespace festung

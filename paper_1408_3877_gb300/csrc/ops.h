@@ -1,6 +1,7 @@
 // Launchers of the operator kernels (defined in apply_f64.cu / apply_f32.cu).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -31,15 +32,11 @@ int elem_grid(const festung_ctx *c);
 cudaError_t upload_tables_f64(const festung_ctx *c);
 cudaError_t upload_tables_f32(const festung_ctx *c);
 
-// Block-Jacobi preconditioner: P <- inverse of the N x N diagonal blocks of S (E1),
-// built in FP32 from the FP32 copies of geometry, tables and D; layout [(i N + j) K + k].
-// flags (device int) gets bit 0 set if a block is singular.
-void launch_blockjacobi(const festung_ctx *c, float *P, double tau, int *flags, cudaStream_t st);
-
-// y_k = P_k x_k on every triangle; if part != nullptr also the partials of (x, y)
-// (grid nblk x RED_THREADS).  skip: optional device flag (graph early exit).
-template <typename T>
-void launch_precond(const festung_ctx *c, const float *P, const T *x, T *y, double *part, int nblk,
-                    const int *skip, cudaStream_t st);
+// Block-Jacobi preconditioner: Pinv <- inverse of the N x N diagonal blocks of S (E1),
+// built in FP32 (scratch P) from the FP32 copies of geometry, tables and D, inverted in
+// FP64 and stored in BF16; layout [(i N + j) K + k].  flags (device int) gets bit 0 set
+// if a block is singular.
+void launch_blockjacobi(const festung_ctx *c, float *P, __nv_bfloat16 *Pinv, double tau, int *flags,
+                        cudaStream_t st);
 
 }  // namespace festung
