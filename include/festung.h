@@ -168,9 +168,9 @@ int festung_apply_noalloc(festung_ctx *ctx, const void *x, void *y, int prec, do
 
 /* One implicit-Euler step of size dt (Sec. 2.5): forms b of (E2) from the current
  * C, D, f and boundary data, solves (E1) and, only on success, replaces C by C^{n+1}.
- * The initial guess is C^n + dt/dt_prev (C^n - C^{n-1}) after a successful step of
- * size dt_prev (linear extrapolation in time), else C^n; festung_set_state and
- * festung_setup reset this history.  Preconditioner: inverse N x N diagonal blocks of S.  opts may be NULL (tol 1e-10, max_iter 20000,
+ * The initial guess extrapolates the previous states in time: quadratically through
+ * C^{n-2}, C^{n-1}, C^n after two successful steps, linearly after one, else C^n;
+ * festung_set_state and festung_setup reset this history.  Preconditioner: inverse N x N diagonal blocks of S.  opts may be NULL (tol 1e-10, max_iter 20000,
  * FESTUNG_MIXED, inner_tol 1e-2, max_outer 50).  info may be NULL.  Synchronises
  * the context's stream.  Errors: ENOCONV (C unchanged), EINVAL, ESTATE, ECUDA. */
 int festung_step(festung_ctx *ctx, double dt, const festung_step_opts *opts,

@@ -272,6 +272,13 @@ __global__ void k_commit_coeff(int64_t n, const double *src, double *d, float *f
     }
 }
 
+// x = l0 C + l1 C_prev + l2 C_prev2
+__global__ void k_extrapolate3(int64_t n, const double *C, const double *Cp, const double *Cpp, double *x, double l0,
+                               double l1, double l2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = l0 * C[i] + l1 * Cp[i] + l2 * Cpp[i];
+}
+
 // x = C + a (C - C_prev)
 __global__ void k_extrapolate(int64_t n, const double *C, const double *Cp, double *x, double a) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -363,13 +370,13 @@ void free_ctx_device(festung_ctx *c) {
         delete c->ws;
         c->ws = nullptr;
     }
-    void *ptrs[] = {c->dTab, c->fTab, c->dC, c->dD, c->dF, c->fD, c->dCD, c->dGN, c->dSamp, c->dCprev};
+    void *ptrs[] = {c->dTab, c->fTab, c->dC, c->dD, c->dF, c->fD, c->dCD, c->dGN, c->dSamp, c->dCprev, c->dCprev2};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     c->dTab = nullptr;
     c->fTab = nullptr;
-    c->dC = c->dD = c->dF = c->dCD = c->dGN = c->dSamp = c->dCprev = nullptr;
-    c->hist_valid = false;
+    c->dC = c->dD = c->dF = c->dCD = c->dGN = c->dSamp = c->dCprev = c->dCprev2 = nullptr;
+    c->hist = 0;
     c->fD = nullptr;
 }
 
@@ -893,7 +900,7 @@ int festung_set_state(festung_ctx *c, const double *C, int is_samples, int loc) 
         k_to_internal<<<small_grid(KN, c), 256, 0, c->stream>>>(tmp, c->dC, c->K, c->N, c->dPerm); ++c->launches;
         FCK(cudaGetLastError());
     }
-    c->hist_valid = false;
+    c->hist = 0;
     FCK(cudaStreamSynchronize(c->stream));
     return FESTUNG_OK;
 }
@@ -978,7 +985,16 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
     FCK(cudaGetLastError());
     // initial guess: linear extrapolation in time from the two previous states when the
     // previous step exists, else C^n (the result does not depend on it beyond the tolerance)
-    if (c->hist_valid && c->dt_prev > 0.0) {
+    if (c->hist >= 2 && c->dt_prev > 0.0 && c->dt_prev2 > 0.0) {
+        // quadratic Lagrange extrapolation through t_{n-2}, t_{n-1}, t_n to t_{n+1}
+        const double h0 = c->dt_prev2, h1 = c->dt_prev, h = dt;  // t_n - t_{n-1} = h1, t_{n-1} - t_{n-2} = h0
+        const double tn = 0.0, tm1 = -h1, tm2 = -h1 - h0, tp = h;
+        const double l0 = (tp - tm1) * (tp - tm2) / ((tn - tm1) * (tn - tm2));
+        const double l1 = (tp - tn) * (tp - tm2) / ((tm1 - tn) * (tm1 - tm2));
+        const double l2 = (tp - tn) * (tp - tm1) / ((tm2 - tn) * (tm2 - tm1));
+        k_extrapolate3<<<small_grid(KN, c), 256, 0, st>>>(KN, c->dC, c->dCprev, c->dCprev2, V.x, l0, l1, l2);
+        ++c->launches;
+    } else if (c->hist >= 1 && c->dt_prev > 0.0) {
         k_extrapolate<<<small_grid(KN, c), 256, 0, st>>>(KN, c->dC, c->dCprev, V.x, dt / c->dt_prev); ++c->launches;
     } else {
         FCK(cudaMemcpyAsync(V.x, c->dC, KN * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1077,10 +1093,13 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
         return FESTUNG_ENOCONV;
     }
     if (!c->dCprev) FCK(cudaMalloc(&c->dCprev, KN * sizeof(double)));
+    if (!c->dCprev2) FCK(cudaMalloc(&c->dCprev2, KN * sizeof(double)));
+    std::swap(c->dCprev, c->dCprev2);  // C^{n-2} <- C^{n-1}
     FCK(cudaMemcpyAsync(c->dCprev, c->dC, KN * sizeof(double), cudaMemcpyDeviceToDevice, st));
     FCK(cudaMemcpyAsync(c->dC, V.x, KN * sizeof(double), cudaMemcpyDeviceToDevice, st));
     FCK(cudaStreamSynchronize(st));
-    c->hist_valid = true;
+    c->hist = std::min(c->hist + 1, 2);
+    c->dt_prev2 = c->dt_prev;
     c->dt_prev = dt;
     return FESTUNG_OK;
 }

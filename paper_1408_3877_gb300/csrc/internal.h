@@ -110,9 +110,9 @@ struct festung_ctx {
     float *fTab = nullptr;   // FP32 copy
     // state and data (N x K unless noted)
     double *dC = nullptr, *dD = nullptr, *dF = nullptr;
-    double *dCprev = nullptr;  // C^{n-1} for the extrapolated initial guess
-    bool hist_valid = false;
-    double dt_prev = 0.0;
+    double *dCprev = nullptr, *dCprev2 = nullptr;  // C^{n-1}, C^{n-2} for the extrapolated initial guess
+    int hist = 0;                                  // number of valid previous states (0..2)
+    double dt_prev = 0.0, dt_prev2 = 0.0;
     float *fD = nullptr;
     double *dCD = nullptr, *dGN = nullptr;  // K x 3 x R1 boundary samples
     double *dSamp = nullptr;                // K x R2 staging for projections
