@@ -979,7 +979,7 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
     FCK(cudaGetLastError());
     // block-Jacobi preconditioner: inverse diagonal blocks of S for this D and dt
     if (!w.P) FCK(cudaMalloc(&w.P, (size_t)c->N * c->N * c->K * sizeof(float)));
-    if (!w.Pb) FCK(cudaMalloc(&w.Pb, (size_t)c->N * c->N * c->K * sizeof(__nv_bfloat16)));
+    if (!w.Pb) FCK(cudaMalloc(&w.Pb, (size_t)((c->N * c->N + 7) / 8) * c->K * 16));
     FCK(cudaMemsetAsync(w.d_flags, 0, sizeof(int), st));
     launch_blockjacobi(c, w.P, w.Pb, dt, w.d_flags, st);
     FCK(cudaGetLastError());
@@ -1054,7 +1054,9 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
             int it = 0;
             bool cin = false;
             double ir2, ib2;
-            rc = krylov_solve<float>(c, solver, dt, o.inner_tol, o.max_iter - iters, true, &it, &ir2, &ib2, &cin);
+            // the FP32 sweep reduces by inner_tol, or by less when less is still needed
+            const double target = std::min(0.5, std::max(o.inner_tol, 0.5 * o.tol / relres));
+            rc = krylov_solve<float>(c, solver, dt, target, o.max_iter - iters, true, &it, &ir2, &ib2, &cin);
             if (rc) return rc;
             iters += it;
             last_scale = rn;

@@ -19,6 +19,25 @@ namespace festung {
 template <typename T>
 using Acc = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
 
+// y = P_k q for the BF16 block of triangle k (layout of k_blockinv: 16-byte chunks [q][K])
+template <typename T, int N>
+__device__ __forceinline__ void block_matvec(const __nv_bfloat16 *__restrict__ P, int K, int k, const T (&q)[N],
+                                             T (&y)[N]) {
+    constexpr int NQ = (N * N + 7) / 8;
+#pragma unroll
+    for (int i = 0; i < N; ++i) y[i] = T(0);
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) {
+        const uint4 raw = __ldg(reinterpret_cast<const uint4 *>(P) + (int64_t)c * K + k);
+        const __nv_bfloat16 *b = reinterpret_cast<const __nv_bfloat16 *>(&raw);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int e = 8 * c + t;
+            if (e < N * N) y[e / N] += (T)__bfloat162float(b[t]) * q[e % N];
+        }
+    }
+}
+
 // Called by every thread of a block after its partials are written.  True in exactly
 // one block, the last one, which then sees all partials.
 __device__ __forceinline__ bool last_block(unsigned int *counter) {
@@ -118,13 +137,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_bicg_prec(int K, const T *__res
             if (MODE == 1) acc[0] += (Acc<T>)qi * (Acc<T>)qi;
         }
         if (P) {
+            T y[N];
+            block_matvec<T, N>(P, K, k, q, y);
 #pragma unroll
-            for (int i = 0; i < N; ++i) {
-                T y = T(0);
-#pragma unroll
-                for (int j = 0; j < N; ++j) y += (T)__bfloat162float(P[(int64_t)(i * N + j) * K + k]) * q[j];
-                out[i * K + k] = y;
-            }
+            for (int i = 0; i < N; ++i) out[i * K + k] = y[i];
         } else {
             const T iv = inv[k];
 #pragma unroll
@@ -158,7 +174,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_bicg_alpha(int64_t n, const T *
     FLAT_LOOP(n, {
         if (w > 1) {
             const V16<T> a = ld16(r0, i0), b = ld16(v, i0);
-#pragma unroll
             for (int e = 0; e < w; ++e) acc[0] += (Acc<T>)a.v[e] * (Acc<T>)b.v[e];
         } else {
             acc[0] += (Acc<T>)r0[i0] * (Acc<T>)v[i0];
@@ -189,7 +204,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_bicg_omega(int64_t n, const T *
     FLAT_LOOP(n, {
         if (w > 1) {
             const V16<T> a = ld16(t, i0), b = ld16(s, i0);
-#pragma unroll
             for (int e = 0; e < w; ++e) {
                 acc[0] += (Acc<T>)a.v[e] * (Acc<T>)b.v[e];
                 acc[1] += (Acc<T>)a.v[e] * (Acc<T>)a.v[e];
@@ -231,7 +245,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_bicg_xr(int64_t n, T *__restric
             const V16<T> pa = ld16(ph, i0), sa = ld16(sh, i0), sv = ld16(s, i0), tv = ld16(t, i0),
                          rz = ld16(r0, i0);
             V16<T> rv;
-#pragma unroll
             for (int e = 0; e < w; ++e) {
                 xv.v[e] += alpha * pa.v[e] + omega * sa.v[e];
                 rv.v[e] = sv.v[e] - omega * tv.v[e];
@@ -283,7 +296,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_cg_alpha(int64_t n, const T *__
     FLAT_LOOP(n, {
         if (w > 1) {
             const V16<T> a = ld16(p, i0), b = ld16(q, i0);
-#pragma unroll
             for (int e = 0; e < w; ++e) acc[0] += (Acc<T>)a.v[e] * (Acc<T>)b.v[e];
         } else {
             acc[0] += (Acc<T>)p[i0] * (Acc<T>)q[i0];
@@ -316,7 +328,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_cg_xr(int64_t n, T *__restrict_
         if (w > 1) {
             V16<T> xv = ld16(x, i0), rv = ld16(r, i0);
             const V16<T> pv = ld16(p, i0), qv = ld16(q, i0);
-#pragma unroll
             for (int e = 0; e < w; ++e) {
                 xv.v[e] += alpha * pv.v[e];
                 rv.v[e] -= alpha * qv.v[e];
@@ -348,18 +359,17 @@ __global__ void __launch_bounds__(RED_THREADS) k_cg_prec(int K, const T *__restr
         T q[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) q[j] = r[j * K + k];
+        T y[N];
+        if (P) {
+            block_matvec<T, N>(P, K, k, q, y);
+        } else {
+#pragma unroll
+            for (int i = 0; i < N; ++i) y[i] = q[i] * inv[k];
+        }
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            T y;
-            if (P) {
-                y = T(0);
-#pragma unroll
-                for (int j = 0; j < N; ++j) y += (T)__bfloat162float(P[(int64_t)(i * N + j) * K + k]) * q[j];
-            } else {
-                y = q[i] * inv[k];
-            }
-            z[i * K + k] = y;
-            acc[0] += (Acc<T>)y * (Acc<T>)q[i];
+            z[i * K + k] = y[i];
+            acc[0] += (Acc<T>)y[i] * (Acc<T>)q[i];
         }
     }
     block_partials<1>(acc, part);
@@ -394,7 +404,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_cg_p(int64_t n, T *__restrict__
         if (w > 1) {
             V16<T> pv = ld16(p, i0);
             const V16<T> zv = ld16(z, i0);
-#pragma unroll
             for (int e = 0; e < w; ++e) pv.v[e] = init ? zv.v[e] : zv.v[e] + beta * pv.v[e];
             st16(p, i0, pv);
         } else {

@@ -481,64 +481,86 @@ __global__ void __launch_bounds__(128) k_blockdiag(float *__restrict__ P, const 
     }
 }
 
-// Inverse of every N x N block of P (layout [(i N + j) K + k]) by Gauss-Jordan
-// elimination with partial pivoting in FP64, stored in BF16 in Pinv (the preconditioner
-// only steers convergence; its rounding does not enter the solution).  flags |= 1 if a
+// Inverse of every N x N block of P (layout [(i N + j) K + k]), one warp per block:
+// lane l < 2N holds column l of the augmented matrix [A | I] in registers, and
+// Gauss-Jordan elimination with partial pivoting runs in FP32 with the pivot column
+// broadcast by warp shuffles (the preconditioner only steers convergence; its rounding
+// does not enter the solution).  The inverse is stored in BF16 in Pinv as
+// ceil(N^2 / 8) chunks of 16 bytes per triangle, chunk-major ([q][K]), so that a warp
+// reads its 32 triangles' chunk q with one coalesced 512-byte access.  flags |= 1 if a
 // block is singular.
 template <int N>
 __global__ void __launch_bounds__(128) k_blockinv(const float *__restrict__ P, __nv_bfloat16 *__restrict__ Pinv,
                                                   int64_t K, int *__restrict__ flags) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        double A[N][N], X[N][N];
-        for (int i = 0; i < N; ++i)
-            for (int j = 0; j < N; ++j) {
-                A[i][j] = (double)P[(int64_t)(i * N + j) * K + k];
-                X[i][j] = (i == j) ? 1.0 : 0.0;
-            }
+    static_assert(2 * N <= 32, "one warp holds [A | I]");
+    constexpr int NQ = (N * N + 7) / 8;
+    __shared__ float stage[4][N * N + 1];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; k < K; k += nwarps) {
+        float col[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            if (lane < N)
+                col[i] = P[(int64_t)(i * N + lane) * K + k];
+            else
+                col[i] = (lane - N == i) ? 1.0f : 0.0f;
+        }
         bool bad = false;
+#pragma unroll
         for (int c = 0; c < N; ++c) {
-            int piv = c;
-            double best = fabs(A[c][c]);
+            // pivot row: largest |A[i][c]|, i >= c, found by lane c
+            int prow = c;
+            float best = fabsf(col[c]);
+#pragma unroll
             for (int i = c + 1; i < N; ++i)
-                if (fabs(A[i][c]) > best) {
-                    best = fabs(A[i][c]);
-                    piv = i;
+                if (fabsf(col[i]) > best) {
+                    best = fabsf(col[i]);
+                    prow = i;
                 }
-            if (!(best > 0.0)) {
+            prow = __shfl_sync(0xffffffffu, prow, c);
+            best = __shfl_sync(0xffffffffu, best, c);
+            if (!(best > 0.0f)) {
                 bad = true;
                 break;
             }
-            if (piv != c)
-                for (int j = 0; j < N; ++j) {
-                    double t = A[c][j];
-                    A[c][j] = A[piv][j];
-                    A[piv][j] = t;
-                    t = X[c][j];
-                    X[c][j] = X[piv][j];
-                    X[piv][j] = t;
+#pragma unroll
+            for (int i = c + 1; i < N; ++i)
+                if (i == prow) {
+                    const float t = col[c];
+                    col[c] = col[i];
+                    col[i] = t;
                 }
-            const double ip = 1.0 / A[c][c];
-            for (int j = 0; j < N; ++j) {
-                A[c][j] *= ip;
-                X[c][j] *= ip;
-            }
+            const float ip = 1.0f / __shfl_sync(0xffffffffu, col[c], c);
+            col[c] *= ip;
+#pragma unroll
             for (int i = 0; i < N; ++i) {
                 if (i == c) continue;
-                const double f = A[i][c];
-                if (f == 0.0) continue;
-                for (int j = 0; j < N; ++j) {
-                    A[i][j] -= f * A[c][j];
-                    X[i][j] -= f * X[c][j];
-                }
+                const float f = __shfl_sync(0xffffffffu, col[i], c);
+                col[i] -= f * col[c];
             }
         }
         if (bad) {
-            atomicOr(flags, 1);
+            if (lane == 0) atomicOr(flags, 1);
             continue;
         }
-        for (int i = 0; i < N; ++i)
-            for (int j = 0; j < N; ++j) Pinv[(int64_t)(i * N + j) * K + k] = __float2bfloat16((float)X[i][j]);
+        // lanes N..2N-1 hold the columns of the inverse; stage row-major, write chunks
+        __syncwarp();
+        if (lane >= N && lane < 2 * N) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) stage[wib][i * N + (lane - N)] = col[i];
+        }
+        __syncwarp();
+        if (lane < NQ) {
+            __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int e = 8 * lane + t;
+                v[t] = __float2bfloat16(e < N * N ? stage[wib][e] : 0.0f);
+            }
+            reinterpret_cast<uint4 *>(Pinv)[(int64_t)lane * K + k] = *reinterpret_cast<const uint4 *>(v);
+        }
+        __syncwarp();
     }
 }
 
