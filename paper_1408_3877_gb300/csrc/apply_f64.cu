@@ -35,7 +35,7 @@ void launch_rhs(const festung_ctx *c, double *W1, double *W2, double *b, double 
                                                                   c->dPerm);
         k_apply<double, N, R2, R1, MODE_RHS><<<grid, 256, 0, st>>>(c->dC, W1, W2, c->dD, b, c->dB, c->dNbr, c->K,
                                                                    tau, c->eta, c->dTab, c->dF, c->dCD, c->dGN,
-                                                                   c->dPerm, nullptr);
+                                                                   c->dPerm, c->dLift, nullptr);
     });
 }
 
@@ -49,7 +49,7 @@ void launch_apply_twopass<double>(const festung_ctx *c, const double *x, double 
         k_flux<double, N, R2, R1><<<grid, 256, 0, st>>>(x, Z1, Z2, c->dB, c->dNbr, c->K, c->dTab, skip);
         k_apply<double, N, R2, R1, MODE_APPLY><<<grid, 256, 0, st>>>(x, Z1, Z2, c->dD, y, c->dB, c->dNbr, c->K, tau,
                                                                   (double)c->eta, c->dTab, nullptr, nullptr, nullptr,
-                                                                  nullptr, skip);
+                                                                  nullptr, nullptr, skip);
     });
 }
 

@@ -674,6 +674,7 @@ int festung_mesh_create(const double *coordV, int64_t numV, const int32_t *V0T, 
         return fail(e);
     if ((e = cudaMalloc(&c->dHaloSlot, std::max<size_t>(1, hslot16.size()) * sizeof(int16_t))) != cudaSuccess)
         return fail(e);
+    if ((e = cudaMalloc(&c->dLift, K * sizeof(uint8_t))) != cudaSuccess) return fail(e);
     const struct {
         void *dst;
         const void *src;
@@ -685,7 +686,8 @@ int festung_mesh_create(const double *coordV, int64_t numV, const int32_t *V0T, 
               {c->dSlot, slot16.data(), 3 * K * sizeof(int16_t)},
               {c->dHaloPtr, mo.halo_ptr.data(), (T + 1) * sizeof(int32_t)},
               {c->dHalo, mo.halo.data(), mo.halo.size() * sizeof(int32_t)},
-              {c->dHaloSlot, hslot16.data(), hslot16.size() * sizeof(int16_t)}};
+              {c->dHaloSlot, hslot16.data(), hslot16.size() * sizeof(int16_t)},
+              {c->dLift, mo.lift.data(), K * sizeof(uint8_t)}};
     for (const auto &u : up)
         if (u.bytes && (e = cudaMemcpy(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
     *out = c;
@@ -1161,7 +1163,7 @@ void festung_destroy(festung_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_ctx_device(c);
-    void *mesh_ptrs[] = {c->dB, c->fB, c->dNbr, c->dPerm, c->dSlot, c->dHaloPtr, c->dHalo, c->dHaloSlot};
+    void *mesh_ptrs[] = {c->dB, c->fB, c->dNbr, c->dPerm, c->dSlot, c->dHaloPtr, c->dHalo, c->dHaloSlot, c->dLift};
     for (void *q : mesh_ptrs)
         if (q) cudaFree(q);
     delete c;

@@ -63,6 +63,7 @@ struct MeshOrder {
     std::vector<int32_t> halo;      // internal indices
     std::vector<int32_t> slot;      // 3 x K: shared-memory slot of the neighbour across edge n (-1: boundary)
     std::vector<int32_t> halo_slot; // 3 per halo entry: slot of its neighbour, -1 boundary, -2 not resident
+    std::vector<uint8_t> lift;      // K: bit 1 set if the Dirichlet lift reaches the triangle's right-hand side
 };
 void order_and_tile(const double *coordV, const int32_t *V0T, int64_t K, const std::vector<double> &B_usr,
                     const std::vector<int32_t> &nbr_usr, int TE, MeshOrder &o);
@@ -97,6 +98,7 @@ struct festung_ctx {
     int32_t *dHaloPtr = nullptr, *dHalo = nullptr;
     int16_t *dSlot = nullptr;   // 3 x K
     int16_t *dHaloSlot = nullptr;  // 3 per halo entry
+    uint8_t *dLift = nullptr;      // K, see MeshOrder::lift
     bool has_dirichlet = false, has_neumann = false;
     // device mesh
     double *dB = nullptr;

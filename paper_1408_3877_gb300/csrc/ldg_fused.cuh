@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_apply_fused(
     {
         const int o_phiE = 4 * R2 * N + 2 * N * N;  // table layout of table_offsets()
         for (int j = threadIdx.x; j < 3 * R1 * N; j += blockDim.x) phiE_s[j] = tabg[o_phiE + j];
-        if (kBigVolume) {
+        if constexpr (kBigVolume) {
             const int o_phiQ = 0, o_gw1 = 2 * R2 * N, o_gw2 = 3 * R2 * N;
             for (int j = threadIdx.x; j < R2 * NP; j += blockDim.x) {
                 const int r = j / NP, c = j - r * NP;
@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_apply_fused(
     T acc[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) acc[j] = T(0);
-    if (kBigVolume)
+    if constexpr (kBigVolume)
         volume_smem<T, N, R2, NP>(vol_s, vol_s + R2 * NP, vol_s + 2 * R2 * NP, d, z1, z2, b11, b12, b21, b22, acc);
     else
         volume_const<T, N, R2, R1>(d, z1, z2, b11, b12, b21, b22, acc);

@@ -188,7 +188,8 @@ __global__ void __launch_bounds__(256) k_apply(const T *__restrict__ X, const T 
                                                const int32_t *__restrict__ nbr, int64_t K, T tau, T eta,
                                                const T *__restrict__ tabg, const T *__restrict__ F,
                                                const T *__restrict__ cD, const T *__restrict__ gN,
-                                               const int32_t *__restrict__ perm, const int *__restrict__ skip) {
+                                               const int32_t *__restrict__ perm, const uint8_t *__restrict__ lift,
+                                               const int *__restrict__ skip) {
     __shared__ SmemTab<T, N, R2, R1> s;
     if (skip && *skip) return;
     load_tables(s, tabg);
@@ -205,9 +206,12 @@ __global__ void __launch_bounds__(256) k_apply(const T *__restrict__ X, const T 
             acc[j] = T(0);
         }
         const T b11 = Bg[k], b12 = Bg[K + k], b21 = Bg[2 * K + k], b22 = Bg[3 * K + k];
+        // right-hand side: Z = M^{-1} J_D vanishes on this triangle and its neighbours
+        // unless the Dirichlet lift reaches it; then only the Neumann data remain
+        const bool aterms = (MODE == MODE_APPLY) || (lift[k] & 2);
         // volume term -sum_m G^m Z^m
 #pragma unroll 1
-        for (int r = 0; r < R2; ++r) {
+        for (int r = 0; r < (aterms ? R2 : 0); ++r) {
             T dv = T(0), w1 = T(0), w2 = T(0);
 #pragma unroll
             for (int j = 0; j < N; ++j) {
@@ -226,6 +230,7 @@ __global__ void __launch_bounds__(256) k_apply(const T *__restrict__ X, const T 
         for (int n = 0; n < 3; ++n) {
             const int code = nbr[n * K + k];
             if (MODE == MODE_APPLY && code == NBR_NEUMANN) continue;
+            if (!aterms && code != NBR_NEUMANN) continue;
             T nx, ny;
             edge_normal(n, b11, b12, b21, b22, nx, ny);
             T dm[R1], g[R1];

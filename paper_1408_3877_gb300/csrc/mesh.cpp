@@ -166,6 +166,17 @@ void order_and_tile(const double *coordV, const int32_t *V0T, int64_t K, const s
             o.nbr[n * K + i] = code >= 0 ? (int32_t)((int64_t(o.inv[code >> 2]) << 2) | (code & 3)) : code;
         }
     }
+    // triangles whose right-hand side sees the Dirichlet lift: bit 0 = has a Dirichlet
+    // edge, bit 1 = it or an interior neighbour has one
+    o.lift.assign(K, 0);
+    for (int64_t i = 0; i < K; ++i)
+        for (int n = 0; n < 3; ++n)
+            if (o.nbr[n * K + i] == -1) o.lift[i] |= 3;
+    for (int64_t i = 0; i < K; ++i)
+        for (int n = 0; n < 3; ++n) {
+            const int32_t code = o.nbr[n * K + i];
+            if (code >= 0 && (o.lift[code >> 2] & 1)) o.lift[i] |= 2;
+        }
     // tiles of TE consecutive triangles; halo = interior neighbours outside the tile
     o.TE = TE;
     const int64_t T = (K + TE - 1) / TE;
