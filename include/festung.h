@@ -176,6 +176,14 @@ int festung_apply_noalloc(festung_ctx *ctx, const void *x, void *y, int prec, do
 int festung_step(festung_ctx *ctx, double dt, const festung_step_opts *opts,
                  festung_step_info *info);
 
+/* The stationary problem of Sec. 3.9 (the code-verification setting): solves
+ *   (eta (S + S_D) - sum_m A_m M^{-1} B_m) C = eta K_D - K_N + L + sum_m A_m M^{-1} J_D^m
+ * with the current D, f and boundary data, starting from the current C, and replaces C
+ * on success.  Options and info as festung_step (info->rel_residual relative to the
+ * right-hand side).  Needs at least one Dirichlet edge (EINVAL otherwise: with
+ * zero-flux data alone the operator is singular).  Resets the time extrapolation. */
+int festung_solve_stationary(festung_ctx *ctx, const festung_step_opts *opts, festung_step_info *info);
+
 /* Discretisation error ||c_h - c||_{L2} (Sec. 3.5) from samples of the exact c at
  * the triangle points (K x R2, host). */
 int festung_l2_error(const festung_ctx *ctx, const double *c_samples, double *err);

@@ -23,7 +23,7 @@ void launch_apply<float>(const festung_ctx *c, const float *x, float *y, float *
             configured = smem;
         }
         k_apply_fused<float, N, R2, R1><<<tiles, FUSED_THREADS, smem, st>>>(x, y, c->fD, c->fB, c->dNbr, c->dSlot, c->dHaloPtr,
-                                                                c->dHalo, c->dHaloSlot, c->K, c->TE, c->nslot, tau, (float)c->eta,
+                                                                c->dHalo, c->dHaloSlot, c->K, c->TE, c->nslot, tau, (float)c->eta, (float)c->mass,
                                                                 c->fTab, skip);
     });
 }
@@ -36,7 +36,7 @@ void launch_blockjacobi(const festung_ctx *c, float *P, __nv_bfloat16 *Pinv, dou
     dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
         constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
         k_blockdiag<float, N, R2, R1><<<grid, 128, 0, st>>>(P, c->fB, c->dNbr, c->fD, c->K, (float)tau,
-                                                            (float)c->eta, c->fTab);
+                                                            (float)c->eta, (float)c->mass, c->fTab);
         k_blockinv<N><<<grid, 128, 0, st>>>(P, Pinv, c->K, flags);
     });
 }
@@ -50,7 +50,7 @@ void launch_apply_twopass<float>(const festung_ctx *c, const float *x, float *y,
         constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
         k_flux<float, N, R2, R1><<<grid, 256, 0, st>>>(x, Z1, Z2, c->fB, c->dNbr, c->K, c->fTab, skip);
         k_apply<float, N, R2, R1, MODE_APPLY><<<grid, 256, 0, st>>>(x, Z1, Z2, c->fD, y, c->fB, c->dNbr, c->K, tau,
-                                                                  (float)c->eta, c->fTab, nullptr, nullptr, nullptr,
+                                                                  (float)c->eta, (float)c->mass, c->fTab, nullptr, nullptr, nullptr,
                                                                   nullptr, nullptr, skip);
     });
 }

@@ -21,7 +21,7 @@ void launch_apply<double>(const festung_ctx *c, const double *x, double *y, doub
             configured = smem;
         }
         k_apply_fused<double, N, R2, R1><<<tiles, FUSED_THREADS, smem, st>>>(x, y, c->dD, c->dB, c->dNbr, c->dSlot, c->dHaloPtr,
-                                                                c->dHalo, c->dHaloSlot, c->K, c->TE, c->nslot, tau, (double)c->eta,
+                                                                c->dHalo, c->dHaloSlot, c->K, c->TE, c->nslot, tau, (double)c->eta, (double)c->mass,
                                                                 c->dTab, skip);
     });
 }
@@ -34,7 +34,7 @@ void launch_rhs(const festung_ctx *c, double *W1, double *W2, double *b, double 
         k_dirichlet_lift<double, N, R2, R1><<<grid, 256, 0, st>>>(W1, W2, c->dB, c->dNbr, c->K, c->dTab, c->dCD,
                                                                   c->dPerm);
         k_apply<double, N, R2, R1, MODE_RHS><<<grid, 256, 0, st>>>(c->dC, W1, W2, c->dD, b, c->dB, c->dNbr, c->K,
-                                                                   tau, c->eta, c->dTab, c->dF, c->dCD, c->dGN,
+                                                                   tau, c->eta, c->mass, c->dTab, c->dF, c->dCD, c->dGN,
                                                                    c->dPerm, c->dLift, nullptr);
     });
 }
@@ -48,7 +48,7 @@ void launch_apply_twopass<double>(const festung_ctx *c, const double *x, double 
         constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
         k_flux<double, N, R2, R1><<<grid, 256, 0, st>>>(x, Z1, Z2, c->dB, c->dNbr, c->K, c->dTab, skip);
         k_apply<double, N, R2, R1, MODE_APPLY><<<grid, 256, 0, st>>>(x, Z1, Z2, c->dD, y, c->dB, c->dNbr, c->K, tau,
-                                                                  (double)c->eta, c->dTab, nullptr, nullptr, nullptr,
+                                                                  (double)c->eta, (double)c->mass, c->dTab, nullptr, nullptr, nullptr,
                                                                   nullptr, nullptr, skip);
     });
 }

@@ -48,7 +48,7 @@ struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     int solver = 0, chunk = 0, use_P = -1;
     int64_t nodes = 0;
-    double tau = 0.0;
+    double tau = 0.0, mass = 1.0;
     const void *x = nullptr, *b = nullptr;
 };
 
@@ -509,7 +509,7 @@ GraphCache &graph_of<float>(festung_ctx *c) { return c->ws->g32; }
 // x_zero: x is 0 on entry.  Returns iterations in *iters and the final recursive ||r||^2, ||b||^2.
 template <typename T>
 int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_iter, bool x_zero, int *iters,
-                 double *r2, double *b2, bool *conv) {
+                 double *r2, double *b2, bool *conv, bool reweight = false) {
     Workspace &w = *c->ws;
     Vecs<T> &V = vecs<T>(c);
     const int64_t K = c->K;
@@ -520,10 +520,13 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
     for (int restart = 0; restart < 8; ++restart) {
         // r = b - S x
         if (x_zero && restart == 0) {
-            k_kr_init<T><<<g, RED_THREADS, 0, st>>>(K, N, V.b, nullptr, V.r, V.r0, V.p, V.v, w.part, 0); ++c->launches;
+            k_kr_init<T><<<g, RED_THREADS, 0, st>>>(K, N, V.b, nullptr, V.r, V.r0, V.p, V.v, w.part, reweight ? 1 : 0);
+            ++c->launches;
         } else {
             launch_apply<T>(c, V.x, V.t, V.Z1, V.Z2, (T)tau, nullptr, st);
-            k_kr_init<T><<<g, RED_THREADS, 0, st>>>(K, N, V.b, V.t, V.r, V.r0, V.p, V.v, w.part, restart > 0); ++c->launches;
+            k_kr_init<T><<<g, RED_THREADS, 0, st>>>(K, N, V.b, V.t, V.r, V.r0, V.p, V.v, w.part,
+                                                    (restart > 0 || reweight) ? 1 : 0);
+            ++c->launches;
         }
         k_fin_init<<<1, 1024, 0, st>>>(w.scal, w.part, g, tol); ++c->launches;
         if (solver == FESTUNG_SOLVER_CG) {
@@ -534,7 +537,7 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
         FCK(cudaGetLastError());
         // capture (or reuse) a graph of CHUNK iterations
         GraphCache &gc = graph_of<T>(c);
-        if (!gc.exec || gc.solver != solver || gc.tau != tau || gc.use_P != (int)w.use_P) {
+        if (!gc.exec || gc.solver != solver || gc.tau != tau || gc.use_P != (int)w.use_P || gc.mass != c->mass) {
             if (gc.exec) cudaGraphExecDestroy(gc.exec);
             gc.exec = nullptr;
             cudaStream_t cs;
@@ -554,6 +557,7 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
             gc.solver = solver;
             gc.tau = tau;
             gc.use_P = (int)w.use_P;
+            gc.mass = c->mass;
         }
         bool brk = false, drift = false;
         while (true) {
@@ -948,8 +952,19 @@ int festung_apply(festung_ctx *c, const void *x, void *y, int prec, double dt) {
     return FESTUNG_OK;
 }
 
-int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festung_step_info *info) {
-    if (!ready(c)) return c ? FESTUNG_ESTATE : FESTUNG_EINVAL;
+}  // extern "C"
+
+namespace {
+
+// Solve (mass M + dt (eta S_t - sum_m A_m M^{-1} B_m)) C = b: an implicit-Euler step
+// (mass = 1, E1-E2) or the stationary problem of Sec. 3.9 (mass = 0, dt = 1).
+int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts *opts, festung_step_info *info) {
+    struct MassGuard {
+        festung_ctx *c;
+        ~MassGuard() { c->mass = 1.0; }
+    } guard{c};
+    c->mass = mass;
+    const bool stationary = mass == 0.0;
     festung_step_opts o;
     o.tol = 1e-10;
     o.max_iter = 20000;
@@ -987,7 +1002,7 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
     FCK(cudaGetLastError());
     // initial guess: linear extrapolation in time from the two previous states when the
     // previous step exists, else C^n (the result does not depend on it beyond the tolerance)
-    if (c->hist >= 2 && c->dt_prev > 0.0 && c->dt_prev2 > 0.0) {
+    if (!stationary && c->hist >= 2 && c->dt_prev > 0.0 && c->dt_prev2 > 0.0) {
         // quadratic Lagrange extrapolation through t_{n-2}, t_{n-1}, t_n to t_{n+1}
         const double h0 = c->dt_prev2, h1 = c->dt_prev, h = dt;  // t_n - t_{n-1} = h1, t_{n-1} - t_{n-2} = h0
         const double tn = 0.0, tm1 = -h1, tm2 = -h1 - h0, tp = h;
@@ -996,7 +1011,7 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
         const double l2 = (tp - tn) * (tp - tm1) / ((tm2 - tn) * (tm2 - tm1));
         k_extrapolate3<<<small_grid(KN, c), 256, 0, st>>>(KN, c->dC, c->dCprev, c->dCprev2, V.x, l0, l1, l2);
         ++c->launches;
-    } else if (c->hist >= 1 && c->dt_prev > 0.0) {
+    } else if (!stationary && c->hist >= 1 && c->dt_prev > 0.0) {
         k_extrapolate<<<small_grid(KN, c), 256, 0, st>>>(KN, c->dC, c->dCprev, V.x, dt / c->dt_prev); ++c->launches;
     } else {
         FCK(cudaMemcpyAsync(V.x, c->dC, KN * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1029,6 +1044,7 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
         Vecs<float> &F = w.f;
         double prev_rn = -1.0, last_scale = 0.0;
         int failures = 0;
+        bool applied = false;
         for (outer = 1; outer <= o.max_outer; ++outer) {
             double rn, bn;
             if ((rc = residual64(&rn, &bn))) return rc;
@@ -1037,16 +1053,17 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
                 conv = true;
                 break;
             }
-            if (prev_rn >= 0.0 && !(rn < prev_rn)) {
-                // the sweep did not lower the residual: undo it; retry once in FP32
-                // (fresh shadow residual), then finish in FP64
+            if (applied && !(rn < prev_rn)) {
+                // the last sweep did not lower the FP64 residual: undo it
                 k_add_f32<<<small_grid(KN, c), 256, 0, st>>>(KN, V.x, F.x, -last_scale); ++c->launches;
+                applied = false;
                 if (++failures >= 2) {
                     fp64 = true;
                     break;
                 }
                 if ((rc = residual64(&rn, &bn))) return rc;
-            } else {
+                relres = bn > 0 ? rn / bn : rn;
+            } else if (applied) {
                 failures = 0;
             }
             if (iters >= o.max_iter) break;
@@ -1056,13 +1073,24 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
             int it = 0;
             bool cin = false;
             double ir2, ib2;
-            // the FP32 sweep reduces by inner_tol, or by less when less is still needed
+            // the FP32 sweep reduces by inner_tol, or by less when less is still needed;
+            // after a failure the next sweep starts from a reweighted shadow residual
             const double target = std::min(0.5, std::max(o.inner_tol, 0.5 * o.tol / relres));
-            rc = krylov_solve<float>(c, solver, dt, target, o.max_iter - iters, true, &it, &ir2, &ib2, &cin);
+            rc = krylov_solve<float>(c, solver, dt, target, o.max_iter - iters, true, &it, &ir2, &ib2, &cin,
+                                     failures > 0);
             if (rc) return rc;
             iters += it;
+            if (!(ir2 < ib2)) {
+                // no progress (or non-finite values) in FP32: skip the sweep
+                if (++failures >= 2) {
+                    fp64 = true;
+                    break;
+                }
+                continue;
+            }
             last_scale = rn;
             k_add_f32<<<small_grid(KN, c), 256, 0, st>>>(KN, V.x, F.x, rn); ++c->launches;
+            applied = true;
             FCK(cudaGetLastError());
         }
         if (outer > o.max_outer) outer = o.max_outer;
@@ -1096,6 +1124,12 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
         c->err = "Krylov solve did not converge (relative residual " + std::to_string(relres) + ")";
         return FESTUNG_ENOCONV;
     }
+    if (stationary) {
+        FCK(cudaMemcpyAsync(c->dC, V.x, KN * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        FCK(cudaStreamSynchronize(st));
+        c->hist = 0;  // a stationary solve is no time step: the extrapolation restarts
+        return FESTUNG_OK;
+    }
     if (!c->dCprev) FCK(cudaMalloc(&c->dCprev, KN * sizeof(double)));
     if (!c->dCprev2) FCK(cudaMalloc(&c->dCprev2, KN * sizeof(double)));
     std::swap(c->dCprev, c->dCprev2);  // C^{n-2} <- C^{n-1}
@@ -1106,6 +1140,24 @@ int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festu
     c->dt_prev2 = c->dt_prev;
     c->dt_prev = dt;
     return FESTUNG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int festung_step(festung_ctx *c, double dt, const festung_step_opts *opts, festung_step_info *info) {
+    if (!ready(c)) return c ? FESTUNG_ESTATE : FESTUNG_EINVAL;
+    return solve_system(c, dt, 1.0, opts, info);
+}
+
+int festung_solve_stationary(festung_ctx *c, const festung_step_opts *opts, festung_step_info *info) {
+    if (!ready(c)) return c ? FESTUNG_ESTATE : FESTUNG_EINVAL;
+    if (!c->has_dirichlet) {
+        c->err = "the stationary problem needs a Dirichlet edge (with zero-flux data alone it is singular)";
+        return FESTUNG_EINVAL;
+    }
+    return solve_system(c, 1.0, 0.0, opts, info);
 }
 
 int festung_l2_error(const festung_ctx *cc, const double *c_samples, double *err) {

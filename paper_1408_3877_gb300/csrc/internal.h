@@ -107,6 +107,7 @@ struct festung_ctx {
     // order / tables
     int p = -1, N = 0, R2 = 0, R1 = 0, qT = 0;
     double eta = 1.0;
+    double mass = 1.0;  // coefficient of M in the operator: 1 for a step, 0 for the stationary problem
     festung::HostTables tab;
     double *dTab = nullptr;  // FP64 tables, layout table_offsets
     float *fTab = nullptr;   // FP32 copy

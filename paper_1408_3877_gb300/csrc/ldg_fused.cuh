@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_apply_fused(
     const T *__restrict__ X, T *__restrict__ Y, const T *__restrict__ Dc, const T *__restrict__ Bg,
     const int32_t *__restrict__ nbr, const int16_t *__restrict__ slotg, const int32_t *__restrict__ halo_ptr,
     const int32_t *__restrict__ halo, const int16_t *__restrict__ halo_slot, int64_t K, int TE, int NS, T tau,
-    T eta, const T *__restrict__ tabg, const int *__restrict__ skip) {
+    T eta, T mass, const T *__restrict__ tabg, const int *__restrict__ skip) {
     constexpr bool kBigVolume = R2 * N > 150;
     constexpr int NP = ((N * (int)sizeof(T) + 15) / 16) * 16 / (int)sizeof(T);
     constexpr int VOL = kBigVolume ? 3 * R2 * NP : 4;
@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_apply_fused(
     tile_edge<T, N, R2, R1, 2>(c2, c2 >= 0 ? slotg[2 * Ki + k] : 0, tr, NS, i, b11, b12, b21, b22, eta, acc);
     const T det = b11 * b22 - b12 * b21;
 #pragma unroll
-    for (int j = 0; j < N; ++j) Y[j * Ki + k] = det * X[j * Ki + k] + tau * acc[j];
+    for (int j = 0; j < N; ++j) Y[j * Ki + k] = mass * det * X[j * Ki + k] + tau * acc[j];
 }
 
 }  // namespace festung

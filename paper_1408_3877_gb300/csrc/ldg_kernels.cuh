@@ -172,8 +172,9 @@ __global__ void __launch_bounds__(256) k_flux(const T *__restrict__ X, T *__rest
 }
 
 // ---------------------------------------------------------------------------
-// Pass 2.  MODE_APPLY:  y = M x + tau (eta (S + S_D) x + sum_m A_m Z^m)          (E1)
-//          MODE_RHS:    y = M x + tau (M F + eta K_D - K_N + sum_m A_m Z^m)     (E2)
+// Pass 2.  MODE_APPLY:  y = mass M x + tau (eta (S + S_D) x + sum_m A_m Z^m)     (E1)
+//          MODE_RHS:    y = mass M x + tau (M F + eta K_D - K_N + sum_m A_m Z^m) (E2)
+// (mass = 1 for a time step; mass = 0, tau = 1 for the stationary problem of Sec. 3.9)
 // with A_m = -G^m + R^m + R_D^m (G^m Sec. 3.6.3, R^m eq. globR, R_D^m eq. globR:D,
 // S eq. globS, S_D eq. globS:D, K_D eq. globK:D, K_N Sec. 3.6.12).  Volume terms use
 // the triangle rule, edge terms the Gauss rule, as the reference integrals do.
@@ -185,7 +186,7 @@ template <typename T, int N, int R2, int R1, int MODE>
 __global__ void __launch_bounds__(256) k_apply(const T *__restrict__ X, const T *__restrict__ Z1,
                                                const T *__restrict__ Z2, const T *__restrict__ Dc,
                                                T *__restrict__ Y, const T *__restrict__ Bg,
-                                               const int32_t *__restrict__ nbr, int64_t K, T tau, T eta,
+                                               const int32_t *__restrict__ nbr, int64_t K, T tau, T eta, T mass,
                                                const T *__restrict__ tabg, const T *__restrict__ F,
                                                const T *__restrict__ cD, const T *__restrict__ gN,
                                                const int32_t *__restrict__ perm, const uint8_t *__restrict__ lift,
@@ -287,9 +288,8 @@ __global__ void __launch_bounds__(256) k_apply(const T *__restrict__ X, const T 
         const T det = b11 * b22 - b12 * b21;  // M = 2|T_k| I (Sec. 3.6.1)
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            T mass = det * x[i];
             if (MODE == MODE_RHS && F) acc[i] += det * F[i * K + k];
-            Y[i * K + k] = mass + tau * acc[i];
+            Y[i * K + k] = mass * det * x[i] + tau * acc[i];
         }
     }
 }
@@ -348,7 +348,7 @@ namespace festung {
 template <typename T, int N, int R2, int R1>
 __global__ void __launch_bounds__(128) k_blockdiag(float *__restrict__ P, const T *__restrict__ Bg,
                                                    const int32_t *__restrict__ nbr, const T *__restrict__ Dc,
-                                                   int64_t K, T tau, T eta, const T *__restrict__ tabg) {
+                                                   int64_t K, T tau, T eta, T mass, const T *__restrict__ tabg) {
     __shared__ SmemTab<T, N, R2, R1> s;
     load_tables(s, tabg);
     __syncthreads();
@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(128) k_blockdiag(float *__restrict__ P, const 
             }
 #pragma unroll
             for (int i = 0; i < N; ++i)
-                P[(int64_t)(i * N + j) * K + k] = (float)((i == j ? det : T(0)) + tau * acc[i]);
+                P[(int64_t)(i * N + j) * K + k] = (float)((i == j ? mass * det : T(0)) + tau * acc[i]);
         }
     }
 }

@@ -21,7 +21,8 @@ BDR_INTERIOR, BDR_DIRICHLET, BDR_NEUMANN = 0, 1, 2
 EXPORTS = [
     "festung_mesh_create", "festung_setup", "festung_sizes", "festung_quad_points",
     "festung_set_coeff", "festung_set_source", "festung_set_bc", "festung_set_state",
-    "festung_get_state", "festung_apply", "festung_apply_noalloc", "festung_step", "festung_l2_error",
+    "festung_get_state", "festung_apply", "festung_apply_noalloc", "festung_step", "festung_solve_stationary",
+    "festung_l2_error",
     "festung_element_order", "festung_launch_count", "festung_set_stream", "festung_last_error", "festung_destroy",
 ]
 
@@ -69,6 +70,7 @@ def load(path=None):
     lib.festung_apply_noalloc.argtypes = [vp, vp, vp, cint, dbl]
     lib.festung_step.argtypes = [vp, dbl, ctypes.POINTER(StepOpts), ctypes.POINTER(StepInfo)]
     lib.festung_l2_error.argtypes = [vp, vp, ctypes.POINTER(dbl)]
+    lib.festung_solve_stationary.argtypes = [vp, ctypes.POINTER(StepOpts), ctypes.POINTER(StepInfo)]
     lib.festung_set_stream.argtypes = [vp, vp]
     lib.festung_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
     lib.festung_element_order.argtypes = [vp, vp]
@@ -197,6 +199,14 @@ class Solver:
         n = ctypes.c_int64()
         self._check(self.lib.festung_launch_count(self.h, ctypes.byref(n)))
         return n.value
+
+    def solve_stationary(self, tol=1e-10, prec=MIXED, max_iter=100000, inner_tol=1e-2, max_outer=50, solver=0):
+        """The stationary problem of Sec. 3.9 with the current coefficient, source and boundary data."""
+        o = StepOpts(tol, max_iter, prec, inner_tol, max_outer, solver)
+        info = StepInfo()
+        self._check(self.lib.festung_solve_stationary(self.h, ctypes.byref(o), ctypes.byref(info)))
+        return {"iterations": info.iterations, "outer": info.outer, "rel_residual": info.rel_residual,
+                "solver": info.solver, "symmetric": info.symmetric, "fp64_iterations": info.fp64_iterations}
 
     def l2_error(self, c_samples):
         s = np.ascontiguousarray(c_samples, dtype=np.float64)

@@ -1,0 +1,63 @@
+"""The stationary problem of Sec. 3.9 on the GPU: parity with the oracle's direct solve
+and the L2 convergence orders of Tab. 2 (order p + 1) on meshes up to 64 x 64."""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from helpers import edge_samples, gpu_solver, samples
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+MAN = W.Manufactured(W.d_verification, stationary=True)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def _gpu_stationary(n, p, tol, prec, jitter=0.0):
+    cV, V0T, side = W.square_mesh(n, jitter=jitter, seed=3)
+    bdr = W.boundary_types(side, (2, 4), (1, 3))
+    s = gpu_solver(cV, V0T, bdr, p)
+    s.set_coeff(samples(s, lambda x, y: MAN.d(0, x, y)))
+    s.set_source(samples(s, lambda x, y: MAN.f(0, x, y)))
+    s.set_bc(edge_samples(s, lambda x, y: MAN.c(0, x, y)), edge_samples(s, lambda x, y: MAN.gN(0, x, y)))
+    info = s.solve_stationary(tol=tol, prec=prec)
+    return s, info, (cV, V0T, bdr)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_stationary_matches_oracle(p):
+    from oracle.solve import LDG
+    from paper_1408_3877_gb300 import festung as F
+    s, info, (cV, V0T, bdr) = _gpu_stationary(6, p, 1e-13, F.FP64, jitter=0.2)
+    C = s.get_state()
+    L = LDG(cV, V0T, bdr, p)
+    Co = L.stationary(L.project(lambda x, y: MAN.d(0, x, y)), L.project(lambda x, y: MAN.f(0, x, y)),
+                      lambda x, y: MAN.c(0, x, y), lambda x, y: MAN.gN(0, x, y))
+    err = np.linalg.norm(C - Co) / np.linalg.norm(Co)
+    # the stationary operator has no mass term: cond(S) ~ 1e3-1e4 on these meshes
+    assert err <= 1e-9, (err, info)
+    s.close()
+
+
+def test_stationary_rates_on_gpu():
+    """Sec. 3.9 / Tab. 2: errors decrease with order p + 1 (FP64 Krylov, tol 1e-12: without
+    the mass term the stationary operator is too ill-conditioned for FP32 sweeps at p = 4)."""
+    from paper_1408_3877_gb300 import festung as F
+    gold = {int(p): a for p, a in np.loadtxt(os.path.join(GOLDEN, "verification_rates.txt"))}
+    for p in (1, 2, 3, 4):
+        errs = []
+        for n in (8, 16, 32, 64):
+            s, info, _ = _gpu_stationary(n, p, 1e-12, F.FP64)
+            xy, _ = s.quad_points()
+            errs.append(s.l2_error(MAN.c(0, xy[..., 0], xy[..., 1])))
+            s.close()
+        rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+        assert abs(rates[-1] - (p + 1)) < 0.3, (p, errs, rates, gold[p])
