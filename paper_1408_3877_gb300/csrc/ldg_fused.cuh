@@ -47,41 +47,53 @@ __device__ __forceinline__ void ctrace(const T (&c)[N], T (&out)[R1]) {
     }
 }
 
-// Shared-memory traces: field f (0: x, 1: d_h, 2: z^1, 3: z^2) on edge n of slot s
-// occupy RP consecutive values (R1 Gauss points padded to a multiple of 16 bytes), so
-// one thread moves a whole trace with 128-bit accesses.
+// Shared-memory traces of field f (0: x, 1: d_h, 2: z^1, 3: z^2) on edge n of slot s.
+// When padding the R1 Gauss points to 16 bytes costs little, a trace is one padded
+// vector moved with 128-bit accesses; otherwise (R1 = 5 in FP32) the points are stored
+// one array per point, which keeps the shared memory of a block small enough for two
+// blocks per SM.
 template <typename T, int R1>
 struct TraceLayout {
     static constexpr int per16 = 16 / sizeof(T);
-    static constexpr int RP = ((R1 + per16 - 1) / per16) * per16;
-    static constexpr int nvec = RP / per16;
+    static constexpr int RPAD = ((R1 + per16 - 1) / per16) * per16;
+    // vector layout when padding wastes at most a quarter, else one value per access
+    static constexpr bool vec = 4 * (RPAD - R1) <= RPAD;
+    static constexpr int RP = vec ? RPAD : R1;
+    static constexpr int nvec = RPAD / per16;
 };
 
-template <typename T, int R1>
-__device__ __forceinline__ T *tr_ptr(T *tr, int f, int n, int slot, int NS) {
-    return tr + ((size_t)(f * 3 + n) * NS + slot) * TraceLayout<T, R1>::RP;
-}
-
+// vector layout: a trace is RP consecutive values at ((f * 3 + n) * NS + slot) * RP;
+// scalar layout: point r of the trace at (((f * 3 + n) * R1 + r) * NS + slot)
 template <typename T, int R1>
 __device__ __forceinline__ void tr_store(T *tr, int f, int n, int slot, int NS, const T (&v)[R1]) {
     using L = TraceLayout<T, R1>;
-    T buf[L::RP];
+    if constexpr (L::vec) {
+        T buf[L::RP];
 #pragma unroll
-    for (int r = 0; r < L::RP; ++r) buf[r] = r < R1 ? v[r] : T(0);
-    float4 *dst = reinterpret_cast<float4 *>(tr_ptr<T, R1>(tr, f, n, slot, NS));
+        for (int r = 0; r < L::RP; ++r) buf[r] = r < R1 ? v[r] : T(0);
+        float4 *dst = reinterpret_cast<float4 *>(tr + ((size_t)(f * 3 + n) * NS + slot) * L::RP);
 #pragma unroll
-    for (int q = 0; q < L::nvec; ++q) dst[q] = reinterpret_cast<const float4 *>(buf)[q];
+        for (int q = 0; q < L::nvec; ++q) dst[q] = reinterpret_cast<const float4 *>(buf)[q];
+    } else {
+#pragma unroll
+        for (int r = 0; r < R1; ++r) tr[((size_t)(f * 3 + n) * R1 + r) * NS + slot] = v[r];
+    }
 }
 
 template <typename T, int R1>
 __device__ __forceinline__ void tr_load(const T *tr, int f, int n, int slot, int NS, T (&v)[R1]) {
     using L = TraceLayout<T, R1>;
-    T buf[L::RP];
-    const float4 *src = reinterpret_cast<const float4 *>(tr_ptr<T, R1>(const_cast<T *>(tr), f, n, slot, NS));
+    if constexpr (L::vec) {
+        T buf[L::RP];
+        const float4 *src = reinterpret_cast<const float4 *>(tr + ((size_t)(f * 3 + n) * NS + slot) * L::RP);
 #pragma unroll
-    for (int q = 0; q < L::nvec; ++q) reinterpret_cast<float4 *>(buf)[q] = src[q];
+        for (int q = 0; q < L::nvec; ++q) reinterpret_cast<float4 *>(buf)[q] = src[q];
 #pragma unroll
-    for (int r = 0; r < R1; ++r) v[r] = buf[r];
+        for (int r = 0; r < R1; ++r) v[r] = buf[r];
+    } else {
+#pragma unroll
+        for (int r = 0; r < R1; ++r) v[r] = tr[((size_t)(f * 3 + n) * R1 + r) * NS + slot];
+    }
 }
 
 // Phase A1 for triangle e at shared-memory slot `slot`: loads x and d_h of e and stores
