@@ -16,16 +16,35 @@ void launch_apply<float>(const festung_ctx *c, const float *x, float *y, float *
     c->launches += 1;
     dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
         constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
-        const size_t smem = (size_t)4 * 3 * TraceLayout<float, R1>::RP * c->nslot * sizeof(float);
-        static size_t configured = 0;
-        if (smem > configured) {
-            cudaFuncSetAttribute(k_apply_fused<float, N, R2, R1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            configured = smem;
-        }
+        const size_t smem = fused_smem<float, R1>(c->nslot);
+        static const bool smem_ok = allow_max_smem(k_apply_fused<float, N, R2, R1>);
+        (void)smem_ok;
         k_apply_fused<float, N, R2, R1><<<tiles, FUSED_THREADS, smem, st>>>(x, y, c->fD, c->fB, c->dNbr, c->dSlot, c->dHaloPtr,
                                                                 c->dHalo, c->dHaloSlot, c->K, c->TE, c->nslot, tau, (float)c->eta, (float)c->mass,
                                                                 c->fTab, skip);
     });
+}
+
+int fused_resident_blocks(const festung_ctx *c, int nslot) {
+    int nb = 0;
+    dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
+        constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
+        static const bool smem_ok = allow_max_smem(k_apply_fused<float, N, R2, R1>);
+        (void)smem_ok;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_apply_fused<float, N, R2, R1>, FUSED_THREADS,
+                                                          fused_smem<float, R1>(nslot)) != cudaSuccess)
+            nb = 0;
+    });
+    return std::max(1, nb) * c->num_sms;
+}
+
+size_t fused_smem_bytes(const festung_ctx *c, int nslot, bool fp64) {
+    size_t b = 0;
+    dispatch(c->N, c->R2, c->R1, [&](auto, auto, auto r1_) {
+        constexpr int R1 = decltype(r1_)::value;
+        b = fp64 ? fused_smem<double, R1>(nslot) : fused_smem<float, R1>(nslot);
+    });
+    return b;
 }
 
 void launch_blockjacobi(const festung_ctx *c, float *P, __nv_bfloat16 *Pinv, double tau, int *flags,

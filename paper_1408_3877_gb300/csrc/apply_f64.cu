@@ -14,12 +14,9 @@ void launch_apply<double>(const festung_ctx *c, const double *x, double *y, doub
     c->launches += 1;
     dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
         constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
-        const size_t smem = (size_t)4 * 3 * TraceLayout<double, R1>::RP * c->nslot * sizeof(double);
-        static size_t configured = 0;
-        if (smem > configured) {
-            cudaFuncSetAttribute(k_apply_fused<double, N, R2, R1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            configured = smem;
-        }
+        const size_t smem = fused_smem<double, R1>(c->nslot);
+        static const bool smem_ok = allow_max_smem(k_apply_fused<double, N, R2, R1>);
+        (void)smem_ok;
         k_apply_fused<double, N, R2, R1><<<tiles, FUSED_THREADS, smem, st>>>(x, y, c->dD, c->dB, c->dNbr, c->dSlot, c->dHaloPtr,
                                                                 c->dHalo, c->dHaloSlot, c->K, c->TE, c->nslot, tau, (double)c->eta, (double)c->mass,
                                                                 c->dTab, skip);

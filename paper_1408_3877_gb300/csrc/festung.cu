@@ -611,6 +611,76 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
 
 }  // namespace
 
+namespace {
+
+// Tiles of te consecutive triangles of the internal order: halo lists and the
+// shared-memory slots of every neighbour, uploaded to the device (the previous tiling
+// is released on success).
+cudaError_t retile(festung_ctx *c, int te) {
+    MeshOrder mo;
+    tile_mesh(c->hNbrInt, c->K, te, mo);
+    const int64_t K = c->K, T = (K + te - 1) / te;
+    std::vector<int16_t> slot16(mo.slot.begin(), mo.slot.end());
+    std::vector<int16_t> hslot16(mo.halo_slot.begin(), mo.halo_slot.end());
+    int32_t *hp = nullptr, *h = nullptr;
+    int16_t *hs = nullptr;
+    cudaError_t e;
+    auto undo = [&](cudaError_t err) {
+        cudaFree(hp);
+        cudaFree(h);
+        cudaFree(hs);
+        return err;
+    };
+    if ((e = cudaMalloc(&hp, (T + 1) * sizeof(int32_t))) != cudaSuccess) return undo(e);
+    if ((e = cudaMalloc(&h, std::max<size_t>(1, mo.halo.size()) * sizeof(int32_t))) != cudaSuccess) return undo(e);
+    if ((e = cudaMalloc(&hs, std::max<size_t>(1, hslot16.size()) * sizeof(int16_t))) != cudaSuccess) return undo(e);
+    if ((e = cudaMemcpy(hp, mo.halo_ptr.data(), (T + 1) * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return undo(e);
+    if (!mo.halo.empty() &&
+        (e = cudaMemcpy(h, mo.halo.data(), mo.halo.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return undo(e);
+    if (!hslot16.empty() &&
+        (e = cudaMemcpy(hs, hslot16.data(), hslot16.size() * sizeof(int16_t), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return undo(e);
+    if ((e = cudaMemcpy(c->dSlot, slot16.data(), 3 * K * sizeof(int16_t), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return undo(e);
+    cudaFree(c->dHaloPtr);
+    cudaFree(c->dHalo);
+    cudaFree(c->dHaloSlot);
+    c->dHaloPtr = hp;
+    c->dHalo = h;
+    c->dHaloSlot = hs;
+    c->TE = te;
+    c->max_halo = mo.max_halo;
+    c->nslot = te + mo.max_halo;
+    return cudaSuccess;
+}
+
+// Tile size for the kernels of the context's order: whole waves of the FP32 fused
+// apply's resident blocks, and small enough that the FP64 kernel's traces fit in the
+// shared memory of one block.
+int choose_tiles(festung_ctx *c) {
+    int dev = 0, optin = 0;
+    FCK(cudaGetDevice(&dev));
+    FCK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int resident = fused_resident_blocks(c, c->nslot);
+    int te = tile_size(c->K, resident, c->num_sms);
+    for (;;) {
+        if (te != c->TE) FCK(retile(c, te));
+        // static shared memory of the kernels (tables) stays below 16 KB
+        if (fused_smem_bytes(c, c->nslot, true) + 16384 <= (size_t)optin || te <= 32) break;
+        te = std::max(32, ((te / 2 + 31) / 32) * 32);
+    }
+    if (fused_smem_bytes(c, c->nslot, true) + 16384 > (size_t)optin) {
+        c->err = "mesh tiles need more shared memory than a block has (halo of " + std::to_string(c->max_halo) +
+                 " triangles)";
+        return FESTUNG_EMESH;
+    }
+    return FESTUNG_OK;
+}
+
+}  // namespace
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -646,13 +716,12 @@ int festung_mesh_create(const double *coordV, int64_t numV, const int32_t *V0T, 
         if (bdr_type[i] == FESTUNG_BDR_DIRICHLET) c->has_dirichlet = true;
         if (bdr_type[i] == FESTUNG_BDR_NEUMANN) c->has_neumann = true;
     }
-    // internal order: Morton order of centroids, in tiles of 256 triangles
+    // internal order: Morton order of centroids; tiles of 256 triangles until
+    // festung_setup sizes them for the kernels of the chosen order
     MeshOrder mo;
-    order_and_tile(coordV, V0T, numT, c->hB, nbr, 256, mo);
+    order_mesh(coordV, V0T, numT, c->hB, nbr, mo);
     c->perm = mo.perm;
-    c->TE = mo.TE;
-    c->max_halo = mo.max_halo;
-    c->nslot = mo.TE + mo.max_halo;
+    c->hNbrInt = mo.nbr;
     auto fail = [&](cudaError_t e) {
         g_create_err = std::string("CUDA: ") + cudaGetErrorString(e);
         festung_destroy(c);
@@ -668,16 +737,8 @@ int festung_mesh_create(const double *coordV, int64_t numV, const int32_t *V0T, 
     if ((e = cudaMalloc(&c->fB, 4 * K * sizeof(float))) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&c->dNbr, 3 * K * sizeof(int32_t))) != cudaSuccess) return fail(e);
     std::vector<float> fB(mo.B.begin(), mo.B.end());
-    std::vector<int16_t> slot16(mo.slot.begin(), mo.slot.end());
-    std::vector<int16_t> hslot16(mo.halo_slot.begin(), mo.halo_slot.end());
-    const int64_t T = (K + mo.TE - 1) / mo.TE;
     if ((e = cudaMalloc(&c->dPerm, K * sizeof(int32_t))) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&c->dSlot, 3 * K * sizeof(int16_t))) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&c->dHaloPtr, (T + 1) * sizeof(int32_t))) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&c->dHalo, std::max<size_t>(1, mo.halo.size()) * sizeof(int32_t))) != cudaSuccess)
-        return fail(e);
-    if ((e = cudaMalloc(&c->dHaloSlot, std::max<size_t>(1, hslot16.size()) * sizeof(int16_t))) != cudaSuccess)
-        return fail(e);
     if ((e = cudaMalloc(&c->dLift, K * sizeof(uint8_t))) != cudaSuccess) return fail(e);
     const struct {
         void *dst;
@@ -687,13 +748,10 @@ int festung_mesh_create(const double *coordV, int64_t numV, const int32_t *V0T, 
               {c->fB, fB.data(), 4 * K * sizeof(float)},
               {c->dNbr, mo.nbr.data(), 3 * K * sizeof(int32_t)},
               {c->dPerm, mo.perm.data(), K * sizeof(int32_t)},
-              {c->dSlot, slot16.data(), 3 * K * sizeof(int16_t)},
-              {c->dHaloPtr, mo.halo_ptr.data(), (T + 1) * sizeof(int32_t)},
-              {c->dHalo, mo.halo.data(), mo.halo.size() * sizeof(int32_t)},
-              {c->dHaloSlot, hslot16.data(), hslot16.size() * sizeof(int16_t)},
               {c->dLift, mo.lift.data(), K * sizeof(uint8_t)}};
     for (const auto &u : up)
         if (u.bytes && (e = cudaMemcpy(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+    if ((e = retile(c, 256)) != cudaSuccess) return fail(e);
     *out = c;
     return FESTUNG_OK;
 }
@@ -750,6 +808,7 @@ int festung_setup(festung_ctx *c, int p, int quad_order, double eta) {
     FCK(cudaMemcpy(c->fTab, hf.data(), o.total * sizeof(float), cudaMemcpyHostToDevice));
     FCK(upload_tables_f64(c));
     FCK(upload_tables_f32(c));
+    if (int rc = choose_tiles(c)) return rc;
     FCK(cudaMalloc(&c->dC, K * N * sizeof(double)));
     FCK(cudaMalloc(&c->dD, K * N * sizeof(double)));
     FCK(cudaMalloc(&c->fD, K * N * sizeof(float)));

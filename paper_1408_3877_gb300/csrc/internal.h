@@ -65,8 +65,16 @@ struct MeshOrder {
     std::vector<int32_t> halo_slot; // 3 per halo entry: slot of its neighbour, -1 boundary, -2 not resident
     std::vector<uint8_t> lift;      // K: bit 1 set if the Dirichlet lift reaches the triangle's right-hand side
 };
+// order_mesh: perm, inv, B, nbr and lift; tile_mesh: tiles of TE triangles (internal
+// neighbour codes nbr) into o's tile fields.
+void order_mesh(const double *coordV, const int32_t *V0T, int64_t K, const std::vector<double> &B_usr,
+                const std::vector<int32_t> &nbr_usr, MeshOrder &o);
+void tile_mesh(const std::vector<int32_t> &nbr, int64_t K, int TE, MeshOrder &o);
 void order_and_tile(const double *coordV, const int32_t *V0T, int64_t K, const std::vector<double> &B_usr,
                     const std::vector<int32_t> &nbr_usr, int TE, MeshOrder &o);
+// Tile size (32..256, a multiple of 32) for K triangles when `resident` blocks run at
+// once on `sms` multiprocessors.
+int tile_size(int64_t K, int resident, int sms);
 
 // Device-side view passed to kernels.
 template <typename T>
@@ -95,6 +103,7 @@ struct festung_ctx {
     std::vector<int32_t> perm;  // internal index -> caller's triangle index
     int32_t *dPerm = nullptr;   // device copy of perm
     int TE = 0, max_halo = 0, nslot = 0;
+    std::vector<int32_t> hNbrInt;  // 3 x K neighbour codes in internal order (for re-tiling)
     int32_t *dHaloPtr = nullptr, *dHalo = nullptr;
     int16_t *dSlot = nullptr;   // 3 x K
     int16_t *dHaloSlot = nullptr;  // 3 per halo entry

@@ -245,7 +245,16 @@ __device__ __forceinline__ void tile_edge(int code, int sl, const T *tr, int NS,
     }
 }
 
-constexpr int FUSED_THREADS = 320;  // a tile of 256 triangles plus up to 64 halo triangles per round
+constexpr int FUSED_THREADS = 320;  // a tile of up to 256 triangles plus at least 64 halo threads
+constexpr int FUSED_MAX_TE = 256;
+
+// Minimum resident blocks per SM asked of the register allocator: two for the FP32
+// kernels of p >= 3, which would otherwise take 130-168 registers a thread and run
+// one block per SM (0 leaves the allocator's default).
+template <typename T, int N>
+struct FusedOcc {
+    static constexpr int min_blocks = (sizeof(T) == 4 && N >= 10) ? 2 : 0;
+};
 
 // volume term -sum_m G^m Z^m at the triangle points (Sec. 3.6.3), tables in the constant bank
 template <typename T, int N, int R2, int R1>
@@ -299,8 +308,28 @@ __device__ __forceinline__ void volume_smem(const T *phiQ_s, const T *gw1_s, con
     }
 }
 
+// Dynamic shared memory of one block: four traced fields on three edges per slot.
+template <typename T, int R1>
+constexpr size_t fused_smem(int nslot) {
+    return (size_t)4 * 3 * TraceLayout<T, R1>::RP * nslot * sizeof(T);
+}
+
+// Let a kernel take the device's opt-in maximum of dynamic shared memory (once per
+// kernel; the launch then passes only what it needs).
+template <typename Kern>
+bool allow_max_smem(Kern kernel) {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, kernel) != cudaSuccess)
+        return false;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)fa.sharedSizeBytes) == cudaSuccess;
+}
+
 template <typename T, int N, int R2, int R1>
-__global__ void __launch_bounds__(FUSED_THREADS) k_apply_fused(
+__global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_apply_fused(
     const T *__restrict__ X, T *__restrict__ Y, const T *__restrict__ Dc, const T *__restrict__ Bg,
     const int32_t *__restrict__ nbr, const int16_t *__restrict__ slotg, const int32_t *__restrict__ halo_ptr,
     const int32_t *__restrict__ halo, const int16_t *__restrict__ halo_slot, int64_t K, int TE, int NS, T tau,

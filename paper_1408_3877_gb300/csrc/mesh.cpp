@@ -124,8 +124,8 @@ uint64_t spread2(uint64_t v) {
 
 }  // namespace
 
-void order_and_tile(const double *coordV, const int32_t *V0T, int64_t K, const std::vector<double> &B_usr,
-                    const std::vector<int32_t> &nbr_usr, int TE, MeshOrder &o) {
+void order_mesh(const double *coordV, const int32_t *V0T, int64_t K, const std::vector<double> &B_usr,
+                const std::vector<int32_t> &nbr_usr, MeshOrder &o) {
     // Morton order of the triangle centroids: nearby triangles get nearby indices, so a
     // tile of TE consecutive triangles is a compact patch with a short boundary.
     std::vector<double> cx(K), cy(K);
@@ -177,6 +177,9 @@ void order_and_tile(const double *coordV, const int32_t *V0T, int64_t K, const s
             const int32_t code = o.nbr[n * K + i];
             if (code >= 0 && (o.lift[code >> 2] & 1)) o.lift[i] |= 2;
         }
+}
+
+void tile_mesh(const std::vector<int32_t> &nbr, int64_t K, int TE, MeshOrder &o) {
     // tiles of TE consecutive triangles; halo = interior neighbours outside the tile
     o.TE = TE;
     const int64_t T = (K + TE - 1) / TE;
@@ -191,7 +194,7 @@ void order_and_tile(const double *coordV, const int32_t *V0T, int64_t K, const s
         h.clear();
         for (int64_t i = s0; i < s1; ++i)
             for (int n = 0; n < 3; ++n) {
-                const int32_t code = o.nbr[n * K + i];
+                const int32_t code = nbr[n * K + i];
                 if (code < 0) continue;
                 const int64_t k2 = code >> 2;
                 if (k2 < s0 || k2 >= s1) h.push_back((int32_t)k2);
@@ -200,7 +203,7 @@ void order_and_tile(const double *coordV, const int32_t *V0T, int64_t K, const s
         h.erase(std::unique(h.begin(), h.end()), h.end());
         for (int64_t i = s0; i < s1; ++i)
             for (int n = 0; n < 3; ++n) {
-                const int32_t code = o.nbr[n * K + i];
+                const int32_t code = nbr[n * K + i];
                 if (code < 0) continue;
                 const int64_t k2 = code >> 2;
                 if (k2 >= s0 && k2 < s1) {
@@ -214,7 +217,7 @@ void order_and_tile(const double *coordV, const int32_t *V0T, int64_t K, const s
         // halo), -1 on the boundary, -2 if they lie outside the tile's slots
         for (int32_t e : h)
             for (int n = 0; n < 3; ++n) {
-                const int32_t code = o.nbr[n * K + e];
+                const int32_t code = nbr[n * K + e];
                 int32_t sl = -1;
                 if (code >= 0) {
                     const int64_t k2 = code >> 2;
@@ -231,6 +234,24 @@ void order_and_tile(const double *coordV, const int32_t *V0T, int64_t K, const s
         o.halo_ptr[t + 1] = (int32_t)o.halo.size();
         o.max_halo = std::max<int>(o.max_halo, (int)h.size());
     }
+}
+
+void order_and_tile(const double *coordV, const int32_t *V0T, int64_t K, const std::vector<double> &B_usr,
+                    const std::vector<int32_t> &nbr_usr, int TE, MeshOrder &o) {
+    order_mesh(coordV, V0T, K, B_usr, nbr_usr, o);
+    tile_mesh(o.nbr, K, TE, o);
+}
+
+int tile_size(int64_t K, int resident, int sms) {
+    // tiles of at most 256 triangles; while tiles of 256 leave SMs idle, keep them (one
+    // block per SM), else as many as fill a whole number of waves of `resident` blocks,
+    // rounded up to whole warps
+    if ((K + 255) / 256 <= std::max(1, sms)) return 256;
+    const int64_t R = std::max(1, resident);
+    const int64_t waves = (K + 256 * R - 1) / (256 * R);
+    int64_t te = (K + waves * R - 1) / (waves * R);
+    te = ((te + 31) / 32) * 32;
+    return (int)std::min<int64_t>(256, std::max<int64_t>(32, te));
 }
 
 }  // namespace festung

@@ -27,6 +27,12 @@ void launch_rhs(const festung_ctx *c, double *W1, double *W2, double *b, double 
 
 int elem_grid(const festung_ctx *c);
 
+// Blocks of the FP32 fused apply that run at once on the device (resident blocks per
+// SM times SMs) for tiles with nslot shared-memory slots, and the dynamic shared
+// memory of one block of the FP32 or FP64 kernel.
+int fused_resident_blocks(const festung_ctx *c, int nslot);
+size_t fused_smem_bytes(const festung_ctx *c, int nslot, bool fp64);
+
 // Reference tables of the context's (p, quadrature) into the constant bank of the
 // fused apply kernels (FP64 and FP32 copies).
 cudaError_t upload_tables_f64(const festung_ctx *c);

@@ -135,5 +135,21 @@ int main(int argc, char **argv) {
         if (((o.lift[i] & 1) != 0) != own || ((o.lift[i] & 2) != 0) != (own || near)) return fail("lift flags");
     }
     std::printf("ok lift\n");
+    // tile sizes: whole warps, at most 256, and the tiles fill whole waves of resident blocks
+    for (int64_t KK : {1L, 31L, 72L, 8192L, 131072L, 131073L, 2097152L})
+        for (int R : {1, 152, 304, 456}) {
+            const int sms = R < 152 ? R : 152;
+            const int te = tile_size(KK, R, sms);
+            if (te < 32 || te > 256 || te % 32) return fail("tile size range");
+            if ((KK + 255) / 256 <= sms) {
+                if (te != 256) return fail("tiles split although SMs are idle");
+                continue;
+            }
+            const int64_t waves = (KK + 256L * R - 1) / (256L * R);
+            const int64_t tiles = (KK + te - 1) / te;
+            if (te > 32 && tiles > waves * R) return fail("tiles exceed whole waves");
+            if (te - 32 >= (KK + waves * R - 1) / (waves * R)) return fail("tile size larger than needed");
+        }
+    std::printf("ok tile_size\n");
     return 0;
 }

@@ -27,3 +27,4 @@ def test_order_and_tiles(exe, n, te):
     r = subprocess.run([exe, str(n), str(te)], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "ok perm" in r.stdout and "ok neighbours" in r.stdout and "ok tiles" in r.stdout and "ok lift" in r.stdout
+    assert "ok tile_size" in r.stdout
