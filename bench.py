@@ -376,7 +376,8 @@ def profile_apply(args):
         s.set_coeff(np.exp(g(xy[..., 0], xy[..., 1])))
     else:
         s.set_coeff(W.d_config2(0.5, xy[..., 0], xy[..., 1])[0])
-    prec, dt = (F.FP32, torch.float32) if args.prec == "fp32" else (F.FP64, torch.float64)
+    prec, dt = {"fp32": (F.FP32, torch.float32), "fp64": (F.FP64, torch.float64),
+                "dfloat": (F.DFLOAT, torch.float64)}[args.prec]
     x = torch.randn(s.N, s.K, dtype=dt, device="cuda")
     y = torch.empty_like(x)
     for _ in range(2):
@@ -407,7 +408,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--profile-apply", default=None, metavar="WORKLOAD",
                     help="only run the operator apply on WORKLOAD (for ncu captures); prints one line")
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "dfloat"])
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -59,7 +59,12 @@ extern "C" {
 
 #define FESTUNG_FP64      0   /* operator and Krylov iterations in FP64                   */
 #define FESTUNG_FP32      1   /* FP32 operator (FP32 copies of geometry, tables, D)       */
-#define FESTUNG_MIXED     2   /* step only: FP32 inner Krylov, FP64 residual refinement   */
+#define FESTUNG_MIXED     2   /* step only: FP32 inner Krylov, refinement on residuals
+                                 evaluated in double-float arithmetic (FESTUNG_DFLOAT)    */
+#define FESTUNG_DFLOAT    3   /* apply only: FP64 arrays; the operator is evaluated in
+                                 double-float arithmetic (value = hi + lo, two FP32
+                                 numbers, about 48 significant bits) from double-float
+                                 copies of D, the geometry and the tables               */
 
 #define FESTUNG_BDR_INTERIOR  0
 #define FESTUNG_BDR_DIRICHLET 1
@@ -144,8 +149,12 @@ int festung_set_state(festung_ctx *ctx, const double *C, int is_samples, int loc
 int festung_get_state(const festung_ctx *ctx, double *C, int loc);
 
 /* y = S x of (E1) with the current D and time step dt (dt = 0 gives y = M x).
- *   x, y  device arrays in the N x K layout, FP64 (prec = FESTUNG_FP64) or FP32
- *         (prec = FESTUNG_FP32); x and y must not overlap; 16-byte aligned.
+ *   x, y  device arrays in the N x K layout, FP64 (prec = FESTUNG_FP64 or
+ *         FESTUNG_DFLOAT) or FP32 (prec = FESTUNG_FP32); x and y must not overlap;
+ *         16-byte aligned.
+ * FESTUNG_DFLOAT evaluates the operator in double-float arithmetic (the residual of
+ * FESTUNG_MIXED steps): x is split into pairs of FP32 values, the result is rounded
+ * back to FP64; error a few units of 2^-48 times |S| |x| (elementwise magnitudes).
  * Boundary data does not enter (S is the homogeneous operator). Runs on the
  * context's stream and returns without synchronising. */
 int festung_apply(festung_ctx *ctx, const void *x, void *y, int prec, double dt);

@@ -50,34 +50,6 @@ void launch_apply_twopass<double>(const festung_ctx *c, const double *x, double 
     });
 }
 
-// Copy the reference tables of the context's (N, R2, R1) into the constant bank.  The
-// tables depend only on p and the quadrature, so every context of the same shape
-// writes identical values; the copy is done once per process and shape.
-cudaError_t upload_tables_f64(const festung_ctx *c) {
-    cudaError_t err = cudaSuccess;
-    dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
-        constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
-        static bool done = false;
-        if (done) return;
-        CTab<double, N, R2, R1> h;
-        const HostTables &t = c->tab;
-        for (int i = 0; i < R2 * N; ++i) {
-            h.phiQ[i] = (double)t.phiQ[i];
-            h.gw1[i] = (double)t.gw1[i];
-            h.gw2[i] = (double)t.gw2[i];
-        }
-        for (int i = 0; i < N * N; ++i) {
-            h.H1[i] = (double)t.H1[i];
-            h.H2[i] = (double)t.H2[i];
-        }
-        for (int i = 0; i < 3 * R1 * N; ++i) {
-            h.phiE[i] = (double)t.phiE[i];
-            h.wphiE[i] = (double)t.wphiE[i];
-        }
-        err = cudaMemcpyToSymbol(c_tab<double, N, R2, R1>, &h, sizeof(h));
-        if (err == cudaSuccess) done = true;
-    });
-    return err;
-}
+cudaError_t upload_tables_f64(const festung_ctx *c) { return upload_ctab<double>(c); }
 
 }  // namespace festung

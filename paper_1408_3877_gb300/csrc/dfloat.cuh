@@ -1,0 +1,65 @@
+// Double-float arithmetic: a value is the unevaluated sum hi + lo of two floats with
+// |lo| <= ulp(hi) / 2, about 48 significant bits from FP32 instructions.
+//
+// The error-free transformations are the classical ones: the sum of two floats and
+// its exact rounding error (Knuth's two-sum, 6 operations; Dekker's fast two-sum, 3,
+// when |a| >= |b|) and the product with its exact error from one fused multiply-add.
+// Sums and products of double-floats follow Dekker (1971): combine the high parts
+// exactly, add the low-order terms, renormalise.  Each result carries an absolute
+// error of a few units of 2^-48 times the magnitudes of the operands, which is the
+// bound a residual b - S x needs (errors relative to |S| |x|, not to |S x|).
+//
+// Every operation goes through the __fadd_rn / __fmul_rn / __fmaf_rn intrinsics so the
+// compiler cannot contract or reassociate the sequences.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace festung {
+
+struct alignas(8) dfloat {
+    float hi, lo;
+    dfloat() = default;
+    __host__ __device__ constexpr dfloat(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ constexpr dfloat(int v) : hi((float)v), lo(0.0f) {}
+    __host__ __device__ explicit dfloat(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+    __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return dfloat(s, e);
+}
+
+// |a| >= |b| (or a == 0)
+__device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return dfloat(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+__device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
+    const dfloat s = df_two_sum(a.hi, b.hi);
+    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
+__device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
+
+__device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);  // exact error of the product of the high parts
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_fast_two_sum(p, e);
+}
+
+// Division only where the kernels divide once per triangle: through FP64.
+__device__ __forceinline__ dfloat operator/(dfloat a, dfloat b) { return dfloat((double)a / (double)b); }
+
+__device__ __forceinline__ dfloat &operator+=(dfloat &a, dfloat b) { return a = a + b; }
+__device__ __forceinline__ dfloat &operator-=(dfloat &a, dfloat b) { return a = a - b; }
+__device__ __forceinline__ dfloat &operator*=(dfloat &a, dfloat b) { return a = a * b; }
+
+}  // namespace festung

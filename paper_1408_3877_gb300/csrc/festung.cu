@@ -11,6 +11,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "internal.h"
 #include "krylov.cuh"
 #include "krylov_kernels.cuh"
@@ -66,6 +67,7 @@ struct Workspace {
     unsigned int *counter = nullptr;  // last-block counter of the reducing Krylov kernels
     double *part2 = nullptr;          // second partials buffer (CG: (r, r))
     double *res = nullptr, *h_res = nullptr;  // device / pinned host pair for residual norms
+    dfloat *xdf = nullptr, *ydf = nullptr;    // N x K double-float operand and result of the residual apply
     bool use_P = false;        // P is valid for the current step
     GraphCache g64, g32;
 };
@@ -170,7 +172,7 @@ template <typename T>
 __global__ void k_kr_init(int64_t K, int N, const T *b, const T *y, T *r, T *r0, T *p, T *v, double *part,
                           int reweight) {
     using A = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
-    A acc[2] = {A(0), A(0)};
+    A acc[3] = {A(0), A(0), A(0)};
     ELEM_LOOP(k) {
         for (int j = 0; j < N; ++j) {
             const int64_t i = j * K + k;
@@ -187,19 +189,24 @@ __global__ void k_kr_init(int64_t K, int N, const T *b, const T *y, T *r, T *r0,
             if (v) v[i] = T(0);
             acc[0] += (A)ri * (A)ri;
             acc[1] += (A)bi * (A)bi;
+            acc[2] += (A)(ri * wgt) * (A)ri;
         }
     }
-    block_partials<2>(acc, part);
+    block_partials<3>(acc, part);
 }
 
 __global__ void k_fin_init(KScal *sc, const double *part, int nblk, double tol) {
     const double r2 = sum_partials(part, 0, nblk);
     const double b2 = sum_partials(part, 1, nblk);
+    const double r0r = sum_partials(part, 2, nblk);
     if (threadIdx.x == 0) {
         sc->r2 = r2;
         sc->b2 = b2;
         sc->tol2 = tol * tol;
-        sc->rho = r2;
+        sc->rho = r0r;  // (r0, r); CG sets rho = (r, z) itself
+        sc->ss = r2;
+        sc->first = 1;
+        sc->pending = 0;
         sc->alpha = 1.0;
         sc->omega = 1.0;
         sc->beta = 0.0;
@@ -245,6 +252,28 @@ __global__ void k_residual64(int64_t n, const double *b, const double *y, double
         acc[1] += b[i] * b[i];
     }
     block_partials<2>(acc, part);
+}
+
+// r = b - y for a double-float y, with (r, r) and (b, b)
+__global__ void k_residual_df(int64_t n, const double *b, const dfloat *y, double *r, double *part) {
+    double acc[2] = {0.0, 0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double ri = b[i] - (double)y[i];
+        r[i] = ri;
+        acc[0] += ri * ri;
+        acc[1] += b[i] * b[i];
+    }
+    block_partials<2>(acc, part);
+}
+
+__global__ void k_to_df(int64_t n, const double *a, dfloat *b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = dfloat(a[i]);
+}
+
+__global__ void k_from_df(int64_t n, const dfloat *a, double *b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (double)a[i];
 }
 
 __global__ void k_fin_sums(double *out, const double *part, int nblk, int np) {
@@ -328,7 +357,10 @@ int ensure_ws(festung_ctx *c) {
         }
         Workspace &w = *c->ws;
         w.nblk = std::max(1, std::min(c->num_sms * 4, (int)((c->K + RED_THREADS - 1) / RED_THREADS)));
-        FCK(cudaMalloc(&w.part, sizeof(double) * 4 * w.nblk));
+        // partials of the reducing kernels: 4 per block of a reduction or per tile of a
+        // fused apply epilogue
+        const int64_t tiles = (c->K + c->TE - 1) / c->TE;
+        FCK(cudaMalloc(&w.part, sizeof(double) * 4 * std::max<int64_t>(w.nblk, tiles)));
         FCK(cudaMalloc(&w.scal, sizeof(KScal)));
         FCK(cudaMallocHost(&w.h_scal, sizeof(KScal)));
         FCK(cudaMalloc(&w.d_flags, sizeof(int) * 4));
@@ -367,14 +399,19 @@ void free_ctx_device(festung_ctx *c) {
         if (c->ws->res) cudaFree(c->ws->res);
         if (c->ws->h_res) cudaFreeHost(c->ws->h_res);
         if (c->ws->h_flags) cudaFreeHost(c->ws->h_flags);
+        if (c->ws->xdf) cudaFree(c->ws->xdf);
+        if (c->ws->ydf) cudaFree(c->ws->ydf);
         delete c->ws;
         c->ws = nullptr;
     }
-    void *ptrs[] = {c->dTab, c->fTab, c->dC, c->dD, c->dF, c->fD, c->dCD, c->dGN, c->dSamp, c->dCprev, c->dCprev2};
+    void *ptrs[] = {c->dTab, c->fTab, c->dC, c->dD, c->dF, c->fD, c->dCD, c->dGN, c->dSamp, c->dCprev, c->dCprev2,
+                    c->xD, c->xB, c->xTab};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     c->dTab = nullptr;
     c->fTab = nullptr;
+    c->xD = c->xB = c->xTab = nullptr;
+    c->xD_valid = false;
     c->dC = c->dD = c->dF = c->dCD = c->dGN = c->dSamp = c->dCprev = c->dCprev2 = nullptr;
     c->hist = 0;
     c->fD = nullptr;
@@ -441,21 +478,55 @@ bool ready(festung_ctx *c) {
 constexpr int CHUNK = 16;  // iterations per captured graph
 
 // preconditioned update kernels (templated on N)
+// s = r - alpha v, sh = P^{-1} s, (s, s)
 template <typename T>
-void launch_bicg_prec(festung_ctx *c, int mode, const T *r, T *pv, const T *v, T *out, cudaStream_t st) {
+void launch_bicg_s(festung_ctx *c, cudaStream_t st) {
     Workspace &w = *c->ws;
+    Vecs<T> &V = vecs<T>(c);
     const __nv_bfloat16 *P = w.use_P ? w.Pb : nullptr;
-    const T *inv = vecs<T>(c).inv;
     dispatch(c->N, c->R2, c->R1, [&](auto n_, auto, auto) {
         constexpr int N = decltype(n_)::value;
-        if (mode == 0)
-            k_bicg_prec<T, N, 0><<<w.nblk, RED_THREADS, 0, st>>>((int)c->K, r, pv, v, out, P, inv, w.part, w.scal,
-                                                                 w.counter);
-        else
-            k_bicg_prec<T, N, 1><<<w.nblk, RED_THREADS, 0, st>>>((int)c->K, r, pv, v, out, P, inv, w.part, w.scal,
-                                                                 w.counter);
+        k_bicg_s<T, N><<<w.nblk, RED_THREADS, 0, st>>>((int)c->K, V.r, V.s, V.v, V.sh, P, V.inv, w.part, w.scal,
+                                                       w.counter);
     });
+    ++c->launches;
 }
+
+// the owed update of x and r, p = r + beta (p - omega v), ph = P^{-1} p
+template <typename T>
+void launch_bicg_next(festung_ctx *c, cudaStream_t st) {
+    Workspace &w = *c->ws;
+    Vecs<T> &V = vecs<T>(c);
+    const __nv_bfloat16 *P = w.use_P ? w.Pb : nullptr;
+    dispatch(c->N, c->R2, c->R1, [&](auto n_, auto, auto) {
+        constexpr int N = decltype(n_)::value;
+        k_bicg_next<T, N><<<w.nblk, RED_THREADS, 0, st>>>((int)c->K, V.x, V.ph, V.sh, V.s, V.t, V.r, V.p, V.v, P,
+                                                          V.inv, w.scal);
+    });
+    ++c->launches;
+}
+
+}  // namespace
+
+namespace festung {
+
+template <>
+void launch_apply_bicg<double>(const festung_ctx *c, const double *x, double *y, double tau, int epi,
+                               const double *e1, const double *e2, double *part, KScal *sc, unsigned int *counter,
+                               const int *skip, cudaStream_t st) {
+    launch_apply<double>(c, x, y, nullptr, nullptr, tau, skip, st);
+    const int g = c->ws->nblk;
+    const int64_t n = c->K * c->N;
+    if (epi == FUSED_EPI_ALPHA)
+        k_bicg_epi<double, 1><<<g, RED_THREADS, 0, st>>>(n, y, e1, e2, part, sc, counter);
+    else
+        k_bicg_epi<double, 2><<<g, RED_THREADS, 0, st>>>(n, y, e1, e2, part, sc, counter);
+    ++c->launches;
+}
+
+}  // namespace festung
+
+namespace {
 
 template <typename T>
 void launch_cg_prec(festung_ctx *c, const T *r, T *z, int init, cudaStream_t st) {
@@ -479,14 +550,14 @@ void record_iterations(festung_ctx *c, int solver, T tau, cudaStream_t st) {
     const int *skip = &w.scal->done;
     for (int it = 0; it < CHUNK; ++it) {
         if (solver == FESTUNG_SOLVER_BICGSTAB) {
-            launch_bicg_prec<T>(c, 0, V.r, V.p, V.v, V.ph, st);                 // p, ph = P^{-1} p
-            launch_apply<T>(c, V.ph, V.v, V.Z1, V.Z2, tau, skip, st);           // v = S ph
-            k_bicg_alpha<T><<<g, RED_THREADS, 0, st>>>(n, V.r0, V.v, w.part, w.scal, w.counter);
-            launch_bicg_prec<T>(c, 1, V.r, V.s, V.v, V.sh, st);                 // s, sh = P^{-1} s
-            launch_apply<T>(c, V.sh, V.t, V.Z1, V.Z2, tau, skip, st);           // t = S sh
-            k_bicg_omega<T><<<g, RED_THREADS, 0, st>>>(n, V.t, V.s, w.part, w.scal, w.counter);
-            k_bicg_xr<T><<<g, RED_THREADS, 0, st>>>(n, V.x, V.ph, V.sh, V.s, V.t, V.r, V.r0, w.part, w.scal,
-                                                    w.counter);
+            // four launches per iteration: the reductions ride on the applies, and the
+            // updates of x and r on the next iteration's first kernel
+            launch_bicg_next<T>(c, st);                                          // (x, r), p, ph = P^{-1} p
+            launch_apply_bicg<T>(c, V.ph, V.v, tau, FUSED_EPI_ALPHA, V.r0, nullptr, w.part, w.scal, w.counter,
+                                 skip, st);                                      // v = S ph, alpha
+            launch_bicg_s<T>(c, st);                                             // s, sh = P^{-1} s
+            launch_apply_bicg<T>(c, V.sh, V.t, tau, FUSED_EPI_OMEGA, V.s, V.r0, w.part, w.scal, w.counter,
+                                 skip, st);                                      // t = S sh, omega, beta
         } else {
             // CG: p (search), v = S p, s = z
             launch_apply<T>(c, V.p, V.v, V.Z1, V.Z2, tau, skip, st);
@@ -568,6 +639,9 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
                 if (h.sconv) {
                     k_axpy_alpha<T><<<g, RED_THREADS, 0, st>>>(K, N, V.x, V.ph, w.scal); ++c->launches;
                     FCK(cudaGetLastError());
+                } else if (h.pending) {
+                    k_bicg_finish<T><<<g, RED_THREADS, 0, st>>>(K * N, V.x, V.ph, V.sh, w.scal); ++c->launches;
+                    FCK(cudaGetLastError());
                 }
                 total += h.iter;
                 *r2 = h.r2;
@@ -593,6 +667,10 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
                 break;
             }
             if (total + h.iter >= max_iter) {
+                if (h.pending) {
+                    k_bicg_finish<T><<<g, RED_THREADS, 0, st>>>(K * N, V.x, V.ph, V.sh, w.scal); ++c->launches;
+                    FCK(cudaGetLastError());
+                }
                 total += h.iter;
                 *r2 = h.r2;
                 *b2 = h.b2;
@@ -612,6 +690,27 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
 }  // namespace
 
 namespace {
+
+// y = S x in double-float arithmetic for an FP64 x (N x K): x is split into
+// double-floats, the result is left in ws->ydf and, if y is given, written back as
+// FP64.
+int apply_df(festung_ctx *c, const double *x, double *y, double dt, cudaStream_t st) {
+    Workspace &w = *c->ws;
+    const int64_t KN = c->K * c->N;
+    if (!w.xdf) FCK(cudaMalloc(&w.xdf, KN * sizeof(dfloat)));
+    if (!w.ydf) FCK(cudaMalloc(&w.ydf, KN * sizeof(dfloat)));
+    if (!c->xD_valid) {
+        k_to_df<<<small_grid(KN, c), 256, 0, st>>>(KN, c->dD, c->xD); ++c->launches;
+        c->xD_valid = true;
+    }
+    k_to_df<<<small_grid(KN, c), 256, 0, st>>>(KN, x, w.xdf); ++c->launches;
+    launch_apply_df(c, w.xdf, w.ydf, dt, st);
+    if (y) {
+        k_from_df<<<small_grid(KN, c), 256, 0, st>>>(KN, w.ydf, y); ++c->launches;
+    }
+    FCK(cudaGetLastError());
+    return FESTUNG_OK;
+}
 
 // Tiles of te consecutive triangles of the internal order: halo lists and the
 // shared-memory slots of every neighbour, uploaded to the device (the previous tiling
@@ -808,6 +907,20 @@ int festung_setup(festung_ctx *c, int p, int quad_order, double eta) {
     FCK(cudaMemcpy(c->fTab, hf.data(), o.total * sizeof(float), cudaMemcpyHostToDevice));
     FCK(upload_tables_f64(c));
     FCK(upload_tables_f32(c));
+    FCK(upload_tables_f32_kr(c));
+    FCK(upload_tables_df(c));
+    {
+        // double-float copies of the tables and the geometry (residual applies)
+        std::vector<dfloat> hx(o.total);
+        for (int i = 0; i < o.total; ++i) hx[i] = dfloat(h[i]);
+        FCK(cudaMalloc(&c->xTab, o.total * sizeof(dfloat)));
+        FCK(cudaMemcpy(c->xTab, hx.data(), o.total * sizeof(dfloat), cudaMemcpyHostToDevice));
+        FCK(cudaMalloc(&c->xB, 4 * c->K * sizeof(dfloat)));
+        k_to_df<<<small_grid(4 * c->K, c), 256>>>(4 * c->K, c->dB, c->xB); ++c->launches;
+        FCK(cudaGetLastError());
+        FCK(cudaMalloc(&c->xD, c->K * c->N * sizeof(dfloat)));
+        c->xD_valid = false;
+    }
     if (int rc = choose_tiles(c)) return rc;
     FCK(cudaMalloc(&c->dC, K * N * sizeof(double)));
     FCK(cudaMalloc(&c->dD, K * N * sizeof(double)));
@@ -892,6 +1005,7 @@ int festung_set_coeff(festung_ctx *c, const double *d_samples, int loc) {
     }
     k_commit_coeff<<<small_grid(KN, c), 256, 0, c->stream>>>(KN, w.scratch64, c->dD, c->fD); ++c->launches;
     FCK(cudaGetLastError());
+    c->xD_valid = false;
     // S is symmetric iff d_h is elementwise constant (always so for p = 0)
     c->symmetric = (c->p == 0) || !(flags & 4);
     return FESTUNG_OK;
@@ -993,13 +1107,16 @@ int festung_get_state(const festung_ctx *cc, double *C, int loc) {
 
 int festung_apply(festung_ctx *c, const void *x, void *y, int prec, double dt) {
     if (!ready(c)) return c ? FESTUNG_ESTATE : FESTUNG_EINVAL;
-    if (!x || !y || x == y || !(dt >= 0.0) || (prec != FESTUNG_FP64 && prec != FESTUNG_FP32)) {
+    if (!x || !y || x == y || !(dt >= 0.0) ||
+        (prec != FESTUNG_FP64 && prec != FESTUNG_FP32 && prec != FESTUNG_DFLOAT)) {
         c->err = "bad apply arguments";
         return FESTUNG_EINVAL;
     }
     int rc = ensure_ws(c);
     if (rc) return rc;
-    if (prec == FESTUNG_FP64) {
+    if (prec == FESTUNG_DFLOAT) {
+        if ((rc = apply_df(c, (const double *)x, (double *)y, dt, c->stream))) return rc;
+    } else if (prec == FESTUNG_FP64) {
         if ((rc = alloc_vecs<double>(c, c->ws->d, false))) return rc;
         launch_apply<double>(c, (const double *)x, (double *)y, c->ws->d.Z1, c->ws->d.Z2, dt, nullptr, c->stream);
     } else {
@@ -1083,9 +1200,16 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
     bool conv = false;
     double relres = 0.0;
     // FP64 residual r = b - S x and its norms (rn, bn)
+    // (FESTUNG_MIXED: S x in double-float arithmetic, about 48 significant bits)
+    const bool df_residual = o.prec == FESTUNG_MIXED;
     auto residual64 = [&](double *rn, double *bn) -> int {
-        launch_apply<double>(c, V.x, V.t, V.Z1, V.Z2, dt, nullptr, st);
-        k_residual64<<<w.nblk, RED_THREADS, 0, st>>>(KN, V.b, V.t, V.r, w.part);
+        if (df_residual) {
+            if ((rc = apply_df(c, V.x, nullptr, dt, st))) return rc;
+            k_residual_df<<<w.nblk, RED_THREADS, 0, st>>>(KN, V.b, w.ydf, V.r, w.part);
+        } else {
+            launch_apply<double>(c, V.x, V.t, V.Z1, V.Z2, dt, nullptr, st);
+            k_residual64<<<w.nblk, RED_THREADS, 0, st>>>(KN, V.b, V.t, V.r, w.part);
+        }
         k_fin_sums<<<1, 1024, 0, st>>>(W1, w.part, w.nblk, 2);
         c->launches += 2;
         double h[2];

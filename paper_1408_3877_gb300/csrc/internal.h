@@ -91,6 +91,7 @@ struct TableOffsets {
 TableOffsets table_offsets(int N, int R2, int R1);
 
 struct Workspace;  // Krylov vectors
+struct dfloat;     // double-float value (dfloat.cuh)
 
 }  // namespace festung
 
@@ -126,6 +127,11 @@ struct festung_ctx {
     int hist = 0;                                  // number of valid previous states (0..2)
     double dt_prev = 0.0, dt_prev2 = 0.0;
     float *fD = nullptr;
+    // double-float copies for the residual of the mixed-precision refinement
+    festung::dfloat *xD = nullptr;    // N x K, refreshed from dD when xD_valid is false
+    festung::dfloat *xB = nullptr;    // 4 x K geometry
+    festung::dfloat *xTab = nullptr;  // tables, layout table_offsets
+    bool xD_valid = false;
     double *dCD = nullptr, *dGN = nullptr;  // K x 3 x R1 boundary samples
     double *dSamp = nullptr;                // K x R2 staging for projections
     bool symmetric = true;

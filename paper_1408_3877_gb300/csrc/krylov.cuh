@@ -12,10 +12,21 @@ struct KScal {
     double rho, alpha, omega, beta;
     double r2, b2, tol2;
     double den;
+    double ss;    // BiCGStab: (s, s) of the current iteration
     int done, breakdown, iter, sconv;
+    int first;    // BiCGStab: no update of x and r is owed from a previous iteration
+    int pending;  // BiCGStab: x += alpha ph + omega sh, r = s - omega t still to apply
 };
 
 constexpr int RED_THREADS = 256;
+
+// Reductions of a BiCGStab step fused into the end of an operator apply y = S x:
+//   FUSED_EPI_NONE   none;
+//   FUSED_EPI_ALPHA  y = v:  (r0, v) -> alpha;
+//   FUSED_EPI_OMEGA  y = t:  (t, s), (t, t), (r0, s), (r0, t) -> omega, rho, beta.
+constexpr int FUSED_EPI_NONE = 0;
+constexpr int FUSED_EPI_ALPHA = 1;
+constexpr int FUSED_EPI_OMEGA = 2;
 
 // Block sum of up to 3 values; thread 0 writes part[p * nblk + blockIdx.x].
 template <int NP>

@@ -49,6 +49,74 @@ __device__ __forceinline__ bool last_block(unsigned int *counter) {
     return amlast;
 }
 
+// Block sum of NP values for any block size (a multiple of 32, at most 1024); thread 0
+// of warp 0 writes part[p * gridDim.x + blockIdx.x].
+template <int NP, typename A>
+__device__ __forceinline__ void block_partials_any(A (&v)[NP], double *part) {
+    __shared__ double sh[NP][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)((blockDim.x + 31) >> 5);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        A a = v[p];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) sh[p][wid] = (double)a;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            double a = lane < nw ? sh[p][lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) part[p * gridDim.x + blockIdx.x] = a;
+        }
+    }
+}
+
+// Scalar updates of BiCGStab, run by one thread of the last block of a reduction.
+// After v = S ph: alpha = rho / (r0, v).  The update owed from the previous iteration
+// has been applied by now (k_bicg_next).
+__device__ __forceinline__ void bicg_alpha_scalars(double r0v, KScal *sc) {
+    if (!(fabs(r0v) > 1e-300) || !isfinite(r0v)) {
+        sc->breakdown = 1;
+        sc->done = 1;
+    } else {
+        sc->alpha = sc->rho / r0v;
+    }
+    sc->first = 0;
+    sc->pending = 0;
+}
+
+// After t = S sh: omega = (t, s) / (t, t); the next residual r = s - omega t is not
+// formed here, its dot products follow from those of s and t:
+//   (r0, r) = (r0, s) - omega (r0, t),  (r, r) = (s, s) - omega (t, s);
+// beta = ((r0, r) / rho) (alpha / omega).  The updates of x and r are left to the
+// next iteration's k_bicg_next (or to k_bicg_finish once the solve stops).
+__device__ __forceinline__ void bicg_omega_scalars(double ts, double tt, double r0s, double r0t, KScal *sc) {
+    if (!(tt > 0.0) || !isfinite(ts) || ts == 0.0 || !isfinite(r0s) || !isfinite(r0t)) {
+        sc->breakdown = 1;
+        sc->done = 1;
+        return;
+    }
+    const double omega = ts / tt;
+    const double rho_new = r0s - omega * r0t;
+    const double r2 = fmax(0.0, sc->ss - omega * ts);
+    sc->omega = omega;
+    sc->iter += 1;
+    sc->r2 = r2;
+    sc->pending = 1;
+    if (r2 <= sc->tol2 * sc->b2) {
+        sc->done = 1;
+    } else if (!(fabs(rho_new) > 1e-300) || !isfinite(rho_new)) {
+        sc->breakdown = 1;
+        sc->done = 1;
+    } else {
+        sc->beta = (rho_new / sc->rho) * (sc->alpha / omega);
+        sc->rho = rho_new;
+    }
+}
+
 // Sum of slot p of the partials of a grid of nblk blocks, read past L1 (the partials
 // were written by other SMs); called by all threads of one block.
 __device__ __forceinline__ double sum_partials_cg(const double *part, int p, int nblk) {
@@ -115,171 +183,140 @@ __device__ __forceinline__ void st16(T *p, int64_t i, const V16<T> &r) {
 // BiCGStab (right preconditioner P^{-1} = block-Jacobi inverse, or 1/(2|T_k|))
 // ---------------------------------------------------------------------------
 
-// MODE 0: p = r + beta (p - omega v); out = P^{-1} p.
-// MODE 1: s = r - alpha v; out = P^{-1} s; (s, s) -> last block: converged on s?
-template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(RED_THREADS) k_bicg_prec(int K, const T *__restrict__ r, T *__restrict__ pv,
-                                                           const T *__restrict__ v, T *__restrict__ out,
-                                                           const __nv_bfloat16 *__restrict__ P,
-                                                           const T *__restrict__ inv, double *part, KScal *sc,
-                                                           unsigned int *counter) {
+// s = r - alpha v; sh = P^{-1} s; (s, s) -> last block: converged on s?
+template <typename T, int N>
+__global__ void __launch_bounds__(RED_THREADS) k_bicg_s(int K, const T *__restrict__ r, T *__restrict__ s,
+                                                        const T *__restrict__ v, T *__restrict__ sh,
+                                                        const __nv_bfloat16 *__restrict__ P,
+                                                        const T *__restrict__ inv, double *part, KScal *sc,
+                                                        unsigned int *counter) {
     if (sc->done) return;
-    const T beta = (T)sc->beta, omega = (T)sc->omega, alpha = (T)sc->alpha;
+    const T alpha = (T)sc->alpha;
     Acc<T> acc[1] = {Acc<T>(0)};
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
         T q[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             const int i = j * K + k;
-            const T qi = MODE == 0 ? r[i] + beta * (pv[i] - omega * v[i]) : r[i] - alpha * v[i];
-            pv[i] = qi;
+            const T qi = r[i] - alpha * v[i];
+            s[i] = qi;
             q[j] = qi;
-            if (MODE == 1) acc[0] += (Acc<T>)qi * (Acc<T>)qi;
+            acc[0] += (Acc<T>)qi * (Acc<T>)qi;
         }
         if (P) {
             T y[N];
             block_matvec<T, N>(P, K, k, q, y);
 #pragma unroll
-            for (int i = 0; i < N; ++i) out[i * K + k] = y[i];
+            for (int i = 0; i < N; ++i) sh[i * K + k] = y[i];
         } else {
             const T iv = inv[k];
 #pragma unroll
-            for (int i = 0; i < N; ++i) out[i * K + k] = q[i] * iv;
+            for (int i = 0; i < N; ++i) sh[i * K + k] = q[i] * iv;
         }
     }
-    if (MODE == 1) {
-        block_partials<1>(acc, part);
-        if (last_block(counter)) {
-            const double s2 = sum_partials_cg(part, 0, gridDim.x);
-            if (threadIdx.x == 0) {
-                if (s2 <= sc->tol2 * sc->b2) {
-                    sc->sconv = 1;
-                    sc->r2 = s2;
-                    sc->iter += 1;
-                    sc->done = 1;
-                }
-                *counter = 0;
-            }
-        }
-    }
-}
-
-// (r0, v) -> alpha = rho / (r0, v)
-template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) k_bicg_alpha(int64_t n, const T *__restrict__ r0,
-                                                            const T *__restrict__ v, double *part, KScal *sc,
-                                                            unsigned int *counter) {
-    if (sc->done) return;
-    Acc<T> acc[1] = {Acc<T>(0)};
-    FLAT_LOOP(n, {
-        if (w > 1) {
-            const V16<T> a = ld16(r0, i0), b = ld16(v, i0);
-            for (int e = 0; e < w; ++e) acc[0] += (Acc<T>)a.v[e] * (Acc<T>)b.v[e];
-        } else {
-            acc[0] += (Acc<T>)r0[i0] * (Acc<T>)v[i0];
-        }
-    })
     block_partials<1>(acc, part);
     if (last_block(counter)) {
-        const double den = sum_partials_cg(part, 0, gridDim.x);
+        const double s2 = sum_partials_cg(part, 0, gridDim.x);
         if (threadIdx.x == 0) {
-            if (!(fabs(den) > 1e-300) || !isfinite(den)) {
-                sc->breakdown = 1;
+            sc->ss = s2;
+            if (s2 <= sc->tol2 * sc->b2) {
+                sc->sconv = 1;
+                sc->r2 = s2;
+                sc->iter += 1;
                 sc->done = 1;
-            } else {
-                sc->alpha = sc->rho / den;
             }
             *counter = 0;
         }
     }
 }
 
-// (t, s), (t, t) -> omega = (t, s) / (t, t)
-template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) k_bicg_omega(int64_t n, const T *__restrict__ t,
-                                                            const T *__restrict__ s, double *part, KScal *sc,
-                                                            unsigned int *counter) {
+// Start of a BiCGStab iteration: the update owed from the previous iteration,
+// x += alpha ph + omega sh and r = s - omega t (none in the first iteration of a
+// solve), then p = r + beta (p - omega v) and ph = P^{-1} p.
+template <typename T, int N>
+__global__ void __launch_bounds__(RED_THREADS) k_bicg_next(int K, T *__restrict__ x, T *ph,
+                                                           const T *__restrict__ sh, const T *__restrict__ s,
+                                                           const T *__restrict__ t, T *__restrict__ r,
+                                                           T *__restrict__ pv, const T *__restrict__ v,
+                                                           const __nv_bfloat16 *__restrict__ P,
+                                                           const T *__restrict__ inv, const KScal *sc) {
     if (sc->done) return;
-    Acc<T> acc[2] = {Acc<T>(0), Acc<T>(0)};
-    FLAT_LOOP(n, {
-        if (w > 1) {
-            const V16<T> a = ld16(t, i0), b = ld16(s, i0);
-            for (int e = 0; e < w; ++e) {
-                acc[0] += (Acc<T>)a.v[e] * (Acc<T>)b.v[e];
-                acc[1] += (Acc<T>)a.v[e] * (Acc<T>)a.v[e];
+    const bool first = sc->first != 0;
+    const T alpha = (T)sc->alpha, omega = (T)sc->omega, beta = (T)sc->beta;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+        T q[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const int i = j * K + k;
+            T ri;
+            if (first) {
+                ri = r[i];
+            } else {
+                x[i] += alpha * ph[i] + omega * sh[i];
+                ri = s[i] - omega * t[i];
+                r[i] = ri;
             }
+            q[j] = ri + beta * (pv[i] - omega * v[i]);
+            pv[i] = q[j];
+        }
+        if (P) {
+            T y[N];
+            block_matvec<T, N>(P, K, k, q, y);
+#pragma unroll
+            for (int i = 0; i < N; ++i) ph[i * K + k] = y[i];
         } else {
-            acc[0] += (Acc<T>)t[i0] * (Acc<T>)s[i0];
-            acc[1] += (Acc<T>)t[i0] * (Acc<T>)t[i0];
+            const T iv = inv[k];
+#pragma unroll
+            for (int i = 0; i < N; ++i) ph[i * K + k] = q[i] * iv;
         }
-    })
-    block_partials<2>(acc, part);
+    }
+}
+
+// The reductions of FUSED_EPI_ALPHA / FUSED_EPI_OMEGA as a pass of their own over
+// y = v or t (used where the apply has no fused epilogue).
+template <typename T, int EPI>
+__global__ void __launch_bounds__(RED_THREADS) k_bicg_epi(int64_t n, const T *__restrict__ y,
+                                                          const T *__restrict__ e1, const T *__restrict__ e2,
+                                                          double *part, KScal *sc, unsigned int *counter) {
+    if (sc->done) return;
+    constexpr int ND = EPI == 2 ? 4 : 1;
+    Acc<T> dots[ND];
+#pragma unroll
+    for (int q = 0; q < ND; ++q) dots[q] = Acc<T>(0);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const Acc<T> yi = (Acc<T>)y[i];
+        if constexpr (EPI == 1) {
+            dots[0] += (Acc<T>)e1[i] * yi;
+        } else {
+            const Acc<T> si = (Acc<T>)e1[i], ri = (Acc<T>)e2[i];
+            dots[0] += yi * si;
+            dots[1] += yi * yi;
+            dots[2] += ri * si;
+            dots[3] += ri * yi;
+        }
+    }
+    block_partials_any<ND>(dots, part);
     if (last_block(counter)) {
-        const double ts = sum_partials_cg(part, 0, gridDim.x);
-        const double tt = sum_partials_cg(part, 1, gridDim.x);
+        double sum[ND];
+#pragma unroll
+        for (int q = 0; q < ND; ++q) sum[q] = sum_partials_cg(part, q, gridDim.x);
         if (threadIdx.x == 0) {
-            if (!(tt > 0.0) || !isfinite(ts) || ts == 0.0) {
-                sc->breakdown = 1;
-                sc->done = 1;
-            } else {
-                sc->omega = ts / tt;
-            }
+            if constexpr (EPI == 1)
+                bicg_alpha_scalars(sum[0], sc);
+            else
+                bicg_omega_scalars(sum[0], sum[1], sum[2], sum[3], sc);
             *counter = 0;
         }
     }
 }
 
-// x += alpha ph + omega sh; r = s - omega t; (r0, r), (r, r) -> next rho, beta, convergence
+// After the last iteration of a solve: the owed x += alpha ph + omega sh.
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) k_bicg_xr(int64_t n, T *__restrict__ x, const T *__restrict__ ph,
-                                                         const T *__restrict__ sh, const T *__restrict__ s,
-                                                         const T *__restrict__ t, T *__restrict__ r,
-                                                         const T *__restrict__ r0, double *part, KScal *sc,
-                                                         unsigned int *counter) {
-    if (sc->done) return;
+__global__ void __launch_bounds__(RED_THREADS) k_bicg_finish(int64_t n, T *__restrict__ x, const T *__restrict__ ph,
+                                                             const T *__restrict__ sh, const KScal *sc) {
     const T alpha = (T)sc->alpha, omega = (T)sc->omega;
-    Acc<T> acc[2] = {Acc<T>(0), Acc<T>(0)};
-    FLAT_LOOP(n, {
-        if (w > 1) {
-            V16<T> xv = ld16(x, i0);
-            const V16<T> pa = ld16(ph, i0), sa = ld16(sh, i0), sv = ld16(s, i0), tv = ld16(t, i0),
-                         rz = ld16(r0, i0);
-            V16<T> rv;
-            for (int e = 0; e < w; ++e) {
-                xv.v[e] += alpha * pa.v[e] + omega * sa.v[e];
-                rv.v[e] = sv.v[e] - omega * tv.v[e];
-                acc[0] += (Acc<T>)rz.v[e] * (Acc<T>)rv.v[e];
-                acc[1] += (Acc<T>)rv.v[e] * (Acc<T>)rv.v[e];
-            }
-            st16(x, i0, xv);
-            st16(r, i0, rv);
-        } else {
-            x[i0] += alpha * ph[i0] + omega * sh[i0];
-            const T ri = s[i0] - omega * t[i0];
-            r[i0] = ri;
-            acc[0] += (Acc<T>)r0[i0] * (Acc<T>)ri;
-            acc[1] += (Acc<T>)ri * (Acc<T>)ri;
-        }
-    })
-    block_partials<2>(acc, part);
-    if (last_block(counter)) {
-        const double rho_new = sum_partials_cg(part, 0, gridDim.x);
-        const double r2 = sum_partials_cg(part, 1, gridDim.x);
-        if (threadIdx.x == 0) {
-            sc->iter += 1;
-            sc->r2 = r2;
-            if (r2 <= sc->tol2 * sc->b2) {
-                sc->done = 1;
-            } else if (!(fabs(rho_new) > 1e-300) || !isfinite(rho_new)) {
-                sc->breakdown = 1;
-                sc->done = 1;
-            } else {
-                sc->beta = (rho_new / sc->rho) * (sc->alpha / sc->omega);
-                sc->rho = rho_new;
-            }
-            *counter = 0;
-        }
-    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += alpha * ph[i] + omega * sh[i];
 }
 
 // ---------------------------------------------------------------------------

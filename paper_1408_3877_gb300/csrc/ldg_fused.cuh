@@ -11,6 +11,8 @@
 // The flux unknowns never leave the chip, and every trace is evaluated once per slot.
 #pragma once
 
+#include "dispatch.h"
+#include "krylov_kernels.cuh"
 #include "ldg_kernels.cuh"
 
 namespace festung {
@@ -31,8 +33,47 @@ struct CTab {
     T wphiE[3 * R1 * N];
 };
 
+// One copy of the tables per translation unit (internal linkage): every unit that
+// launches fused kernels fills its own copy with upload_ctab, which has internal
+// linkage too, so the linker cannot merge the units' instantiations.
+namespace {
 template <typename T, int N, int R2, int R1>
 __constant__ CTab<T, N, R2, R1> c_tab;
+
+// Copy the reference tables of the context's (N, R2, R1) into this translation unit's
+// constant bank, once per device.  The tables depend only on p and the quadrature, so
+// every context of the same shape writes identical values.
+template <typename T>
+cudaError_t upload_ctab(const festung_ctx *c) {
+    cudaError_t err = cudaSuccess;
+    int dev = 0;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+    dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
+        constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
+        static unsigned long long done = 0;  // bit d: device d holds the tables
+        const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+        if (done & bit) return;
+        CTab<T, N, R2, R1> h;
+        const HostTables &t = c->tab;
+        for (int i = 0; i < R2 * N; ++i) {
+            h.phiQ[i] = (T)t.phiQ[i];
+            h.gw1[i] = (T)t.gw1[i];
+            h.gw2[i] = (T)t.gw2[i];
+        }
+        for (int i = 0; i < N * N; ++i) {
+            h.H1[i] = (T)t.H1[i];
+            h.H2[i] = (T)t.H2[i];
+        }
+        for (int i = 0; i < 3 * R1 * N; ++i) {
+            h.phiE[i] = (T)t.phiE[i];
+            h.wphiE[i] = (T)t.wphiE[i];
+        }
+        err = cudaMemcpyToSymbol(c_tab<T, N, R2, R1>, &h, sizeof(h));
+        if (err == cudaSuccess) done |= bit;
+    });
+    return err;
+}
+}  // namespace
 
 // own-edge trace with a compile-time edge index (constant-bank table)
 template <typename T, int N, int R2, int R1, int n>
@@ -68,7 +109,7 @@ template <typename T, int R1>
 __device__ __forceinline__ void tr_store(T *tr, int f, int n, int slot, int NS, const T (&v)[R1]) {
     using L = TraceLayout<T, R1>;
     if constexpr (L::vec) {
-        T buf[L::RP];
+        alignas(16) T buf[L::RP];
 #pragma unroll
         for (int r = 0; r < L::RP; ++r) buf[r] = r < R1 ? v[r] : T(0);
         float4 *dst = reinterpret_cast<float4 *>(tr + ((size_t)(f * 3 + n) * NS + slot) * L::RP);
@@ -84,7 +125,7 @@ template <typename T, int R1>
 __device__ __forceinline__ void tr_load(const T *tr, int f, int n, int slot, int NS, T (&v)[R1]) {
     using L = TraceLayout<T, R1>;
     if constexpr (L::vec) {
-        T buf[L::RP];
+        alignas(16) T buf[L::RP];
         const float4 *src = reinterpret_cast<const float4 *>(tr + ((size_t)(f * 3 + n) * NS + slot) * L::RP);
 #pragma unroll
         for (int q = 0; q < L::nvec; ++q) reinterpret_cast<float4 *>(buf)[q] = src[q];
@@ -287,7 +328,9 @@ __device__ __forceinline__ void volume_smem(const T *phiQ_s, const T *gw1_s, con
                                             T (&acc)[N]) {
 #pragma unroll 1
     for (int r = 0; r < R2; ++r) {
-        T ph[NP], g1[NP], g2[NP];
+        alignas(16) T ph[NP];
+        alignas(16) T g1[NP];
+        alignas(16) T g2[NP];
 #pragma unroll
         for (int q = 0; q < NP * (int)sizeof(T) / 16; ++q) {
             reinterpret_cast<float4 *>(ph)[q] = reinterpret_cast<const float4 *>(phiQ_s + r * NP)[q];
@@ -328,12 +371,17 @@ bool allow_max_smem(Kern kernel) {
                                 optin - (int)fa.sharedSizeBytes) == cudaSuccess;
 }
 
-template <typename T, int N, int R2, int R1>
+// EPI: reductions fused into the end of the apply (FUSED_EPI_* in krylov.cuh; one
+// partial per block, the last block updates the scalars); e1, e2: r0 (ALPHA); s, r0
+// (OMEGA).
+template <typename T, int N, int R2, int R1, int EPI = FUSED_EPI_NONE>
 __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_apply_fused(
     const T *__restrict__ X, T *__restrict__ Y, const T *__restrict__ Dc, const T *__restrict__ Bg,
     const int32_t *__restrict__ nbr, const int16_t *__restrict__ slotg, const int32_t *__restrict__ halo_ptr,
     const int32_t *__restrict__ halo, const int16_t *__restrict__ halo_slot, int64_t K, int TE, int NS, T tau,
-    T eta, T mass, const T *__restrict__ tabg, const int *__restrict__ skip) {
+    T eta, T mass, const T *__restrict__ tabg, const int *__restrict__ skip, const T *__restrict__ e1 = nullptr,
+    const T *__restrict__ e2 = nullptr, double *part = nullptr, KScal *sc = nullptr,
+    unsigned int *counter = nullptr) {
     constexpr bool kBigVolume = R2 * N > 150;
     constexpr int NP = ((N * (int)sizeof(T) + 15) / 16) * 16 / (int)sizeof(T);
     constexpr int VOL = kBigVolume ? 3 * R2 * NP : 4;
@@ -388,24 +436,58 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
         }
     }
     __syncthreads();
-    if (i >= cnt) return;
-    // B: volume and edge terms of the tile triangles
-    const int k = start + i;
-    const T b11 = Bg[k], b12 = Bg[Ki + k], b21 = Bg[2 * Ki + k], b22 = Bg[3 * Ki + k];
-    T acc[N];
+    using A = Acc<T>;
+    constexpr int ND = EPI == FUSED_EPI_OMEGA ? 4 : 1;
+    A dots[ND];
 #pragma unroll
-    for (int j = 0; j < N; ++j) acc[j] = T(0);
-    if constexpr (kBigVolume)
-        volume_smem<T, N, R2, NP>(vol_s, vol_s + R2 * NP, vol_s + 2 * R2 * NP, d, z1, z2, b11, b12, b21, b22, acc);
-    else
-        volume_const<T, N, R2, R1>(d, z1, z2, b11, b12, b21, b22, acc);
-    const int c0 = nbr[k], c1 = nbr[Ki + k], c2 = nbr[2 * Ki + k];
-    tile_edge<T, N, R2, R1, 0>(c0, c0 >= 0 ? slotg[k] : 0, tr, NS, i, b11, b12, b21, b22, eta, acc);
-    tile_edge<T, N, R2, R1, 1>(c1, c1 >= 0 ? slotg[Ki + k] : 0, tr, NS, i, b11, b12, b21, b22, eta, acc);
-    tile_edge<T, N, R2, R1, 2>(c2, c2 >= 0 ? slotg[2 * Ki + k] : 0, tr, NS, i, b11, b12, b21, b22, eta, acc);
-    const T det = b11 * b22 - b12 * b21;
+    for (int q = 0; q < ND; ++q) dots[q] = A(0);
+    if (i < cnt) {
+        // B: volume and edge terms of the tile triangles
+        const int k = start + i;
+        const T b11 = Bg[k], b12 = Bg[Ki + k], b21 = Bg[2 * Ki + k], b22 = Bg[3 * Ki + k];
+        T acc[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) Y[j * Ki + k] = mass * det * X[j * Ki + k] + tau * acc[j];
+        for (int j = 0; j < N; ++j) acc[j] = T(0);
+        if constexpr (kBigVolume)
+            volume_smem<T, N, R2, NP>(vol_s, vol_s + R2 * NP, vol_s + 2 * R2 * NP, d, z1, z2, b11, b12, b21, b22,
+                                      acc);
+        else
+            volume_const<T, N, R2, R1>(d, z1, z2, b11, b12, b21, b22, acc);
+        const int c0 = nbr[k], c1 = nbr[Ki + k], c2 = nbr[2 * Ki + k];
+        tile_edge<T, N, R2, R1, 0>(c0, c0 >= 0 ? slotg[k] : 0, tr, NS, i, b11, b12, b21, b22, eta, acc);
+        tile_edge<T, N, R2, R1, 1>(c1, c1 >= 0 ? slotg[Ki + k] : 0, tr, NS, i, b11, b12, b21, b22, eta, acc);
+        tile_edge<T, N, R2, R1, 2>(c2, c2 >= 0 ? slotg[2 * Ki + k] : 0, tr, NS, i, b11, b12, b21, b22, eta, acc);
+        const T det = b11 * b22 - b12 * b21;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const T yj = mass * det * X[j * Ki + k] + tau * acc[j];
+            Y[j * Ki + k] = yj;
+            if constexpr (EPI == FUSED_EPI_ALPHA) {
+                dots[0] += (A)e1[j * Ki + k] * (A)yj;
+            } else if constexpr (EPI == FUSED_EPI_OMEGA) {
+                const A sj = (A)e1[j * Ki + k], rj = (A)e2[j * Ki + k];
+                dots[0] += (A)yj * sj;
+                dots[1] += (A)yj * (A)yj;
+                dots[2] += rj * sj;
+                dots[3] += rj * (A)yj;
+            }
+        }
+    }
+    if constexpr (EPI != FUSED_EPI_NONE) {
+        block_partials_any<ND>(dots, part);
+        if (last_block(counter)) {
+            double sum[ND];
+#pragma unroll
+            for (int q = 0; q < ND; ++q) sum[q] = sum_partials_cg(part, q, gridDim.x);
+            if (threadIdx.x == 0) {
+                if constexpr (EPI == FUSED_EPI_ALPHA)
+                    bicg_alpha_scalars(sum[0], sc);
+                else
+                    bicg_omega_scalars(sum[0], sum[1], sum[2], sum[3], sc);
+                *counter = 0;
+            }
+        }
+    }
 }
 
 }  // namespace festung

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "krylov.cuh"
 
 namespace festung {
 
@@ -14,6 +15,19 @@ namespace festung {
 template <typename T>
 void launch_apply(const festung_ctx *c, const T *x, T *y, T *Z1, T *Z2, T tau, const int *skip,
                   cudaStream_t st);
+
+// y = S x followed by the reductions of one BiCGStab step, epi = 1 (FUSED_EPI_ALPHA):
+// e1 = r0, (r0, y) -> alpha; epi = 2 (FUSED_EPI_OMEGA): e1 = s, e2 = r0, (y, s), (y, y),
+// (r0, s), (r0, y) -> omega, rho, beta.  FP32: fused into the end of the apply (part
+// holds 4 partials per tile); FP64: a reduction pass of its own after the apply (part
+// holds 4 partials per block of that pass).
+template <typename T>
+void launch_apply_bicg(const festung_ctx *c, const T *x, T *y, T tau, int epi, const T *e1, const T *e2,
+                       double *part, KScal *sc, unsigned int *counter, const int *skip, cudaStream_t st);
+
+// y = S x in double-float arithmetic (dfloat.cuh) from the double-float copies of D,
+// the geometry and the tables (c->xD, c->xB, c->xTab); x, y: N x K double-floats.
+void launch_apply_df(const festung_ctx *c, const dfloat *x, dfloat *y, double tau, cudaStream_t st);
 
 // The same y = S x in two passes: k_flux writes Z^1, Z^2 to the N x K scratch arrays
 // Z1, Z2 in global memory, k_apply reads them back.
@@ -37,6 +51,8 @@ size_t fused_smem_bytes(const festung_ctx *c, int nslot, bool fp64);
 // fused apply kernels (FP64 and FP32 copies).
 cudaError_t upload_tables_f64(const festung_ctx *c);
 cudaError_t upload_tables_f32(const festung_ctx *c);
+cudaError_t upload_tables_f32_kr(const festung_ctx *c);
+cudaError_t upload_tables_df(const festung_ctx *c);
 
 // Block-Jacobi preconditioner: Pinv <- inverse of the N x N diagonal blocks of S (E1),
 // built in FP32 (scratch P) from the FP32 copies of geometry, tables and D, inverted in

@@ -3,6 +3,9 @@
 FP64: |y_gpu - y_oracle| is bounded by a small multiple of the rounding scale
 eps64 |S| |x| (the two sides sum the same quadrature terms in different orders).
 FP32: the same bound with eps32 (geometry, tables, D and x rounded to FP32).
+Double-float (FESTUNG_DFLOAT): the same bound with 2^-47 (value = hi + lo of two
+FP32 numbers; inputs split with 2^-48 relative error, sums and products with errors
+of a few units of 2^-48 of the operand magnitudes).
 """
 import numpy as np
 import pytest
@@ -14,6 +17,7 @@ pytestmark = pytest.mark.gpu
 
 EPS64 = np.finfo(np.float64).eps
 EPS32 = np.finfo(np.float32).eps
+EPSDF = 2.0 ** -47
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -37,7 +41,7 @@ def _case(n, p, mix, tau, quad_order=None, seed=1, jitter=0.2):
     y_or = S @ x
     out = {}
     order = s.element_order()
-    for prec, dt in ((F.FP64, torch.float64), (F.FP32, torch.float32)):
+    for prec, dt in ((F.FP64, torch.float64), (F.FP32, torch.float32), (F.DFLOAT, torch.float64)):
         xg = to_gpu_layout(x, L.K, L.N, dt, order)
         yg = torch.empty_like(xg)
         s.apply(xg, yg, tau, prec)
@@ -61,6 +65,8 @@ def test_apply_matches_oracle(p, mix):
     # element by element
     scale = np.abs(S) @ np.abs(x)
     assert np.all(np.abs(out[F.FP64] - y) <= 256 * EPS64 * (scale + 1e-300))
+    assert np.all(np.abs(out[F.DFLOAT] - y) <= 256 * EPSDF * (scale + 1e-300)), \
+        np.max(np.abs(out[F.DFLOAT] - y) / (scale + 1e-300))
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4])

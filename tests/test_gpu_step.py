@@ -72,7 +72,70 @@ def test_step_mixed_matches_oracle(p):
     err = np.linalg.norm(C - Co) / np.linalg.norm(Co)
     assert err <= 1e-9, (err, info)
     assert info["outer"] >= 2
+    assert info["fp64_iterations"] == 0, info  # the FP32 sweeps converge without the FP64 fallback
     s.close()
+
+
+@pytest.mark.parametrize("p", [1, 4])
+def test_mixed_residual_holds_in_fp64(p):
+    """The mixed step certifies its tolerance with residuals evaluated in double-float
+    arithmetic; its result must meet the same tolerance in FP64.  With C_ref from an
+    FP64 solve at 1e-14, b - S C = S (C_ref - C) + r_ref, and S (C_ref - C) is applied
+    in FP64 to the (small) difference."""
+    import torch
+    from paper_1408_3877_gb300 import festung as F
+    cV, V0T, side = W.square_mesh(24, jitter=0.2, seed=8)
+    bdr = W.boundary_types(side, (2, 4), (1, 3))
+    man = W.Manufactured(W.d_config2)
+    tau, t = 1e-3, 1e-3
+    res = {}
+    for prec, tol in ((F.FP64, 1e-14), (F.MIXED, 1e-10)):
+        s = gpu_solver(cV, V0T, bdr, p)
+        s.set_state(samples(s, lambda x, y: man.c(0.0, x, y)), is_samples=True)
+        _load_step_data(s, man, t)
+        info = s.step(tau, tol=tol, prec=prec, inner_tol=1e-2)
+        res[prec] = (s.get_state(), info)
+        if prec == F.FP64:
+            order = s.element_order()
+            keep = s
+        else:
+            s.close()
+    from helpers import from_gpu_layout, to_gpu_layout
+    Cref, Cmix = res[F.FP64][0], res[F.MIXED][0]
+    K, N = keep.K, keep.N
+    x = to_gpu_layout(Cref.ravel(), K, N, torch.float64, order)
+    b = torch.empty_like(x)
+    keep.apply(x, b, tau, F.FP64)                      # S C_ref = b up to 1e-14 ||b||
+    dx = to_gpu_layout((Cref - Cmix).ravel(), K, N, torch.float64, order)
+    r = torch.empty_like(dx)
+    keep.apply(dx, r, tau, F.FP64)
+    torch.cuda.synchronize()
+    rel = float(torch.linalg.norm(r) / torch.linalg.norm(b))
+    assert res[F.FP64][1]["rel_residual"] <= 1e-14
+    assert rel <= 1.2e-10, (rel, res[F.MIXED][1])
+    keep.close()
+
+
+@pytest.mark.parametrize("p", [2, 4])
+def test_mixed_sweeps_converge_like_fp64(p):
+    """The FP32 BiCGStab sweeps (reductions fused into the applies) need about as many
+    iterations as the FP64 BiCGStab for the same reduction, and no FP64 fallback."""
+    from paper_1408_3877_gb300 import festung as F
+    cV, V0T, side = W.square_mesh(32, jitter=0.2, seed=6)
+    bdr = W.boundary_types(side, (2, 4), (1, 3))
+    man = W.Manufactured(W.d_config2)
+    tau, t = 1e-3, 1e-3
+    its = {}
+    for prec in (F.FP64, F.MIXED):
+        s = gpu_solver(cV, V0T, bdr, p)
+        s.set_state(samples(s, lambda x, y: man.c(0.0, x, y)), is_samples=True)
+        _load_step_data(s, man, t)
+        info = s.step(tau, tol=1e-10, prec=prec, inner_tol=1e-2)
+        assert info["rel_residual"] <= 1e-10
+        its[prec] = info
+        s.close()
+    assert its[F.MIXED]["fp64_iterations"] == 0, its
+    assert its[F.MIXED]["iterations"] <= 2 * its[F.FP64]["iterations"] + 10, its
 
 
 def test_square8_p1_ten_steps():
