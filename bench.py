@@ -231,6 +231,13 @@ def run_festung(args):
     pin = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64).pin_memory()
     host_inputs = [step_inputs(s, cfg, man, (nsteps + i + 1) * dt, pin) for i in range(args.steps)]
     out = torch.empty((K, N), dtype=torch.float64).pin_memory()
+    # The first DMA from freshly pinned pages on this host costs several ms of one-time
+    # mapping; an application streams through pinned buffers it reuses, so each buffer is
+    # read once by a copy before the timed region (the timed steps still copy every input).
+    for h in host_inputs:
+        for a in h:
+            torch.empty(a.shape, dtype=a.dtype, device="cuda").copy_(a, non_blocking=True)
+    torch.empty((K, N), dtype=torch.float64, device="cuda").copy_(out, non_blocking=True)
     h2d = sum(int(a.numel() * 8) for a in host_inputs[0])
     d2h = K * N * 8
     barrier()
@@ -319,14 +326,15 @@ def run_festung(args):
     line = {
         "metric": METRIC, "value": sec_per_step, "unit": "s/step", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sec_per_step * 1e3 * world, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+dfloat+f64",
         "data": "synthetic (seeded manufactured solution on a seeded jittered mesh)",
         "config": {"workload": CFG_NAME, "triangles": K, "p": p, "dofs": K * N, "dt": dt, "tol": tol,
-                   "precision": "FP32 inner Krylov, FP64 residual refinement", "l2": "flushed between steps",
+                   "precision": "FP32 inner Krylov; refinement on double-float (48-bit) residuals; FP64 state and right-hand side", "l2": "flushed between steps",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "iterations_per_step": float(np.mean([i["iterations"] for i in infos])),
         "outer_per_step": float(np.mean([i["outer"] for i in infos])),
         "rel_residual_max": float(max(i["rel_residual"] for i in infos)),
+        "initial_rel_residual_median": float(np.median([i["initial_rel_residual"] for i in infos])),
         "apply": apply_main, "apply_large": apply_big,
         "roofline": roof,
         "e2e": {"value": e2e, "unit": "s/step", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

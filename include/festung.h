@@ -87,11 +87,12 @@ typedef struct festung_step_opts {
 typedef struct festung_step_info {
     int    iterations;   /* Krylov iterations (summed over refinement sweeps)                  */
     int    outer;        /* refinement sweeps (1 for FESTUNG_FP64)                              */
-    double rel_residual; /* final ||b - S C||_2 / ||b||_2, evaluated in FP64                    */
+    double rel_residual; /* final ||b - S C||_2 / ||b||_2 (FESTUNG_MIXED: S C in double-float)  */
     int    solver;       /* FESTUNG_SOLVER_CG or FESTUNG_SOLVER_BICGSTAB                        */
     int    symmetric;    /* 1 if d_h is elementwise constant (S symmetric, Sec. 2.4.3-2.4.4)   */
     int    fp64_iterations; /* FESTUNG_MIXED: iterations of the FP64 solve that finished the step
                                after an FP32 sweep failed to lower the residual (else 0)            */
+    double initial_rel_residual; /* ||b - S C0||_2 / ||b||_2 of the initial guess C0               */
 } festung_step_info;
 
 /* Build the grid lists of Tab. 1 (Sec. 3.1, routine generateGridData): edges,
@@ -193,9 +194,17 @@ int festung_step(festung_ctx *ctx, double dt, const festung_step_opts *opts,
  * zero-flux data alone the operator is singular).  Resets the time extrapolation. */
 int festung_solve_stationary(festung_ctx *ctx, const festung_step_opts *opts, festung_step_info *info);
 
-/* Discretisation error ||c_h - c||_{L2} (Sec. 3.5) from samples of the exact c at
- * the triangle points (K x R2, host). */
+/* Discretisation error ||c_h - c||_{L2} (Sec. 3.5) of the current C from samples of the
+ * exact c at the triangle points (K x R2, host), with the context's triangle rule;
+ * evaluated on the device. */
 int festung_l2_error(const festung_ctx *ctx, const double *c_samples, double *err);
+
+/* Recover the flux unknown z_h = -grad c_h in the mixed form (Sec. 2.2) from the
+ * current C: Z^m = -M^{-1} (B_m C + J_D^m), block rows 1-2 of eq. timeDepSystem, with
+ * the Dirichlet data last given to festung_set_bc.  Z: 2 x K x N (Z^1 then Z^2, each
+ * K x N in the caller's order like the state), host or device (loc).  Synchronises the
+ * context's stream. */
+int festung_get_flux(const festung_ctx *ctx, double *Z, int loc);
 
 /* The internal triangle order of the device layout: order[i] is the caller's index of
  * the triangle stored at position i (order holds K entries, host memory). */

@@ -36,6 +36,25 @@ void launch_rhs(const festung_ctx *c, double *W1, double *W2, double *b, double 
     });
 }
 
+void launch_flux(const festung_ctx *c, const double *x, double *Z1, double *Z2, cudaStream_t st) {
+    const int grid = elem_grid(c);
+    c->launches += 1;
+    dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
+        constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
+        k_flux<double, N, R2, R1><<<grid, 256, 0, st>>>(x, Z1, Z2, c->dB, c->dNbr, c->K, c->dTab, nullptr);
+    });
+}
+
+void launch_lift(const festung_ctx *c, double *W1, double *W2, cudaStream_t st) {
+    const int grid = elem_grid(c);
+    c->launches += 1;
+    dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
+        constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
+        k_dirichlet_lift<double, N, R2, R1><<<grid, 256, 0, st>>>(W1, W2, c->dB, c->dNbr, c->K, c->dTab, c->dCD,
+                                                                  c->dPerm);
+    });
+}
+
 template <>
 void launch_apply_twopass<double>(const festung_ctx *c, const double *x, double *y, double *Z1, double *Z2, double tau,
                                   const int *skip, cudaStream_t st) {

@@ -204,6 +204,7 @@ __global__ void k_fin_init(KScal *sc, const double *part, int nblk, double tol) 
         sc->b2 = b2;
         sc->tol2 = tol * tol;
         sc->rho = r0r;  // (r0, r); CG sets rho = (r, z) itself
+        sc->r2_0 = r2;
         sc->ss = r2;
         sc->first = 1;
         sc->pending = 0;
@@ -274,6 +275,42 @@ __global__ void k_to_df(int64_t n, const double *a, dfloat *b) {
 __global__ void k_from_df(int64_t n, const dfloat *a, double *b) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         b[i] = (double)a[i];
+}
+
+// Z^m = Zh^m - W^m in the caller's order: out[(m K + u) N + j], u = perm[i]
+__global__ void k_flux_public(int64_t K, int N, const double *Z1, const double *Z2, const double *W1,
+                              const double *W2, const int32_t *perm, double *out) {
+    ELEM_LOOP(i) {
+        const int64_t u = perm[i];
+        for (int j = 0; j < N; ++j) {
+            out[u * N + j] = Z1[j * K + i] - W1[j * K + i];
+            out[(K + u) * N + j] = Z2[j * K + i] - W2[j * K + i];
+        }
+    }
+}
+
+struct QuadWeights {
+    double w[32];
+};
+
+// Squared L2 error of c_h against samples of c at the triangle points (Sec. 3.5):
+// sum_k 2|T_k| sum_r w_r (c_h(F_k(q_r)) - c(F_k(q_r)))^2; samples in the caller's order.
+__global__ void k_l2_error(int64_t K, int N, int R2, const double *C, const double *samp, const double *phiQ,
+                           QuadWeights qw, const double *Bg, const int32_t *perm, double *part) {
+    double acc[1] = {0.0};
+    ELEM_LOOP(i) {
+        const int64_t u = perm[i];
+        const double det = Bg[i] * Bg[3 * K + i] - Bg[K + i] * Bg[2 * K + i];
+        double e = 0.0;
+        for (int r = 0; r < R2; ++r) {
+            double ch = 0.0;
+            for (int j = 0; j < N; ++j) ch += C[j * K + i] * phiQ[r * N + j];
+            const double dlt = ch - samp[u * R2 + r];
+            e += qw.w[r] * dlt * dlt;
+        }
+        acc[0] += det * e;
+    }
+    block_partials<1>(acc, part);
 }
 
 __global__ void k_fin_sums(double *out, const double *part, int nblk, int np) {
@@ -580,7 +617,7 @@ GraphCache &graph_of<float>(festung_ctx *c) { return c->ws->g32; }
 // x_zero: x is 0 on entry.  Returns iterations in *iters and the final recursive ||r||^2, ||b||^2.
 template <typename T>
 int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_iter, bool x_zero, int *iters,
-                 double *r2, double *b2, bool *conv, bool reweight = false) {
+                 double *r2, double *b2, bool *conv, bool reweight = false, double *relres0 = nullptr) {
     Workspace &w = *c->ws;
     Vecs<T> &V = vecs<T>(c);
     const int64_t K = c->K;
@@ -635,6 +672,7 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
             FCK(cudaMemcpyAsync(w.h_scal, w.scal, sizeof(KScal), cudaMemcpyDeviceToHost, st));
             FCK(cudaStreamSynchronize(st));
             const KScal h = *w.h_scal;
+            if (relres0 && restart == 0) *relres0 = h.b2 > 0 ? std::sqrt(h.r2_0 / h.b2) : std::sqrt(h.r2_0);
             if (h.done) {
                 if (h.sconv) {
                     k_axpy_alpha<T><<<g, RED_THREADS, 0, st>>>(K, N, V.x, V.ph, w.scal); ++c->launches;
@@ -1198,7 +1236,7 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
     int iters = 0, outer = 0, iters64 = 0;
     double r2 = 0, b2 = 0;
     bool conv = false;
-    double relres = 0.0;
+    double relres = 0.0, relres0 = -1.0;
     // FP64 residual r = b - S x and its norms (rn, bn)
     // (FESTUNG_MIXED: S x in double-float arithmetic, about 48 significant bits)
     const bool df_residual = o.prec == FESTUNG_MIXED;
@@ -1232,6 +1270,7 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
             double rn, bn;
             if ((rc = residual64(&rn, &bn))) return rc;
             relres = bn > 0 ? rn / bn : rn;
+            if (relres0 < 0.0) relres0 = relres;
             if (relres <= o.tol || rn == 0.0) {
                 conv = true;
                 break;
@@ -1282,8 +1321,10 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
         // FP64 Krylov; verified with the true residual and restarted if the recursion drifted
         for (int sweep = 1; sweep <= o.max_outer; ++sweep, ++outer) {
             int it = 0;
+            double rr0 = -1.0;
             rc = krylov_solve<double>(c, solver, dt, o.tol, std::max(1, o.max_iter - iters), false, &it, &r2, &b2,
-                                      &conv);
+                                      &conv, false, &rr0);
+            if (relres0 < 0.0) relres0 = rr0;
             if (rc) return rc;
             iters += it;
             if (o.prec == FESTUNG_MIXED) iters64 += it;
@@ -1302,6 +1343,7 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
         info->solver = solver;
         info->symmetric = c->symmetric ? 1 : 0;
         info->fp64_iterations = iters64;
+        info->initial_rel_residual = relres0;
     }
     if (!conv) {
         c->err = "Krylov solve did not converge (relative residual " + std::to_string(relres) + ")";
@@ -1350,24 +1392,56 @@ int festung_l2_error(const festung_ctx *cc, const double *c_samples, double *err
         c->err = "NULL argument";
         return FESTUNG_EINVAL;
     }
-    const int64_t K = c->K, N = c->N;
-    std::vector<double> C(K * N);
-    int rc = festung_get_state(c, C.data(), FESTUNG_HOST);
+    int rc = ensure_ws(c);
     if (rc) return rc;
-    const HostTables &T = c->tab;
-    double s = 0.0;
-    for (int64_t k = 0; k < K; ++k) {
-        const double det = c->hB[k] * c->hB[3 * K + k] - c->hB[K + k] * c->hB[2 * K + k];
-        double e = 0.0;
-        for (int r = 0; r < c->R2; ++r) {
-            double ch = 0.0;
-            for (int j = 0; j < N; ++j) ch += C[k * N + j] * T.phiQ[r * N + j];
-            const double d = ch - c_samples[k * c->R2 + r];
-            e += T.tri.w[r] * d * d;
-        }
-        s += det * e;
+    Workspace &w = *c->ws;
+    const int64_t n = c->K * c->R2;
+    FCK(cudaMemcpyAsync(c->dSamp, c_samples, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    QuadWeights qw{};
+    for (int r = 0; r < c->R2; ++r) qw.w[r] = c->tab.tri.w[r];
+    const TableOffsets o = table_offsets(c->N, c->R2, c->R1);
+    k_l2_error<<<w.nblk, RED_THREADS, 0, c->stream>>>(c->K, c->N, c->R2, c->dC, c->dSamp, c->dTab + o.phiQ, qw,
+                                                     c->dB, c->dPerm, w.part);
+    k_fin_sums<<<1, 1024, 0, c->stream>>>(w.res, w.part, w.nblk, 1);
+    c->launches += 2;
+    FCK(cudaGetLastError());
+    FCK(cudaMemcpyAsync(w.h_res, w.res, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    FCK(cudaStreamSynchronize(c->stream));
+    *err = std::sqrt(std::max(0.0, w.h_res[0]));
+    return FESTUNG_OK;
+}
+
+int festung_get_flux(const festung_ctx *cc, double *Z, int loc) {
+    festung_ctx *c = const_cast<festung_ctx *>(cc);
+    if (!ready(c)) return c ? FESTUNG_ESTATE : FESTUNG_EINVAL;
+    if (!Z || (loc != FESTUNG_HOST && loc != FESTUNG_DEVICE)) {
+        c->err = "Z is NULL or bad loc";
+        return FESTUNG_EINVAL;
     }
-    *err = std::sqrt(s);
+    int rc = ensure_ws(c);
+    if (rc) return rc;
+    Workspace &w = *c->ws;
+    const int64_t KN = c->K * c->N;
+    if ((rc = alloc_vecs<double>(c, w.d, false))) return rc;
+    if (!w.scratch64) FCK(cudaMalloc(&w.scratch64, 2 * KN * sizeof(double)));
+    double *W1 = w.scratch64, *W2 = w.scratch64 + KN;
+    cudaStream_t st = c->stream;
+    launch_flux(c, c->dC, w.d.Z1, w.d.Z2, st);
+    launch_lift(c, W1, W2, st);
+    double *out = Z;
+    double *tmp = nullptr;
+    if (loc == FESTUNG_HOST) FCK(cudaMalloc(&tmp, 2 * KN * sizeof(double)));
+    if (tmp) out = tmp;
+    k_flux_public<<<small_grid(KN, c), 256, 0, st>>>(c->K, c->N, w.d.Z1, w.d.Z2, W1, W2, c->dPerm, out);
+    ++c->launches;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && tmp) e = cudaMemcpyAsync(Z, tmp, 2 * KN * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) {
+        c->err = std::string("festung_get_flux: ") + cudaGetErrorString(e);
+        return FESTUNG_ECUDA;
+    }
     return FESTUNG_OK;
 }
 

@@ -13,6 +13,7 @@ struct KScal {
     double r2, b2, tol2;
     double den;
     double ss;    // BiCGStab: (s, s) of the current iteration
+    double r2_0;  // (r, r) at the start of the solve
     int done, breakdown, iter, sconv;
     int first;    // BiCGStab: no update of x and r is owed from a previous iteration
     int pending;  // BiCGStab: x += alpha ph + omega sh, r = s - omega t still to apply

@@ -39,6 +39,11 @@ void launch_apply_twopass(const festung_ctx *c, const T *x, T *y, T *Z1, T *Z2, 
 // (the Dirichlet lift M^{-1} J_D^m).
 void launch_rhs(const festung_ctx *c, double *W1, double *W2, double *b, double tau, cudaStream_t st);
 
+// The flux unknowns of eq. timeDepSystem, block rows 1-2, in two parts (FP64, N x K):
+// launch_flux: Z^m = -M^{-1} B_m x;  launch_lift: W^m = M^{-1} J_D^m from the context's c_D.
+void launch_flux(const festung_ctx *c, const double *x, double *Z1, double *Z2, cudaStream_t st);
+void launch_lift(const festung_ctx *c, double *W1, double *W2, cudaStream_t st);
+
 int elem_grid(const festung_ctx *c);
 
 // Blocks of the FP32 fused apply that run at once on the device (resident blocks per

@@ -22,7 +22,7 @@ EXPORTS = [
     "festung_mesh_create", "festung_setup", "festung_sizes", "festung_quad_points",
     "festung_set_coeff", "festung_set_source", "festung_set_bc", "festung_set_state",
     "festung_get_state", "festung_apply", "festung_apply_noalloc", "festung_step", "festung_solve_stationary",
-    "festung_l2_error",
+    "festung_l2_error", "festung_get_flux",
     "festung_element_order", "festung_launch_count", "festung_set_stream", "festung_last_error", "festung_destroy",
 ]
 
@@ -34,7 +34,8 @@ class StepOpts(ctypes.Structure):
 
 class StepInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("outer", ctypes.c_int), ("rel_residual", ctypes.c_double),
-                ("solver", ctypes.c_int), ("symmetric", ctypes.c_int), ("fp64_iterations", ctypes.c_int)]
+                ("solver", ctypes.c_int), ("symmetric", ctypes.c_int), ("fp64_iterations", ctypes.c_int),
+                ("initial_rel_residual", ctypes.c_double)]
 
 
 class FestungError(RuntimeError):
@@ -70,6 +71,7 @@ def load(path=None):
     lib.festung_apply_noalloc.argtypes = [vp, vp, vp, cint, dbl]
     lib.festung_step.argtypes = [vp, dbl, ctypes.POINTER(StepOpts), ctypes.POINTER(StepInfo)]
     lib.festung_l2_error.argtypes = [vp, vp, ctypes.POINTER(dbl)]
+    lib.festung_get_flux.argtypes = [vp, vp, ctypes.c_int]
     lib.festung_solve_stationary.argtypes = [vp, ctypes.POINTER(StepOpts), ctypes.POINTER(StepInfo)]
     lib.festung_set_stream.argtypes = [vp, vp]
     lib.festung_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
@@ -188,7 +190,8 @@ class Solver:
         info = StepInfo()
         self._check(self.lib.festung_step(self.h, dt, ctypes.byref(o), ctypes.byref(info)))
         return {"iterations": info.iterations, "outer": info.outer, "rel_residual": info.rel_residual,
-                "solver": info.solver, "symmetric": info.symmetric, "fp64_iterations": info.fp64_iterations}
+                "solver": info.solver, "symmetric": info.symmetric, "fp64_iterations": info.fp64_iterations,
+                "initial_rel_residual": info.initial_rel_residual}
 
     def element_order(self):
         """order[i] = caller's index of the triangle at position i of the device layout."""
@@ -207,7 +210,14 @@ class Solver:
         info = StepInfo()
         self._check(self.lib.festung_solve_stationary(self.h, ctypes.byref(o), ctypes.byref(info)))
         return {"iterations": info.iterations, "outer": info.outer, "rel_residual": info.rel_residual,
-                "solver": info.solver, "symmetric": info.symmetric, "fp64_iterations": info.fp64_iterations}
+                "solver": info.solver, "symmetric": info.symmetric, "fp64_iterations": info.fp64_iterations,
+                "initial_rel_residual": info.initial_rel_residual}
+
+    def get_flux(self):
+        """Z^1, Z^2 (each K x N, caller order) of the flux unknown z_h = -grad c_h from the current state."""
+        Z = np.empty((2, self.K, self.N))
+        self._check(self.lib.festung_get_flux(self.h, Z.ctypes.data, HOST))
+        return Z
 
     def l2_error(self, c_samples):
         s = np.ascontiguousarray(c_samples, dtype=np.float64)
