@@ -406,6 +406,93 @@ def profile_apply(args):
     return out
 
 
+def run_batched(args):
+    """The batched workload: independent problems of uneven size and order advanced together
+    (festung_batch_step), against the same problems stepped one after the other with the
+    plain FP64 solve and with the single-problem mixed solve.  Timed: the solves only; the
+    per-step loading of sources and boundary data is reported apart."""
+    import torch
+    from paper_1408_3877_gb300 import festung as F
+    cfg = W.CONFIGS["batched512"]
+    specs = W.batched_problems(args.nprob or cfg["nprob"], cfg["seed"])
+    dt, tol = cfg["dt"], cfg["tol"]
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    t0 = time.perf_counter()
+    solvers, data = [], []
+    for sp in specs:
+        cV, V0T, side = W.square_mesh(sp["n"])
+        bdr = W.boundary_types(side, cfg["dirichlet"], cfg["neumann"])
+        s = F.Solver(cV, V0T, bdr).setup(sp["p"])
+        man = W.Manufactured(W.grf_coefficient(W.GaussianField(sp["grf_seed"], sp["length"])))
+        xy, exy = s.quad_points()
+        X, Y = xy[..., 0], xy[..., 1]
+        s.set_coeff(man.d(0.0, X, Y))
+        s.set_state(man.c(0.0, X, Y), is_samples=True)
+        # c = cos7x cos7y exp(-t) and a time-independent d: f(t) = exp(-t) f(0), c_D(t) = exp(-t) c_D(0)
+        dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+        data.append((dev(man.f(0.0, X, Y)), dev(man.c(0.0, exy[..., 0], exy[..., 1]))))
+        solvers.append(s)
+    prep = time.perf_counter() - t0
+    K = sum(s.K for s in solvers)
+    dofs = sum(s.K * s.N for s in solvers)
+
+    def load(t):
+        a = time.perf_counter()
+        e = float(np.exp(-t))
+        for s, (f0, c0) in zip(solvers, data):
+            s.set_source(f0 * e)
+            s.set_bc(c0 * e, None)
+        torch.cuda.synchronize()
+        return time.perf_counter() - a
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        out = fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3, out
+
+    batch = F.Batch(solvers)
+    step = 0
+    load_s, batch_s, infos = [], [], []
+    for k in range(args.warmup + args.steps):
+        step += 1
+        load_s.append(load(step * dt))
+        sec, info = timed(lambda: batch.step(dt, tol=tol, inner_tol=1e-2))
+        if k >= args.warmup:
+            batch_s.append(sec)
+            infos.append(info)
+    launches = batch.launch_count()
+    batch.close()
+    # the same problems one after the other: single-problem mixed solve, then plain FP64
+    single = {}
+    for name, prec, nsteps in (("mixed_per_problem", F.MIXED, 3), ("fp64_per_problem", F.FP64, 2)):
+        secs = []
+        for k in range(nsteps):
+            step += 1
+            load(step * dt)
+            sec, _ = timed(lambda: [s.step(dt, tol=tol, prec=prec, inner_tol=1e-2) for s in solvers])
+            secs.append(sec)
+        single[name] = secs[-1]
+    value = float(np.mean(batch_s))
+    its = [i["iterations"] for step_info in infos for i in step_info]
+    return {"metric": "sec per implicit step of the whole batch at 1e-10 rel. residual per problem",
+            "value": value, "unit": "s/step", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": False, "dtype": "f32+dfloat+f64", "data": "synthetic (seeded meshes, fields)",
+            "config": {"workload": "batched512", "problems": len(solvers), "triangles": K, "dofs": dofs,
+                       "orders": {str(p): sum(1 for sp in specs if sp["p"] == p) for p in (1, 2, 3)},
+                       "dt": dt, "tol": tol, "groups": "one union mesh per order, one Krylov per group"},
+            "dof_per_s": dofs / value, "iterations_per_step_mean": float(np.mean(its)),
+            "rel_residual_max": float(max(i["rel_residual"] for step_info in infos for i in step_info)),
+            "input_loading_s_per_step": float(np.mean(load_s)), "host_preparation_s": prep,
+            "gpu_launches_per_step": launches / (args.warmup + args.steps),
+            "same_problems_one_by_one": {k: {"value": v, "unit": "s/step", "speedup_of_batch": v / value}
+                                         for k, v in single.items()}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -418,11 +505,16 @@ def main():
                     help="only run the operator apply on WORKLOAD (for ncu captures); prints one line")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "dfloat"])
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--workload", default=None, choices=["batched512"],
+                    help="run another workload than the default step benchmark; prints one line")
+    ap.add_argument("--nprob", type=int, default=None, help="batched512: number of problems (default 512)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.profile_apply:
         line = profile_apply(args)
+    elif args.workload == "batched512":
+        line = run_batched(args)
     elif args.impl == "reference":
         line = run_reference(args)
     else:

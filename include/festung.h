@@ -206,6 +206,33 @@ int festung_l2_error(const festung_ctx *ctx, const double *c_samples, double *er
  * context's stream. */
 int festung_get_flux(const festung_ctx *ctx, double *Z, int loc);
 
+/* ---- Batches of independent problems -------------------------------------------
+ * Many problems (each its own context, set up, with its own mesh, order, coefficient,
+ * source and boundary data) advance by one implicit-Euler step together.  Problems of
+ * the same p, quadrature and eta form a group whose meshes are joined into one internal
+ * mesh: each kernel of the step runs over all problems of the group at once.  The
+ * Krylov iteration runs on the block-diagonal union system; refinement and convergence
+ * are per problem (each problem's residual is normalised on its own, and every problem
+ * reaches tol on its own residual).  The paper has no counterpart: it solves one
+ * problem at a time.
+ *
+ * festung_batch_create: problems[0..nprob) stay owned by the caller and must outlive the
+ * batch; they must not be set up again while in it.  Their data are set with the usual
+ * calls (festung_set_coeff, _source, _bc, _state) before each festung_batch_step, which
+ * reads them, steps all problems (FESTUNG_MIXED only; opts as festung_step) and writes
+ * every C back (festung_get_state reads it).  infos: nprob entries or NULL.  Groups are
+ * stepped one after the other; on an error the problems of the failing group and of the
+ * groups after it keep their C.  The extrapolated initial guess of a group restarts when
+ * one of its problems' state was set from outside since the last batch step. */
+typedef struct festung_batch festung_batch;
+int festung_batch_create(festung_ctx *const *problems, int nprob, festung_batch **out);
+int festung_batch_set_stream(festung_batch *batch, void *cuda_stream);
+int festung_batch_step(festung_batch *batch, double dt, const festung_step_opts *opts, festung_step_info *infos);
+int festung_batch_launch_count(const festung_batch *batch, int64_t *n);
+/* Message of the last failed batch call (batch = NULL: of the last failed create). */
+const char *festung_batch_last_error(const festung_batch *batch);
+void festung_batch_destroy(festung_batch *batch);
+
 /* The internal triangle order of the device layout: order[i] is the caller's index of
  * the triangle stored at position i (order holds K entries, host memory). */
 int festung_element_order(const festung_ctx *ctx, int64_t *order);

@@ -451,6 +451,7 @@ void free_ctx_device(festung_ctx *c) {
     c->xD_valid = false;
     c->dC = c->dD = c->dF = c->dCD = c->dGN = c->dSamp = c->dCprev = c->dCprev2 = nullptr;
     c->hist = 0;
+    ++c->state_gen;
     c->fD = nullptr;
 }
 
@@ -750,6 +751,37 @@ int apply_df(festung_ctx *c, const double *x, double *y, double dt, cudaStream_t
     return FESTUNG_OK;
 }
 
+cudaError_t retile(festung_ctx *c, int te);
+
+// Device copies of a mesh in internal order (geometry in FP64 and FP32, neighbour
+// codes, permutation, lift flags) and a first tiling of 256 triangles.
+cudaError_t upload_mesh(festung_ctx *c, const MeshOrder &mo) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int64_t K = c->K;
+    if ((e = cudaMalloc(&c->dB, 4 * K * sizeof(double))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&c->fB, 4 * K * sizeof(float))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&c->dNbr, 3 * K * sizeof(int32_t))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&c->dPerm, K * sizeof(int32_t))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&c->dSlot, 3 * K * sizeof(int16_t))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&c->dLift, K * sizeof(uint8_t))) != cudaSuccess) return e;
+    std::vector<float> fB(mo.B.begin(), mo.B.end());
+    const struct {
+        void *dst;
+        const void *src;
+        size_t bytes;
+    } up[] = {{c->dB, mo.B.data(), 4 * K * sizeof(double)},
+              {c->fB, fB.data(), 4 * K * sizeof(float)},
+              {c->dNbr, mo.nbr.data(), 3 * K * sizeof(int32_t)},
+              {c->dPerm, mo.perm.data(), K * sizeof(int32_t)},
+              {c->dLift, mo.lift.data(), K * sizeof(uint8_t)}};
+    for (const auto &u : up)
+        if (u.bytes && (e = cudaMemcpy(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    return retile(c, 256);
+}
+
 // Tiles of te consecutive triangles of the internal order: halo lists and the
 // shared-memory slots of every neighbour, uploaded to the device (the previous tiling
 // is released on success).
@@ -864,31 +896,8 @@ int festung_mesh_create(const double *coordV, int64_t numV, const int32_t *V0T, 
         festung_destroy(c);
         return e == cudaErrorMemoryAllocation ? FESTUNG_ENOMEM : FESTUNG_ECUDA;
     };
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    cudaError_t e = upload_mesh(c, mo);
     if (e != cudaSuccess) return fail(e);
-    e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return fail(e);
-    const int64_t K = numT;
-    if ((e = cudaMalloc(&c->dB, 4 * K * sizeof(double))) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&c->fB, 4 * K * sizeof(float))) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&c->dNbr, 3 * K * sizeof(int32_t))) != cudaSuccess) return fail(e);
-    std::vector<float> fB(mo.B.begin(), mo.B.end());
-    if ((e = cudaMalloc(&c->dPerm, K * sizeof(int32_t))) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&c->dSlot, 3 * K * sizeof(int16_t))) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&c->dLift, K * sizeof(uint8_t))) != cudaSuccess) return fail(e);
-    const struct {
-        void *dst;
-        const void *src;
-        size_t bytes;
-    } up[] = {{c->dB, mo.B.data(), 4 * K * sizeof(double)},
-              {c->fB, fB.data(), 4 * K * sizeof(float)},
-              {c->dNbr, mo.nbr.data(), 3 * K * sizeof(int32_t)},
-              {c->dPerm, mo.perm.data(), K * sizeof(int32_t)},
-              {c->dLift, mo.lift.data(), K * sizeof(uint8_t)}};
-    for (const auto &u : up)
-        if (u.bytes && (e = cudaMemcpy(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
-    if ((e = retile(c, 256)) != cudaSuccess) return fail(e);
     *out = c;
     return FESTUNG_OK;
 }
@@ -1118,6 +1127,7 @@ int festung_set_state(festung_ctx *c, const double *C, int is_samples, int loc) 
         FCK(cudaGetLastError());
     }
     c->hist = 0;
+    ++c->state_gen;
     FCK(cudaStreamSynchronize(c->stream));
     return FESTUNG_OK;
 }
@@ -1172,14 +1182,8 @@ namespace {
 
 // Solve (mass M + dt (eta S_t - sum_m A_m M^{-1} B_m)) C = b: an implicit-Euler step
 // (mass = 1, E1-E2) or the stationary problem of Sec. 3.9 (mass = 0, dt = 1).
-int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts *opts, festung_step_info *info) {
-    struct MassGuard {
-        festung_ctx *c;
-        ~MassGuard() { c->mass = 1.0; }
-    } guard{c};
-    c->mass = mass;
-    const bool stationary = mass == 0.0;
-    festung_step_opts o;
+// Step options with the defaults of festung_step; false if out of range.
+bool step_options(const festung_step_opts *opts, festung_step_opts &o) {
     o.tol = 1e-10;
     o.max_iter = 20000;
     o.prec = FESTUNG_MIXED;
@@ -1187,19 +1191,20 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
     o.max_outer = 50;
     o.solver = 0;
     if (opts) o = *opts;
-    if (!(dt > 0.0) || !(o.tol > 0.0) || o.max_iter < 1 ||
-        (o.prec != FESTUNG_FP64 && o.prec != FESTUNG_MIXED) || o.max_outer < 1 ||
-        !(o.inner_tol > 0.0 && o.inner_tol < 1.0) ||
-        (o.solver != 0 && o.solver != FESTUNG_SOLVER_CG && o.solver != FESTUNG_SOLVER_BICGSTAB)) {
-        c->err = "bad step arguments";
-        return FESTUNG_EINVAL;
-    }
+    return o.tol > 0.0 && o.max_iter >= 1 && (o.prec == FESTUNG_FP64 || o.prec == FESTUNG_MIXED) &&
+           o.max_outer >= 1 && o.inner_tol > 0.0 && o.inner_tol < 1.0 &&
+           (o.solver == 0 || o.solver == FESTUNG_SOLVER_CG || o.solver == FESTUNG_SOLVER_BICGSTAB);
+}
+
+// Everything before the Krylov solve of a step: vectors, b (E2) into V.b (W^m of the
+// Dirichlet lift left in scratch64), the block-Jacobi preconditioner, and the initial
+// guess V.x extrapolated in time from the previous states.
+int prepare_solve(festung_ctx *c, double dt, bool stationary, bool mixed) {
     int rc = ensure_ws(c);
     if (rc) return rc;
     Workspace &w = *c->ws;
     if ((rc = alloc_vecs<double>(c, w.d, true))) return rc;
-    if (o.prec == FESTUNG_MIXED && (rc = alloc_vecs<float>(c, w.f, true))) return rc;
-    const int solver = o.solver ? o.solver : (c->symmetric ? FESTUNG_SOLVER_CG : FESTUNG_SOLVER_BICGSTAB);
+    if (mixed && (rc = alloc_vecs<float>(c, w.f, true))) return rc;
     const int64_t KN = c->K * c->N;
     cudaStream_t st = c->stream;
     Vecs<double> &V = w.d;
@@ -1214,8 +1219,8 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
     FCK(cudaMemsetAsync(w.d_flags, 0, sizeof(int), st));
     launch_blockjacobi(c, w.P, w.Pb, dt, w.d_flags, st);
     FCK(cudaGetLastError());
-    // initial guess: linear extrapolation in time from the two previous states when the
-    // previous step exists, else C^n (the result does not depend on it beyond the tolerance)
+    // initial guess: extrapolation in time from the previous states when they exist,
+    // else C^n (the result does not depend on it beyond the tolerance)
     if (!stationary && c->hist >= 2 && c->dt_prev > 0.0 && c->dt_prev2 > 0.0) {
         // quadratic Lagrange extrapolation through t_{n-2}, t_{n-1}, t_n to t_{n+1}
         const double h0 = c->dt_prev2, h1 = c->dt_prev, h = dt;  // t_n - t_{n-1} = h1, t_{n-1} - t_{n-2} = h0
@@ -1233,6 +1238,55 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
     FCK(cudaMemcpyAsync(w.h_flags, w.d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     FCK(cudaStreamSynchronize(st));
     w.use_P = (w.h_flags[0] == 0);
+    return FESTUNG_OK;
+}
+
+// C <- V.x after a converged solve; a time step also shifts the history of previous
+// states for the next extrapolation.
+int commit_solution(festung_ctx *c, double dt, bool stationary) {
+    Workspace &w = *c->ws;
+    const int64_t KN = c->K * c->N;
+    cudaStream_t st = c->stream;
+    if (stationary) {
+        FCK(cudaMemcpyAsync(c->dC, w.d.x, KN * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        FCK(cudaStreamSynchronize(st));
+        c->hist = 0;  // a stationary solve is no time step: the extrapolation restarts
+        ++c->state_gen;
+        return FESTUNG_OK;
+    }
+    if (!c->dCprev) FCK(cudaMalloc(&c->dCprev, KN * sizeof(double)));
+    if (!c->dCprev2) FCK(cudaMalloc(&c->dCprev2, KN * sizeof(double)));
+    std::swap(c->dCprev, c->dCprev2);  // C^{n-2} <- C^{n-1}
+    FCK(cudaMemcpyAsync(c->dCprev, c->dC, KN * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    FCK(cudaMemcpyAsync(c->dC, w.d.x, KN * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    FCK(cudaStreamSynchronize(st));
+    c->hist = std::min(c->hist + 1, 2);
+    c->dt_prev2 = c->dt_prev;
+    c->dt_prev = dt;
+    ++c->state_gen;
+    return FESTUNG_OK;
+}
+
+int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts *opts, festung_step_info *info) {
+    struct MassGuard {
+        festung_ctx *c;
+        ~MassGuard() { c->mass = 1.0; }
+    } guard{c};
+    c->mass = mass;
+    const bool stationary = mass == 0.0;
+    festung_step_opts o;
+    if (!step_options(opts, o) || !(dt > 0.0)) {
+        c->err = "bad step arguments";
+        return FESTUNG_EINVAL;
+    }
+    int rc = prepare_solve(c, dt, stationary, o.prec == FESTUNG_MIXED);
+    if (rc) return rc;
+    Workspace &w = *c->ws;
+    const int solver = o.solver ? o.solver : (c->symmetric ? FESTUNG_SOLVER_CG : FESTUNG_SOLVER_BICGSTAB);
+    const int64_t KN = c->K * c->N;
+    cudaStream_t st = c->stream;
+    Vecs<double> &V = w.d;
+    double *W1 = w.scratch64;
     int iters = 0, outer = 0, iters64 = 0;
     double r2 = 0, b2 = 0;
     bool conv = false;
@@ -1349,22 +1403,7 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
         c->err = "Krylov solve did not converge (relative residual " + std::to_string(relres) + ")";
         return FESTUNG_ENOCONV;
     }
-    if (stationary) {
-        FCK(cudaMemcpyAsync(c->dC, V.x, KN * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        FCK(cudaStreamSynchronize(st));
-        c->hist = 0;  // a stationary solve is no time step: the extrapolation restarts
-        return FESTUNG_OK;
-    }
-    if (!c->dCprev) FCK(cudaMalloc(&c->dCprev, KN * sizeof(double)));
-    if (!c->dCprev2) FCK(cudaMalloc(&c->dCprev2, KN * sizeof(double)));
-    std::swap(c->dCprev, c->dCprev2);  // C^{n-2} <- C^{n-1}
-    FCK(cudaMemcpyAsync(c->dCprev, c->dC, KN * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    FCK(cudaMemcpyAsync(c->dC, V.x, KN * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    FCK(cudaStreamSynchronize(st));
-    c->hist = std::min(c->hist + 1, 2);
-    c->dt_prev2 = c->dt_prev;
-    c->dt_prev = dt;
-    return FESTUNG_OK;
+    return commit_solution(c, dt, stationary);
 }
 
 }  // namespace
@@ -1476,6 +1515,451 @@ void festung_destroy(festung_ctx *c) {
     for (void *q : mesh_ptrs)
         if (q) cudaFree(q);
     delete c;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Batches of independent problems
+//
+// Problems of the same order (and quadrature and penalty) form a group.  The union of
+// their meshes is one internal context: every kernel of a step runs over all problems of
+// the group at once, and the Krylov iteration runs on the block-diagonal union system
+// (no kernel couples two problems).  Refinement and convergence are per problem: each
+// problem's residual is normalised on its own before an inner FP32 solve, its correction
+// is scaled back with its own norm, and a converged problem enters later sweeps with a
+// zero right-hand side, which the Krylov recursion keeps exactly zero.
+// ===========================================================================
+namespace {
+
+struct MemberPtrs {
+    double *C;
+    const double *D, *F, *CD, *GN;
+    int64_t K, off;
+};
+
+// union <- members: C, D (and its FP32 copy), F in the N x K internal layout; c_D, g_N
+// (K x 3 x R1) in the concatenated caller order.  Member q owns union elements
+// [off_q, off_q + K_q) in both orders.
+__global__ void k_batch_gather(int64_t K, int N, int E, const int32_t *eprob, const MemberPtrs *mem, double *C,
+                               double *D, float *fD, double *F, double *CD, double *GN) {
+    ELEM_LOOP(i) {
+        const MemberPtrs m = mem[eprob[i]];
+        const int64_t l = i - m.off;
+        for (int j = 0; j < N; ++j) {
+            C[j * K + i] = m.C[j * m.K + l];
+            const double d = m.D[j * m.K + l];
+            D[j * K + i] = d;
+            fD[j * K + i] = (float)d;
+            F[j * K + i] = m.F[j * m.K + l];
+        }
+        for (int e = 0; e < E; ++e) {
+            CD[i * E + e] = m.CD[l * E + e];
+            GN[i * E + e] = m.GN[l * E + e];
+        }
+    }
+}
+
+// members <- union: C
+__global__ void k_batch_scatter(int64_t K, int N, const int32_t *eprob, const MemberPtrs *mem, const double *C) {
+    ELEM_LOOP(i) {
+        const MemberPtrs m = mem[eprob[i]];
+        const int64_t l = i - m.off;
+        for (int j = 0; j < N; ++j) m.C[j * m.K + l] = C[j * K + i];
+    }
+}
+
+// r = b - y (y double-float) and per-problem (r, r), (b, b) into acc[2 q], acc[2 q + 1]
+// (acc zeroed by the caller).  A warp whose elements belong to one problem adds its sums
+// with one atomic per value.
+__global__ void k_residual_df_batch(int64_t K, int N, const double *b, const dfloat *y, double *r,
+                                    const int32_t *eprob, double *acc) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < K; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        double rr = 0.0, bb = 0.0;
+        int q = -1;
+        if (i < K) {
+            q = eprob[i];
+            for (int j = 0; j < N; ++j) {
+                const int64_t idx = j * K + i;
+                const double ri = b[idx] - (double)y[idx];
+                r[idx] = ri;
+                rr += ri * ri;
+                bb += b[idx] * b[idx];
+            }
+        }
+        const int q0 = __shfl_sync(0xffffffffu, q, 0);
+        if (__all_sync(0xffffffffu, q == q0 || q < 0)) {
+            for (int o = 16; o > 0; o >>= 1) {
+                rr += __shfl_xor_sync(0xffffffffu, rr, o);
+                bb += __shfl_xor_sync(0xffffffffu, bb, o);
+            }
+            if ((threadIdx.x & 31) == 0 && q0 >= 0) {
+                atomicAdd(acc + 2 * q0, rr);
+                atomicAdd(acc + 2 * q0 + 1, bb);
+            }
+        } else if (q >= 0) {
+            atomicAdd(acc + 2 * q, rr);
+            atomicAdd(acc + 2 * q + 1, bb);
+        }
+    }
+}
+
+// Fb = scale_q r (FP32)
+__global__ void k_scale_batch(int64_t K, int N, const double *r, float *Fb, const int32_t *eprob, const double *scale) {
+    ELEM_LOOP(i) {
+        const double sc = scale[eprob[i]];
+        for (int j = 0; j < N; ++j) Fb[j * K + i] = (float)(r[j * K + i] * sc);
+    }
+}
+
+// x += scale_q Fx
+__global__ void k_add_batch(int64_t K, int N, double *x, const float *Fx, const int32_t *eprob, const double *scale) {
+    ELEM_LOOP(i) {
+        const double sc = scale[eprob[i]];
+        if (sc != 0.0)
+            for (int j = 0; j < N; ++j) x[j * K + i] += sc * (double)Fx[j * K + i];
+    }
+}
+
+struct BatchGroup {
+    festung_ctx *u = nullptr;       // union context
+    std::vector<int> members;       // problem indices
+    std::vector<int64_t> off;       // element offset of each member (members + 1 entries)
+    std::vector<uint64_t> gen;      // member state generations seen after the last step
+    int32_t *eprob = nullptr;       // K: member of each union element
+    MemberPtrs *dmem = nullptr;     // device table of member arrays
+    double *dacc = nullptr, *hacc = nullptr;      // 2 per member: residual sums
+    double *dscale = nullptr, *hscale = nullptr;  // 1 per member
+};
+
+void free_group(BatchGroup &g) {
+    if (g.u) festung_destroy(g.u);
+    cudaFree(g.eprob);
+    cudaFree(g.dmem);
+    cudaFree(g.dacc);
+    cudaFree(g.dscale);
+    if (g.hacc) cudaFreeHost(g.hacc);
+    if (g.hscale) cudaFreeHost(g.hscale);
+    g = BatchGroup();
+}
+
+}  // namespace
+
+struct festung_batch {
+    std::vector<festung_ctx *> probs;
+    std::vector<BatchGroup> groups;
+    cudaStream_t stream = nullptr;
+    std::string err;
+};
+
+namespace {
+
+// Union context of the members of one group (all set up with the same p, quadrature and eta).
+int build_group(festung_batch *b, BatchGroup &g) {
+    festung_ctx *first = b->probs[g.members[0]];
+    int64_t K = 0;
+    g.off.assign(1, 0);
+    for (int q : g.members) {
+        K += b->probs[q]->K;
+        g.off.push_back(K);
+    }
+    if (K * (int64_t)first->N >= (int64_t(1) << 31)) {
+        b->err = "batch group too large: K * N must stay below 2^31";
+        return FESTUNG_EINVAL;
+    }
+    festung_ctx *u = new (std::nothrow) festung_ctx();
+    if (!u) return FESTUNG_ENOMEM;
+    g.u = u;
+    u->K = K;
+    MeshOrder mo;
+    mo.perm.resize(K);
+    mo.B.assign(4 * K, 0.0);
+    mo.nbr.assign(3 * K, 0);
+    std::vector<int32_t> ep(K);
+    for (size_t m = 0; m < g.members.size(); ++m) {
+        const festung_ctx *c = b->probs[g.members[m]];
+        const int64_t Kq = c->K, off = g.off[m];
+        u->has_dirichlet |= c->has_dirichlet;
+        u->has_neumann |= c->has_neumann;
+        for (int64_t i = 0; i < Kq; ++i) {
+            const int64_t cu = c->perm[i];
+            mo.perm[off + i] = (int32_t)(off + cu);
+            for (int r = 0; r < 4; ++r) mo.B[r * K + off + i] = c->hB[r * Kq + cu];
+            for (int n = 0; n < 3; ++n) {
+                const int32_t code = c->hNbrInt[n * Kq + i];
+                mo.nbr[n * K + off + i] = code >= 0 ? (int32_t)((((code >> 2) + off) << 2) | (code & 3)) : code;
+            }
+            ep[off + i] = (int32_t)m;
+        }
+    }
+    lift_flags(mo.nbr, K, mo.lift);
+    u->perm = mo.perm;
+    u->hNbrInt = mo.nbr;
+    cudaError_t e = upload_mesh(u, mo);
+    if (e != cudaSuccess) {
+        b->err = std::string("CUDA: ") + cudaGetErrorString(e);
+        return FESTUNG_ECUDA;
+    }
+    int rc = festung_setup(u, first->p, first->qT, first->eta);
+    if (rc) {
+        b->err = u->err;
+        return rc;
+    }
+    const size_t nm = g.members.size();
+    std::vector<MemberPtrs> hm(nm);
+    for (size_t m = 0; m < nm; ++m) {
+        festung_ctx *c = b->probs[g.members[m]];
+        hm[m] = MemberPtrs{c->dC, c->dD, c->dF, c->dCD, c->dGN, c->K, g.off[m]};
+    }
+    if ((e = cudaMalloc(&g.eprob, K * sizeof(int32_t))) != cudaSuccess ||
+        (e = cudaMemcpy(g.eprob, ep.data(), K * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMalloc(&g.dmem, nm * sizeof(MemberPtrs))) != cudaSuccess ||
+        (e = cudaMemcpy(g.dmem, hm.data(), nm * sizeof(MemberPtrs), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMalloc(&g.dacc, 2 * nm * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&g.dscale, nm * sizeof(double))) != cudaSuccess ||
+        (e = cudaMallocHost(&g.hacc, 2 * nm * sizeof(double))) != cudaSuccess ||
+        (e = cudaMallocHost(&g.hscale, nm * sizeof(double))) != cudaSuccess) {
+        b->err = std::string("CUDA: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? FESTUNG_ENOMEM : FESTUNG_ECUDA;
+    }
+    g.gen.assign(nm, ~0ull);
+    return FESTUNG_OK;
+}
+
+// One implicit-Euler step of every member of a group (FESTUNG_MIXED).
+int solve_group(festung_batch *b, BatchGroup &g, double dt, const festung_step_opts &o, festung_step_info *infos) {
+    festung_ctx *c = g.u;
+    const int nm = (int)g.members.size();
+    const int64_t K = c->K, KN = K * c->N;
+    cudaStream_t st = c->stream;
+    // members' data into the union; the extrapolation history is kept only while no
+    // member's state was changed from outside since the last batch step
+    bool fresh = false, symmetric = true;
+    for (int m = 0; m < nm; ++m) {
+        const festung_ctx *p = b->probs[g.members[m]];
+        fresh |= p->state_gen != g.gen[m];
+        symmetric &= p->symmetric;
+    }
+    if (fresh) c->hist = 0;
+    c->symmetric = symmetric;
+    k_batch_gather<<<small_grid(K, c), 256, 0, st>>>(K, c->N, 3 * c->R1, g.eprob, g.dmem, c->dC, c->dD, c->fD, c->dF,
+                                                     c->dCD, c->dGN);
+    ++c->launches;
+    FCK(cudaGetLastError());
+    c->xD_valid = false;
+    int rc = prepare_solve(c, dt, false, true);
+    if (rc) return rc;
+    Workspace &w = *c->ws;
+    Vecs<double> &V = w.d;
+    Vecs<float> &F = w.f;
+    const int solver = o.solver ? o.solver : (c->symmetric ? FESTUNG_SOLVER_CG : FESTUNG_SOLVER_BICGSTAB);
+    std::vector<double> rn(nm), bn(nm), rel(nm), rel0(nm, -1.0), prev(nm, -1.0), last(nm, 0.0);
+    std::vector<int> conv(nm, 0), outer_of(nm, 0), fails(nm, 0);
+    std::vector<char> applied(nm, 0);
+    // per-member residual norms (S x in double-float arithmetic)
+    auto residuals = [&]() -> int {
+        if ((rc = apply_df(c, V.x, nullptr, dt, st))) return rc;
+        FCK(cudaMemsetAsync(g.dacc, 0, 2 * nm * sizeof(double), st));
+        k_residual_df_batch<<<small_grid(K, c), 256, 0, st>>>(K, c->N, V.b, w.ydf, V.r, g.eprob, g.dacc);
+        ++c->launches;
+        FCK(cudaGetLastError());
+        FCK(cudaMemcpyAsync(g.hacc, g.dacc, 2 * nm * sizeof(double), cudaMemcpyDeviceToHost, st));
+        FCK(cudaStreamSynchronize(st));
+        for (int m = 0; m < nm; ++m) {
+            rn[m] = std::sqrt(g.hacc[2 * m]);
+            bn[m] = std::sqrt(g.hacc[2 * m + 1]);
+            rel[m] = bn[m] > 0 ? rn[m] / bn[m] : rn[m];
+            if (rel0[m] < 0.0) rel0[m] = rel[m];
+        }
+        return FESTUNG_OK;
+    };
+    auto add_scaled = [&](const std::vector<double> &sc) -> int {
+        for (int m = 0; m < nm; ++m) g.hscale[m] = sc[m];
+        FCK(cudaMemcpyAsync(g.dscale, g.hscale, nm * sizeof(double), cudaMemcpyHostToDevice, st));
+        k_add_batch<<<small_grid(K, c), 256, 0, st>>>(K, c->N, V.x, F.x, g.eprob, g.dscale);
+        ++c->launches;
+        FCK(cudaGetLastError());
+        return FESTUNG_OK;
+    };
+    int iters = 0, outer = 0;
+    bool all = false;
+    for (outer = 1; outer <= o.max_outer; ++outer) {
+        if ((rc = residuals())) return rc;
+        // members whose last sweep did not lower their residual: undo it
+        std::vector<double> undo(nm, 0.0);
+        bool any_undo = false, give_up = false;
+        for (int m = 0; m < nm; ++m) {
+            if (conv[m]) continue;
+            if (rel[m] <= o.tol || rn[m] == 0.0) {
+                conv[m] = 1;
+                outer_of[m] = outer;
+                continue;
+            }
+            if (applied[m] && !(rn[m] < prev[m])) {
+                undo[m] = -last[m];
+                any_undo = true;
+                if (++fails[m] >= 2) give_up = true;
+            } else if (applied[m]) {
+                fails[m] = 0;
+            }
+            applied[m] = 0;
+        }
+        if (any_undo) {
+            if ((rc = add_scaled(undo))) return rc;
+            if ((rc = residuals())) return rc;
+        }
+        all = true;
+        for (int m = 0; m < nm; ++m) all &= conv[m] != 0;
+        if (all || give_up || iters >= o.max_iter) break;
+        // normalised residuals of the open members; the sweep reduces by inner_tol, or by
+        // less when every open member needs less
+        double target = 0.5;
+        for (int m = 0; m < nm; ++m) {
+            g.hscale[m] = conv[m] ? 0.0 : 1.0 / rn[m];
+            if (!conv[m]) target = std::min(target, std::max(o.inner_tol, 0.5 * o.tol / rel[m]));
+        }
+        FCK(cudaMemcpyAsync(g.dscale, g.hscale, nm * sizeof(double), cudaMemcpyHostToDevice, st));
+        k_scale_batch<<<small_grid(K, c), 256, 0, st>>>(K, c->N, V.r, F.b, g.eprob, g.dscale);
+        ++c->launches;
+        FCK(cudaMemsetAsync(F.x, 0, KN * sizeof(float), st));
+        int it = 0;
+        bool cin = false;
+        double ir2, ib2;
+        rc = krylov_solve<float>(c, solver, dt, target, o.max_iter - iters, true, &it, &ir2, &ib2, &cin,
+                                 outer > 1 && any_undo);
+        if (rc) return rc;
+        iters += it;
+        if (!(ir2 < ib2)) break;  // no progress in FP32
+        std::vector<double> sc(nm, 0.0);
+        for (int m = 0; m < nm; ++m)
+            if (!conv[m]) {
+                sc[m] = rn[m];
+                last[m] = rn[m];
+                prev[m] = rn[m];
+                applied[m] = 1;
+            }
+        if ((rc = add_scaled(sc))) return rc;
+    }
+    if (outer > o.max_outer) outer = o.max_outer;
+    for (int m = 0; m < nm; ++m) {
+        if (infos) {
+            festung_step_info &in = infos[g.members[m]];
+            in.iterations = iters;
+            in.outer = conv[m] ? outer_of[m] : outer;
+            in.rel_residual = rel[m];
+            in.solver = solver;
+            in.symmetric = c->symmetric ? 1 : 0;
+            in.fp64_iterations = 0;
+            in.initial_rel_residual = rel0[m];
+        }
+    }
+    if (!all) {
+        b->err = "batched step did not converge for every problem";
+        return FESTUNG_ENOCONV;
+    }
+    if ((rc = commit_solution(c, dt, false))) return rc;
+    k_batch_scatter<<<small_grid(K, c), 256, 0, st>>>(K, c->N, g.eprob, g.dmem, c->dC);
+    ++c->launches;
+    FCK(cudaGetLastError());
+    FCK(cudaStreamSynchronize(st));
+    for (int m = 0; m < nm; ++m) {
+        festung_ctx *p = b->probs[g.members[m]];
+        p->hist = 0;  // the member's own step history no longer describes its state
+        ++p->state_gen;
+        g.gen[m] = p->state_gen;
+    }
+    return FESTUNG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int festung_batch_create(festung_ctx *const *problems, int nprob, festung_batch **out) {
+    g_create_err.clear();
+    if (!out || !problems || nprob < 1) {
+        g_create_err = "NULL argument or empty batch";
+        return FESTUNG_EINVAL;
+    }
+    *out = nullptr;
+    for (int q = 0; q < nprob; ++q) {
+        if (!problems[q] || problems[q]->p < 0) {
+            g_create_err = "problem " + std::to_string(q) + " is NULL or not set up";
+            return FESTUNG_ESTATE;
+        }
+        for (int r = 0; r < q; ++r)
+            if (problems[r] == problems[q]) {
+                g_create_err = "problem " + std::to_string(q) + " appears twice";
+                return FESTUNG_EINVAL;
+            }
+    }
+    festung_batch *b = new (std::nothrow) festung_batch();
+    if (!b) return FESTUNG_ENOMEM;
+    b->probs.assign(problems, problems + nprob);
+    for (int q = 0; q < nprob; ++q) {
+        const festung_ctx *c = problems[q];
+        BatchGroup *hit = nullptr;
+        for (auto &g : b->groups) {
+            const festung_ctx *f = b->probs[g.members[0]];
+            if (f->p == c->p && f->qT == c->qT && f->eta == c->eta) hit = &g;
+        }
+        if (!hit) {
+            b->groups.emplace_back();
+            hit = &b->groups.back();
+        }
+        hit->members.push_back(q);
+    }
+    for (auto &g : b->groups) {
+        int rc = build_group(b, g);
+        if (rc) {
+            g_create_err = b->err;
+            festung_batch_destroy(b);
+            return rc;
+        }
+    }
+    *out = b;
+    return FESTUNG_OK;
+}
+
+int festung_batch_set_stream(festung_batch *b, void *stream) {
+    if (!b) return FESTUNG_EINVAL;
+    b->stream = (cudaStream_t)stream;
+    for (auto &g : b->groups) festung_set_stream(g.u, stream);
+    return FESTUNG_OK;
+}
+
+int festung_batch_step(festung_batch *b, double dt, const festung_step_opts *opts, festung_step_info *infos) {
+    if (!b) return FESTUNG_EINVAL;
+    festung_step_opts o;
+    if (!step_options(opts, o) || !(dt > 0.0) || o.prec != FESTUNG_MIXED) {
+        b->err = "bad batch step arguments (FESTUNG_MIXED only)";
+        return FESTUNG_EINVAL;
+    }
+    for (auto &g : b->groups) {
+        int rc = solve_group(b, g, dt, o, infos);
+        if (rc) {
+            if (b->err.empty() || rc == FESTUNG_ECUDA) b->err = g.u->err;
+            return rc;
+        }
+    }
+    return FESTUNG_OK;
+}
+
+int festung_batch_launch_count(const festung_batch *b, int64_t *n) {
+    if (!b || !n) return FESTUNG_EINVAL;
+    *n = 0;
+    for (const auto &g : b->groups) *n += g.u->launches;
+    return FESTUNG_OK;
+}
+
+const char *festung_batch_last_error(const festung_batch *b) { return b ? b->err.c_str() : g_create_err.c_str(); }
+
+void festung_batch_destroy(festung_batch *b) {
+    if (!b) return;
+    for (auto &g : b->groups) free_group(g);
+    delete b;
 }
 
 }  // extern "C"

@@ -70,6 +70,8 @@ struct MeshOrder {
 void order_mesh(const double *coordV, const int32_t *V0T, int64_t K, const std::vector<double> &B_usr,
                 const std::vector<int32_t> &nbr_usr, MeshOrder &o);
 void tile_mesh(const std::vector<int32_t> &nbr, int64_t K, int TE, MeshOrder &o);
+// Dirichlet-lift flags (MeshOrder::lift) from internal neighbour codes.
+void lift_flags(const std::vector<int32_t> &nbr, int64_t K, std::vector<uint8_t> &lift);
 void order_and_tile(const double *coordV, const int32_t *V0T, int64_t K, const std::vector<double> &B_usr,
                     const std::vector<int32_t> &nbr_usr, int TE, MeshOrder &o);
 // Tile size (32..256, a multiple of 32) for K triangles when `resident` blocks run at
@@ -125,6 +127,7 @@ struct festung_ctx {
     double *dC = nullptr, *dD = nullptr, *dF = nullptr;
     double *dCprev = nullptr, *dCprev2 = nullptr;  // C^{n-1}, C^{n-2} for the extrapolated initial guess
     int hist = 0;                                  // number of valid previous states (0..2)
+    uint64_t state_gen = 0;                        // bumped whenever C changes (batches detect outside changes)
     double dt_prev = 0.0, dt_prev2 = 0.0;
     float *fD = nullptr;
     // double-float copies for the residual of the mixed-precision refinement

@@ -166,16 +166,20 @@ void order_mesh(const double *coordV, const int32_t *V0T, int64_t K, const std::
             o.nbr[n * K + i] = code >= 0 ? (int32_t)((int64_t(o.inv[code >> 2]) << 2) | (code & 3)) : code;
         }
     }
+    lift_flags(o.nbr, K, o.lift);
+}
+
+void lift_flags(const std::vector<int32_t> &nbr, int64_t K, std::vector<uint8_t> &lift) {
     // triangles whose right-hand side sees the Dirichlet lift: bit 0 = has a Dirichlet
     // edge, bit 1 = it or an interior neighbour has one
-    o.lift.assign(K, 0);
+    lift.assign(K, 0);
     for (int64_t i = 0; i < K; ++i)
         for (int n = 0; n < 3; ++n)
-            if (o.nbr[n * K + i] == -1) o.lift[i] |= 3;
+            if (nbr[n * K + i] == -1) lift[i] |= 3;
     for (int64_t i = 0; i < K; ++i)
         for (int n = 0; n < 3; ++n) {
-            const int32_t code = o.nbr[n * K + i];
-            if (code >= 0 && (o.lift[code >> 2] & 1)) o.lift[i] |= 2;
+            const int32_t code = nbr[n * K + i];
+            if (code >= 0 && (lift[code >> 2] & 1)) lift[i] |= 2;
         }
 }
 

@@ -24,6 +24,8 @@ EXPORTS = [
     "festung_get_state", "festung_apply", "festung_apply_noalloc", "festung_step", "festung_solve_stationary",
     "festung_l2_error", "festung_get_flux",
     "festung_element_order", "festung_launch_count", "festung_set_stream", "festung_last_error", "festung_destroy",
+    "festung_batch_create", "festung_batch_set_stream", "festung_batch_step", "festung_batch_launch_count",
+    "festung_batch_last_error", "festung_batch_destroy",
 ]
 
 
@@ -80,8 +82,17 @@ def load(path=None):
     lib.festung_last_error.restype = ctypes.c_char_p
     lib.festung_destroy.argtypes = [vp]
     lib.festung_destroy.restype = None
+    lib.festung_batch_create.argtypes = [vp, cint, ctypes.POINTER(vp)]
+    lib.festung_batch_set_stream.argtypes = [vp, vp]
+    lib.festung_batch_step.argtypes = [vp, dbl, ctypes.POINTER(StepOpts), vp]
+    lib.festung_batch_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
+    lib.festung_batch_last_error.argtypes = [vp]
+    lib.festung_batch_last_error.restype = ctypes.c_char_p
+    lib.festung_batch_destroy.argtypes = [vp]
+    lib.festung_batch_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("festung_last_error", "festung_destroy"):
+        if name not in ("festung_last_error", "festung_destroy", "festung_batch_last_error",
+                        "festung_batch_destroy"):
             getattr(lib, name).restype = cint
     if path is None:
         _lib = lib
@@ -224,3 +235,54 @@ class Solver:
         e = ctypes.c_double()
         self._check(self.lib.festung_l2_error(self.h, s.ctypes.data, ctypes.byref(e)))
         return e.value
+
+
+def _info_dict(info):
+    return {"iterations": info.iterations, "outer": info.outer, "rel_residual": info.rel_residual,
+            "solver": info.solver, "symmetric": info.symmetric, "fp64_iterations": info.fp64_iterations,
+            "initial_rel_residual": info.initial_rel_residual}
+
+
+class Batch:
+    """Independent problems (set-up Solver objects) stepped together (festung_batch_*)."""
+
+    def __init__(self, solvers):
+        self.lib = load()
+        self.solvers = list(solvers)
+        arr = (ctypes.c_void_p * len(self.solvers))(*[s.h.value for s in self.solvers])
+        h = ctypes.c_void_p()
+        rc = self.lib.festung_batch_create(arr, len(self.solvers), ctypes.byref(h))
+        if rc:
+            raise FestungError(rc, self.lib.festung_batch_last_error(None).decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc:
+            raise FestungError(rc, self.lib.festung_batch_last_error(self.h).decode())
+
+    def set_stream(self, stream):
+        """Run on a torch.cuda.Stream (or a raw cudaStream_t as int)."""
+        raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self._check(self.lib.festung_batch_set_stream(self.h, ctypes.c_void_p(raw)))
+
+    def step(self, dt, tol=1e-10, max_iter=20000, inner_tol=1e-2, max_outer=50, solver=0):
+        o = StepOpts(tol, max_iter, MIXED, inner_tol, max_outer, solver)
+        infos = (StepInfo * len(self.solvers))()
+        self._check(self.lib.festung_batch_step(self.h, dt, ctypes.byref(o), infos))
+        return [_info_dict(i) for i in infos]
+
+    def launch_count(self):
+        n = ctypes.c_int64()
+        self._check(self.lib.festung_batch_launch_count(self.h, ctypes.byref(n)))
+        return n.value
+
+    def close(self):
+        if self.h:
+            self.lib.festung_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -166,6 +166,42 @@ class GaussianField:
                 + (1 - a) * b * G[i, j + 1] + a * b * G[i + 1, j + 1])
 
 
+def grf_gradient(field, x, y):
+    """(g, g_x, g_y) of the bilinear interpolant of a GaussianField (its derivative
+    inside each grid cell)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    u = (x - field.lo) / field.dx
+    v = (y - field.lo) / field.dx
+    i = np.clip(np.floor(u).astype(np.int64), 0, field.m - 2)
+    j = np.clip(np.floor(v).astype(np.int64), 0, field.m - 2)
+    a, b = u - i, v - j
+    G = field.grid
+    g00, g10, g01, g11 = G[i, j], G[i + 1, j], G[i, j + 1], G[i + 1, j + 1]
+    g = (1 - a) * (1 - b) * g00 + a * (1 - b) * g10 + (1 - a) * b * g01 + a * b * g11
+    gx = ((1 - b) * (g10 - g00) + b * (g11 - g01)) / field.dx
+    gy = ((1 - a) * (g01 - g00) + a * (g11 - g10)) / field.dx
+    return g, gx, gy
+
+
+def grf_coefficient(field):
+    """d = exp(g) with its gradient, as the callable d(t, x, y) -> (d, d_x, d_y) that
+    Manufactured takes (time-independent)."""
+    def d(t, x, y):
+        g, gx, gy = grf_gradient(field, x, y)
+        e = np.exp(g)
+        return e, e * gx, e * gy
+    return d
+
+
+def batched_problems(nprob, seed):
+    """Specs of the batched workload: per problem an n x n grid, n ~ U{16..192}, order
+    p ~ U{1, 2, 3}, and its own Gaussian field length l ~ U[0.02, 0.2] (variance 1)."""
+    rng = np.random.default_rng(seed)
+    return [dict(n=int(rng.integers(16, 193)), p=int(rng.integers(1, 4)), length=float(rng.uniform(0.02, 0.2)),
+                 grf_seed=int(rng.integers(0, 2**31 - 1))) for _ in range(nprob)]
+
+
 def random_state(K, N, seed):
     """C0[k, j] ~ N(0, 1) / (1 + j): seeded normal coefficients scaled by basis index."""
     rng = np.random.default_rng(seed)
@@ -184,4 +220,8 @@ CONFIGS = {
                         dirichlet=(), neumann=(1, 2, 3, 4), coeff="grf", grf_length=0.05),
     "grf128_p3": dict(n=128, jitter=0.2, p=3, quad_order=None, dt=1e-3, steps=20,
                        dirichlet=(), neumann=(1, 2, 3, 4), coeff="grf", grf_length=0.05),
+    # 512 independent problems (specs from batched_problems), each with d = exp(g) of its own
+    # field, the manufactured c and f of square8_p1, Dirichlet data from c on the whole boundary
+    "batched512": dict(nprob=512, seed=2024, dt=1e-3, steps=20, tol=1e-10,
+                        dirichlet=(1, 2, 3, 4), neumann=(), coeff="grf-manufactured"),
 }
