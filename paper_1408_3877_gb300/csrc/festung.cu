@@ -395,8 +395,8 @@ int ensure_ws(festung_ctx *c) {
         Workspace &w = *c->ws;
         w.nblk = std::max(1, std::min(c->num_sms * 4, (int)((c->K + RED_THREADS - 1) / RED_THREADS)));
         // partials of the reducing kernels: 4 per block of a reduction or per tile of a
-        // fused apply epilogue
-        const int64_t tiles = (c->K + c->TE - 1) / c->TE;
+        // fused apply epilogue (tiles of at least 32 triangles, whatever the tiling)
+        const int64_t tiles = (c->K + 31) / 32;
         FCK(cudaMalloc(&w.part, sizeof(double) * 4 * std::max<int64_t>(w.nblk, tiles)));
         FCK(cudaMalloc(&w.scal, sizeof(KScal)));
         FCK(cudaMallocHost(&w.h_scal, sizeof(KScal)));
@@ -848,12 +848,69 @@ int choose_tiles(festung_ctx *c) {
     return FESTUNG_OK;
 }
 
+// Time the FP32 fused apply for tile sizes 96..256 (multiples of 32) around the
+// heuristic choice and keep the fastest.  Tiles that would not fit the FP64 traces in a
+// block's shared memory are skipped.  Only speed depends on the tiling.
+int autotune_tiles(festung_ctx *c, int *chosen) {
+    int rc = ensure_ws(c);
+    if (rc) return rc;
+    int dev = 0, optin = 0;
+    FCK(cudaGetDevice(&dev));
+    FCK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int64_t KN = c->K * c->N;
+    float *x = nullptr, *y = nullptr;
+    FCK(cudaMalloc(&x, KN * sizeof(float)));
+    cudaError_t e = cudaMalloc(&y, KN * sizeof(float));
+    if (e != cudaSuccess) {
+        cudaFree(x);
+        FCK(e);
+    }
+    cudaStream_t st = c->stream;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaMemsetAsync(x, 0, KN * sizeof(float), st);
+    const int64_t saved = c->launches;
+    int best = c->TE;
+    float best_ms = 1e30f;
+    for (int te = 96; te <= 256; te += 32) {
+        if ((e = retile(c, te)) != cudaSuccess) break;
+        if (fused_smem_bytes(c, c->nslot, true) + 16384 > (size_t)optin) continue;
+        launch_apply<float>(c, x, y, nullptr, nullptr, 1e-3f, nullptr, st);
+        cudaEventRecord(a, st);
+        for (int r = 0; r < 5; ++r) launch_apply<float>(c, x, y, nullptr, nullptr, 1e-3f, nullptr, st);
+        cudaEventRecord(b, st);
+        if ((e = cudaEventSynchronize(b)) != cudaSuccess) break;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = te;
+        }
+    }
+    c->launches = saved;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(x);
+    cudaFree(y);
+    FCK(e);
+    FCK(retile(c, best));
+    reset_graphs(c);  // captured iterations hold the old tiling
+    if (chosen) *chosen = best;
+    return FESTUNG_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
 // C ABI
 // ===========================================================================
 extern "C" {
+
+int festung_autotune(festung_ctx *c, int *tile) {
+    if (!ready(c)) return c ? FESTUNG_ESTATE : FESTUNG_EINVAL;
+    return autotune_tiles(c, tile);
+}
 
 int festung_mesh_create(const double *coordV, int64_t numV, const int32_t *V0T, int64_t numT,
                         const int8_t *bdr_type, festung_ctx **out) {
@@ -1560,10 +1617,13 @@ __global__ void k_batch_gather(int64_t K, int N, int E, const int32_t *eprob, co
     }
 }
 
-// members <- union: C
-__global__ void k_batch_scatter(int64_t K, int N, const int32_t *eprob, const MemberPtrs *mem, const double *C) {
+// members <- union: C, for the members with mask[q] != 0
+__global__ void k_batch_scatter(int64_t K, int N, const int32_t *eprob, const MemberPtrs *mem, const double *C,
+                                const double *mask) {
     ELEM_LOOP(i) {
-        const MemberPtrs m = mem[eprob[i]];
+        const int q = eprob[i];
+        if (mask[q] == 0.0) continue;
+        const MemberPtrs m = mem[q];
         const int64_t l = i - m.off;
         for (int j = 0; j < N; ++j) m.C[j * m.K + l] = C[j * K + i];
     }
@@ -1725,6 +1785,11 @@ int build_group(festung_batch *b, BatchGroup &g) {
         return e == cudaErrorMemoryAllocation ? FESTUNG_ENOMEM : FESTUNG_ECUDA;
     }
     g.gen.assign(nm, ~0ull);
+    int te = 0;
+    if ((rc = autotune_tiles(u, &te))) {
+        b->err = u->err;
+        return rc;
+    }
     return FESTUNG_OK;
 }
 
@@ -1756,7 +1821,8 @@ int solve_group(festung_batch *b, BatchGroup &g, double dt, const festung_step_o
     Vecs<float> &F = w.f;
     const int solver = o.solver ? o.solver : (c->symmetric ? FESTUNG_SOLVER_CG : FESTUNG_SOLVER_BICGSTAB);
     std::vector<double> rn(nm), bn(nm), rel(nm), rel0(nm, -1.0), prev(nm, -1.0), last(nm, 0.0);
-    std::vector<int> conv(nm, 0), outer_of(nm, 0), fails(nm, 0);
+    // state of a member: 0 open, 1 converged, 2 left to its own single-problem solve
+    std::vector<int> state(nm, 0), outer_of(nm, 0), fails(nm, 0);
     std::vector<char> applied(nm, 0);
     // per-member residual norms (S x in double-float arithmetic)
     auto residuals = [&]() -> int {
@@ -1784,23 +1850,24 @@ int solve_group(festung_batch *b, BatchGroup &g, double dt, const festung_step_o
         return FESTUNG_OK;
     };
     int iters = 0, outer = 0;
-    bool all = false;
+    bool reweight = false;
     for (outer = 1; outer <= o.max_outer; ++outer) {
         if ((rc = residuals())) return rc;
-        // members whose last sweep did not lower their residual: undo it
+        // members whose last sweep did not lower their residual: undo it; after two such
+        // sweeps a member is left to the single-problem solve
         std::vector<double> undo(nm, 0.0);
-        bool any_undo = false, give_up = false;
+        bool any_undo = false;
         for (int m = 0; m < nm; ++m) {
-            if (conv[m]) continue;
+            if (state[m]) continue;
             if (rel[m] <= o.tol || rn[m] == 0.0) {
-                conv[m] = 1;
+                state[m] = 1;
                 outer_of[m] = outer;
                 continue;
             }
             if (applied[m] && !(rn[m] < prev[m])) {
                 undo[m] = -last[m];
                 any_undo = true;
-                if (++fails[m] >= 2) give_up = true;
+                if (++fails[m] >= 2) state[m] = 2;
             } else if (applied[m]) {
                 fails[m] = 0;
             }
@@ -1810,15 +1877,16 @@ int solve_group(festung_batch *b, BatchGroup &g, double dt, const festung_step_o
             if ((rc = add_scaled(undo))) return rc;
             if ((rc = residuals())) return rc;
         }
-        all = true;
-        for (int m = 0; m < nm; ++m) all &= conv[m] != 0;
-        if (all || give_up || iters >= o.max_iter) break;
-        // normalised residuals of the open members; the sweep reduces by inner_tol, or by
-        // less when every open member needs less
+        int open = 0;
+        for (int m = 0; m < nm; ++m) open += state[m] == 0;
+        if (open == 0 || iters >= o.max_iter) break;
+        // normalised residuals of the open members.  Each open member has unit norm, so a
+        // union reduction by target / sqrt(open) reduces every member by target: inner_tol,
+        // or less when every open member needs less
         double target = 0.5;
         for (int m = 0; m < nm; ++m) {
-            g.hscale[m] = conv[m] ? 0.0 : 1.0 / rn[m];
-            if (!conv[m]) target = std::min(target, std::max(o.inner_tol, 0.5 * o.tol / rel[m]));
+            g.hscale[m] = state[m] ? 0.0 : 1.0 / rn[m];
+            if (!state[m]) target = std::min(target, std::max(o.inner_tol, 0.5 * o.tol / rel[m]));
         }
         FCK(cudaMemcpyAsync(g.dscale, g.hscale, nm * sizeof(double), cudaMemcpyHostToDevice, st));
         k_scale_batch<<<small_grid(K, c), 256, 0, st>>>(K, c->N, V.r, F.b, g.eprob, g.dscale);
@@ -1827,14 +1895,20 @@ int solve_group(festung_batch *b, BatchGroup &g, double dt, const festung_step_o
         int it = 0;
         bool cin = false;
         double ir2, ib2;
-        rc = krylov_solve<float>(c, solver, dt, target, o.max_iter - iters, true, &it, &ir2, &ib2, &cin,
-                                 outer > 1 && any_undo);
+        rc = krylov_solve<float>(c, solver, dt, target / std::sqrt((double)open), o.max_iter - iters, true, &it, &ir2,
+                                 &ib2, &cin, reweight);
         if (rc) return rc;
         iters += it;
-        if (!(ir2 < ib2)) break;  // no progress in FP32
+        reweight = any_undo;
+        if (!(ir2 < ib2)) {
+            // no progress in FP32: the open members are left to the single-problem solve
+            for (int m = 0; m < nm; ++m)
+                if (state[m] == 0) state[m] = 2;
+            break;
+        }
         std::vector<double> sc(nm, 0.0);
         for (int m = 0; m < nm; ++m)
-            if (!conv[m]) {
+            if (state[m] == 0) {
                 sc[m] = rn[m];
                 last[m] = rn[m];
                 prev[m] = rn[m];
@@ -1843,33 +1917,58 @@ int solve_group(festung_batch *b, BatchGroup &g, double dt, const festung_step_o
         if ((rc = add_scaled(sc))) return rc;
     }
     if (outer > o.max_outer) outer = o.max_outer;
+    // members still open after the sweeps (or the iteration bound) get the single solve
+    for (int m = 0; m < nm; ++m)
+        if (state[m] == 0) state[m] = 2;
     for (int m = 0; m < nm; ++m) {
+        if (!infos) break;
+        festung_step_info &in = infos[g.members[m]];
+        in.iterations = iters;
+        in.outer = state[m] == 1 ? outer_of[m] : outer;
+        in.rel_residual = rel[m];
+        in.solver = solver;
+        in.symmetric = c->symmetric ? 1 : 0;
+        in.fp64_iterations = 0;
+        in.initial_rel_residual = rel0[m];
+    }
+    // the members left over: their own step from C^n (still in the member context), with
+    // the FP64 fallback of the single-problem path
+    for (int m = 0; m < nm; ++m) {
+        if (state[m] != 2) continue;
+        festung_ctx *p = b->probs[g.members[m]];
+        festung_step_info in{};
+        rc = solve_system(p, dt, 1.0, &o, &in);
+        if (rc) {
+            b->err = "problem " + std::to_string(g.members[m]) + ": " + p->err;
+            return rc;
+        }
         if (infos) {
-            festung_step_info &in = infos[g.members[m]];
-            in.iterations = iters;
-            in.outer = conv[m] ? outer_of[m] : outer;
-            in.rel_residual = rel[m];
-            in.solver = solver;
-            in.symmetric = c->symmetric ? 1 : 0;
-            in.fp64_iterations = 0;
+            festung_step_info &out = infos[g.members[m]];
+            in.iterations += iters;
             in.initial_rel_residual = rel0[m];
+            out = in;
         }
     }
-    if (!all) {
-        b->err = "batched step did not converge for every problem";
-        return FESTUNG_ENOCONV;
-    }
+    // C of the union; the members solved by the union get theirs back
     if ((rc = commit_solution(c, dt, false))) return rc;
-    k_batch_scatter<<<small_grid(K, c), 256, 0, st>>>(K, c->N, g.eprob, g.dmem, c->dC);
+    for (int m = 0; m < nm; ++m) g.hscale[m] = state[m] == 1 ? 1.0 : 0.0;
+    FCK(cudaMemcpyAsync(g.dscale, g.hscale, nm * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_batch_scatter<<<small_grid(K, c), 256, 0, st>>>(K, c->N, g.eprob, g.dmem, c->dC, g.dscale);
     ++c->launches;
     FCK(cudaGetLastError());
     FCK(cudaStreamSynchronize(st));
+    bool any_single = false;
     for (int m = 0; m < nm; ++m) {
         festung_ctx *p = b->probs[g.members[m]];
-        p->hist = 0;  // the member's own step history no longer describes its state
-        ++p->state_gen;
+        any_single |= state[m] == 2;
+        if (state[m] == 1) {
+            p->hist = 0;  // the member's own step history no longer describes its state
+            ++p->state_gen;
+        }
         g.gen[m] = p->state_gen;
     }
+    // a member solved on its own differs from the union's C: the union's history restarts
+    if (any_single) c->hist = 0;
     return FESTUNG_OK;
 }
 

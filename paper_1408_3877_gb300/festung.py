@@ -24,7 +24,7 @@ EXPORTS = [
     "festung_get_state", "festung_apply", "festung_apply_noalloc", "festung_step", "festung_solve_stationary",
     "festung_l2_error", "festung_get_flux",
     "festung_element_order", "festung_launch_count", "festung_set_stream", "festung_last_error", "festung_destroy",
-    "festung_batch_create", "festung_batch_set_stream", "festung_batch_step", "festung_batch_launch_count",
+    "festung_autotune", "festung_batch_create", "festung_batch_set_stream", "festung_batch_step", "festung_batch_launch_count",
     "festung_batch_last_error", "festung_batch_destroy",
 ]
 
@@ -82,6 +82,7 @@ def load(path=None):
     lib.festung_last_error.restype = ctypes.c_char_p
     lib.festung_destroy.argtypes = [vp]
     lib.festung_destroy.restype = None
+    lib.festung_autotune.argtypes = [vp, ctypes.POINTER(cint)]
     lib.festung_batch_create.argtypes = [vp, cint, ctypes.POINTER(vp)]
     lib.festung_batch_set_stream.argtypes = [vp, vp]
     lib.festung_batch_step.argtypes = [vp, dbl, ctypes.POINTER(StepOpts), vp]
@@ -223,6 +224,12 @@ class Solver:
         return {"iterations": info.iterations, "outer": info.outer, "rel_residual": info.rel_residual,
                 "solver": info.solver, "symmetric": info.symmetric, "fp64_iterations": info.fp64_iterations,
                 "initial_rel_residual": info.initial_rel_residual}
+
+    def autotune(self):
+        """Pick the tile size of the fused apply by timing; returns it."""
+        t = ctypes.c_int()
+        self._check(self.lib.festung_autotune(self.h, ctypes.byref(t)))
+        return t.value
 
     def get_flux(self):
         """Z^1, Z^2 (each K x N, caller order) of the flux unknown z_h = -grad c_h from the current state."""

@@ -164,3 +164,20 @@ def test_apply_full_size_sampled(cfg):
         torch.cuda.synchronize()
         assert (y1 - y0).abs().max().item() <= 1e-9 * y0.abs().max().item()
     s.close()
+
+
+def test_autotune_changes_only_the_tiling():
+    import torch
+    from paper_1408_3877_gb300 import festung as F
+    cV, V0T, bdr = mesh(40, "mixed", seed=6)   # 3200 triangles: several tiles at every candidate size
+    s = gpu_solver(cV, V0T, bdr, 3)
+    s.set_coeff(samples(s, smooth_d))
+    x = torch.randn(s.N, s.K, dtype=torch.float64, device="cuda")
+    y0, y1 = torch.empty_like(x), torch.empty_like(x)
+    s.apply(x, y0, 0.01, F.FP64)
+    te = s.autotune()
+    assert te in range(96, 257, 32)
+    s.apply(x, y1, 0.01, F.FP64)
+    torch.cuda.synchronize()
+    assert float((y1 - y0).abs().max()) <= 1e-12 * float(y0.abs().max())
+    s.close()
