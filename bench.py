@@ -501,6 +501,110 @@ def run_batched(args):
                                              "failed_solves": f} for k, (v, f) in single.items()}}
 
 
+def run_learned(args):
+    """The learned warm start on the 128 x 128 p = 3 workload (d = exp(g) of a seeded
+    Gaussian field per seed, f = 0, zero flux, random initial state): trajectories of the
+    plain solver give training pairs (features of the step, the step's correction
+    C^{n+1} - C^n over the feature scale); the network is trained with its own kernels;
+    on held-out seeds every step is solved twice from the same C^n, once from the C^n guess
+    and once from C^n plus the network's correction, both to the same tolerance."""
+    import torch
+    from paper_1408_3877_gb300 import festung as F
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    c, cV, V0T, bdr = make_problem("grf128_p3", seed=12)
+    dt, steps, tol = c["dt"], 20, 1e-10
+    s = F.Solver(cV, V0T, bdr).setup(c["p"])
+    K, N = s.K, s.N
+    nf = 3 + 4 * N
+    order = s.element_order()
+    xy, _ = s.quad_points()
+
+    def start(seed):
+        g = W.GaussianField(10_000 + seed, c["grf_length"])
+        s.set_coeff(np.exp(g(xy[..., 0], xy[..., 1])))
+        s.set_source(None)
+        s.set_bc(None, None)
+        s.set_state(W.random_state(K, N, 20_000 + seed))
+
+    def features():
+        X = torch.empty(K, nf, dtype=torch.float32, device="cuda")
+        return X, s.warmstart_features(dt, X)
+
+    t0 = time.perf_counter()
+    Xs, Ts = [], []
+    plain_iters_train = []
+    for seed in range(args.train_seeds):
+        start(seed)
+        for _ in range(steps):
+            X, rs = features()
+            C0 = s.get_state()
+            info = s.step(dt, tol=tol, prec=F.MIXED)
+            plain_iters_train.append(info["iterations"])
+            T = (s.get_state() - C0)[order] / rs
+            Xs.append(X)
+            Ts.append(torch.tensor(T, dtype=torch.float32, device="cuda"))
+    X_all, T_all = torch.cat(Xs), torch.cat(Ts)
+    del Xs, Ts
+    gen_s = time.perf_counter() - t0
+    net = F.MLP(nf, N, seed=7)
+    rng = np.random.default_rng(0)
+    batch = 32768
+    t0 = time.perf_counter()
+    losses = []
+    for it in range(args.train_iters):
+        idx = torch.tensor(rng.integers(0, X_all.shape[0], batch), device="cuda")
+        losses.append(net.grad(X_all[idx].contiguous(), T_all[idx].contiguous()))
+        net.adam(2e-3 if it < args.train_iters // 2 else 5e-4)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    # evaluation on held-out seeds
+    res = {"plain": [], "learned": []}
+
+    def timed_step(delta):
+        s.set_guess(delta)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        info = s.step(dt, tol=tol, prec=F.MIXED)
+        b.record()
+        torch.cuda.synchronize()
+        return info, a.elapsed_time(b) / 1e3
+
+    Y = torch.empty(K, N, dtype=torch.float32, device="cuda")
+    for seed in range(args.train_seeds, args.train_seeds + args.eval_seeds):
+        start(seed)
+        for _ in range(steps):
+            C0 = s.get_state()
+            a = time.perf_counter()
+            X, rs = features()
+            net.forward(X, Y)
+            delta = np.empty((K, N))
+            delta[order] = rs * Y.double().cpu().numpy()
+            infer_s = time.perf_counter() - a
+            info_p, t_p = timed_step(np.zeros((K, N)))
+            s.set_state(C0)
+            info_l, t_l = timed_step(delta)
+            res["plain"].append((info_p["iterations"], t_p, info_p["rel_residual"]))
+            res["learned"].append((info_l["iterations"], t_l + infer_s, info_l["rel_residual"]))
+    net.close()
+    it_p = float(np.mean([r[0] for r in res["plain"]]))
+    it_l = float(np.mean([r[0] for r in res["learned"]]))
+    sp = float(np.mean([r[1] for r in res["plain"]]))
+    sl = float(np.mean([r[1] for r in res["learned"]]))
+    return {"metric": "Krylov iterations and sec per implicit step to 1e-10 rel. residual, learned warm start vs C^n guess",
+            "value": sl, "unit": "s/step", "n_gpus": 1, "higher_is_better": False, "dtype": "f32+bf16+dfloat+f64",
+            "data": "synthetic (seeded fields and initial states)",
+            "config": {"workload": "learned_grf128_p3", "triangles": K, "dofs": K * N, "dt": dt, "tol": tol,
+                       "train_seeds": args.train_seeds, "eval_seeds": args.eval_seeds, "steps_per_seed": steps,
+                       "train_rows": int(X_all.shape[0]), "train_iters": args.train_iters, "batch_rows": batch,
+                       "network": "%d-64-64-%d ReLU, BF16 weights, FP32 accumulate, Adam" % (nf, N)},
+            "iterations_plain": it_p, "iterations_learned": it_l, "s_per_step_plain": sp,
+            "s_per_step_learned_incl_inference": sl, "speedup": sp / sl,
+            "rel_residual_max": float(max(r[2] for v in res.values() for r in v)),
+            "train_loss_first_last": [losses[0], float(np.mean(losses[-20:]))],
+            "data_generation_s": gen_s, "training_s": train_s}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -513,7 +617,10 @@ def main():
                     help="only run the operator apply on WORKLOAD (for ncu captures); prints one line")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "dfloat"])
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--workload", default=None, choices=["batched512"],
+    ap.add_argument("--train-seeds", type=int, default=24, help="learned: training trajectories")
+    ap.add_argument("--eval-seeds", type=int, default=8, help="learned: held-out trajectories")
+    ap.add_argument("--train-iters", type=int, default=600, help="learned: Adam steps")
+    ap.add_argument("--workload", default=None, choices=["batched512", "learned"],
                     help="run another workload than the default step benchmark; prints one line")
     ap.add_argument("--nprob", type=int, default=None, help="batched512: number of problems (default 512)")
     args = ap.parse_args()
@@ -523,6 +630,8 @@ def main():
         line = profile_apply(args)
     elif args.workload == "batched512":
         line = run_batched(args)
+    elif args.workload == "learned":
+        line = run_learned(args)
     elif args.impl == "reference":
         line = run_reference(args)
     else:

@@ -9,7 +9,7 @@ namespace festung {
 template <>
 void launch_apply_bicg<float>(const festung_ctx *c, const float *x, float *y, float tau, int epi, const float *e1,
                               const float *e2, double *part, KScal *sc, unsigned int *counter, const int *skip,
-                              cudaStream_t st) {
+                              cudaStream_t st, const BatchView &bv) {
     const int tiles = (int)((c->K + c->TE - 1) / c->TE);
     c->launches += 1;
     dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
@@ -23,7 +23,7 @@ void launch_apply_bicg<float>(const festung_ctx *c, const float *x, float *y, fl
                                            : k_apply_fused<float, N, R2, R1, FUSED_EPI_OMEGA>;
         kern<<<tiles, FUSED_THREADS, smem, st>>>(x, y, c->fD, c->fB, c->dNbr, c->dSlot, c->dHaloPtr, c->dHalo,
                                                  c->dHaloSlot, c->K, c->TE, c->nslot, tau, (float)c->eta,
-                                                 (float)c->mass, c->fTab, skip, e1, e2, part, sc, counter);
+                                                 (float)c->mass, c->fTab, skip, e1, e2, part, sc, counter, bv);
     });
 }
 

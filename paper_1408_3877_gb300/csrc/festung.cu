@@ -345,6 +345,47 @@ __global__ void k_extrapolate3(int64_t n, const double *C, const double *Cp, con
         x[i] = l0 * C[i] + l1 * Cp[i] + l2 * Cpp[i];
 }
 
+// features of the learned warm start, first pass: sum over triangles of |M^{-1} r_k|^2
+// and of the mean of d_h (mode 0)
+__global__ void k_ws_sums(int64_t K, int N, const double *r, const double *D, const double *Bg, double *part) {
+    double acc[2] = {0.0, 0.0};
+    ELEM_LOOP(k) {
+        const double det = Bg[k] * Bg[3 * K + k] - Bg[K + k] * Bg[2 * K + k];
+        for (int j = 0; j < N; ++j) {
+            const double q = r[j * K + k] / det;
+            acc[0] += q * q;
+        }
+        acc[1] += D[k];
+    }
+    block_partials<2>(acc, part);
+}
+
+// second pass: per triangle (row k of X, F = 3 + 4 N values): d_h modes 0..2 over the
+// mean of mode 0; M^{-1} r of the triangle and of its neighbours across edges 0, 1, 2
+// (zero on the boundary), over the RMS value rs
+__global__ void k_ws_features(int64_t K, int N, const double *r, const double *D, const double *Bg,
+                              const int32_t *nbr, double inv_rs, double inv_d, float *X) {
+    const int F = 3 + 4 * N;
+    ELEM_LOOP(k) {
+        float *x = X + k * F;
+        for (int j = 0; j < 3; ++j) x[j] = j < N ? (float)(D[j * K + k] * inv_d) : 0.0f;
+        for (int e = 0; e < 4; ++e) {
+            int64_t q = k;
+            if (e > 0) {
+                const int code = nbr[(e - 1) * K + k];
+                q = code >= 0 ? (int64_t)(code >> 2) : -1;
+            }
+            float *y = x + 3 + e * N;
+            if (q < 0) {
+                for (int j = 0; j < N; ++j) y[j] = 0.0f;
+                continue;
+            }
+            const double det = Bg[q] * Bg[3 * K + q] - Bg[K + q] * Bg[2 * K + q];
+            for (int j = 0; j < N; ++j) y[j] = (float)(r[j * K + q] / det * inv_rs);
+        }
+    }
+}
+
 // x = C + a (C - C_prev)
 __global__ void k_extrapolate(int64_t n, const double *C, const double *Cp, double *x, double a) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -442,13 +483,15 @@ void free_ctx_device(festung_ctx *c) {
         c->ws = nullptr;
     }
     void *ptrs[] = {c->dTab, c->fTab, c->dC, c->dD, c->dF, c->fD, c->dCD, c->dGN, c->dSamp, c->dCprev, c->dCprev2,
-                    c->xD, c->xB, c->xTab};
+                    c->xD, c->xB, c->xTab, c->dGuess};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     c->dTab = nullptr;
     c->fTab = nullptr;
     c->xD = c->xB = c->xTab = nullptr;
     c->xD_valid = false;
+    c->dGuess = nullptr;
+    c->has_guess = false;
     c->dC = c->dD = c->dF = c->dCD = c->dGN = c->dSamp = c->dCprev = c->dCprev2 = nullptr;
     c->hist = 0;
     ++c->state_gen;
@@ -551,7 +594,7 @@ namespace festung {
 template <>
 void launch_apply_bicg<double>(const festung_ctx *c, const double *x, double *y, double tau, int epi,
                                const double *e1, const double *e2, double *part, KScal *sc, unsigned int *counter,
-                               const int *skip, cudaStream_t st) {
+                               const int *skip, cudaStream_t st, const BatchView &) {
     launch_apply<double>(c, x, y, nullptr, nullptr, tau, skip, st);
     const int g = c->ws->nblk;
     const int64_t n = c->K * c->N;
@@ -1185,6 +1228,7 @@ int festung_set_state(festung_ctx *c, const double *C, int is_samples, int loc) 
     }
     c->hist = 0;
     ++c->state_gen;
+    c->has_guess = false;
     FCK(cudaStreamSynchronize(c->stream));
     return FESTUNG_OK;
 }
@@ -1276,9 +1320,14 @@ int prepare_solve(festung_ctx *c, double dt, bool stationary, bool mixed) {
     FCK(cudaMemsetAsync(w.d_flags, 0, sizeof(int), st));
     launch_blockjacobi(c, w.P, w.Pb, dt, w.d_flags, st);
     FCK(cudaGetLastError());
-    // initial guess: extrapolation in time from the previous states when they exist,
-    // else C^n (the result does not depend on it beyond the tolerance)
-    if (!stationary && c->hist >= 2 && c->dt_prev > 0.0 && c->dt_prev2 > 0.0) {
+    // initial guess: C^n plus a correction given with festung_set_guess, else
+    // extrapolation in time from the previous states when they exist, else C^n (the
+    // result does not depend on it beyond the tolerance)
+    if (!stationary && c->has_guess) {
+        k_extrapolate3<<<small_grid(KN, c), 256, 0, st>>>(KN, c->dC, c->dGuess, c->dGuess, V.x, 1.0, 1.0, 0.0);
+        ++c->launches;
+        c->has_guess = false;
+    } else if (!stationary && c->hist >= 2 && c->dt_prev > 0.0 && c->dt_prev2 > 0.0) {
         // quadratic Lagrange extrapolation through t_{n-2}, t_{n-1}, t_n to t_{n+1}
         const double h0 = c->dt_prev2, h1 = c->dt_prev, h = dt;  // t_n - t_{n-1} = h1, t_{n-1} - t_{n-2} = h0
         const double tn = 0.0, tm1 = -h1, tm2 = -h1 - h0, tp = h;
@@ -1541,6 +1590,59 @@ int festung_get_flux(const festung_ctx *cc, double *Z, int loc) {
     return FESTUNG_OK;
 }
 
+int festung_warmstart_features(festung_ctx *c, double dt, float *X, double *scale) {
+    if (!ready(c)) return c ? FESTUNG_ESTATE : FESTUNG_EINVAL;
+    if (!X || !(dt > 0.0)) {
+        c->err = "X is NULL or dt <= 0";
+        return FESTUNG_EINVAL;
+    }
+    int rc = ensure_ws(c);
+    if (rc) return rc;
+    Workspace &w = *c->ws;
+    if ((rc = alloc_vecs<double>(c, w.d, true))) return rc;
+    const int64_t K = c->K, KN = K * c->N;
+    if (!w.scratch64) FCK(cudaMalloc(&w.scratch64, 2 * KN * sizeof(double)));
+    cudaStream_t st = c->stream;
+    Vecs<double> &V = w.d;
+    launch_rhs(c, w.scratch64, w.scratch64 + KN, V.b, dt, st);
+    if ((rc = apply_df(c, c->dC, nullptr, dt, st))) return rc;
+    k_residual_df<<<w.nblk, RED_THREADS, 0, st>>>(KN, V.b, w.ydf, V.r, w.part);
+    k_ws_sums<<<w.nblk, RED_THREADS, 0, st>>>(K, c->N, V.r, c->dD, c->dB, w.part);
+    k_fin_sums<<<1, 1024, 0, st>>>(w.res, w.part, w.nblk, 2);
+    c->launches += 3;
+    FCK(cudaGetLastError());
+    FCK(cudaMemcpyAsync(w.h_res, w.res, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    FCK(cudaStreamSynchronize(st));
+    const double rs = std::sqrt(w.h_res[0] / (double)KN), dm = w.h_res[1] / (double)K;
+    const double inv_rs = rs > 0.0 ? 1.0 / rs : 0.0, inv_d = dm != 0.0 ? 1.0 / dm : 1.0;
+    k_ws_features<<<small_grid(K, c), 256, 0, st>>>(K, c->N, V.r, c->dD, c->dB, c->dNbr, inv_rs, inv_d, X);
+    ++c->launches;
+    FCK(cudaGetLastError());
+    FCK(cudaStreamSynchronize(st));
+    if (scale) *scale = rs;
+    return FESTUNG_OK;
+}
+
+int festung_set_guess(festung_ctx *c, const double *delta, int loc) {
+    if (!ready(c)) return c ? FESTUNG_ESTATE : FESTUNG_EINVAL;
+    if (!delta) {
+        c->has_guess = false;
+        return FESTUNG_OK;
+    }
+    int rc = ensure_ws(c);
+    if (rc) return rc;
+    Workspace &w = *c->ws;
+    const int64_t KN = c->K * c->N;
+    if (!w.scratch64) FCK(cudaMalloc(&w.scratch64, 2 * KN * sizeof(double)));
+    if (!c->dGuess) FCK(cudaMalloc(&c->dGuess, KN * sizeof(double)));
+    double *tmp = w.scratch64;
+    if ((rc = upload_checked(c, delta, loc, tmp, KN))) return rc;
+    k_to_internal<<<small_grid(KN, c), 256, 0, c->stream>>>(tmp, c->dGuess, c->K, c->N, c->dPerm); ++c->launches;
+    FCK(cudaGetLastError());
+    c->has_guess = true;
+    return FESTUNG_OK;
+}
+
 int festung_element_order(const festung_ctx *c, int64_t *order) {
     if (!c || !order) return FESTUNG_EINVAL;
     for (int64_t k = 0; k < c->K; ++k) order[k] = c->perm[k];
@@ -1683,6 +1785,81 @@ __global__ void k_add_batch(int64_t K, int N, double *x, const float *Fx, const 
     }
 }
 
+// Krylov start for a batch: r = b - y (y = S x, or none for x = 0), the shadow residual
+// r0, p = v = 0, and per-problem (r, r), (b, b), (r0, r)
+template <typename T>
+__global__ void k_kr_init_b(int64_t K, int N, const T *b, const T *y, T *r, T *r0, T *p, T *v, BatchView bv,
+                            int reweight) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < K; base += stride) {
+        const int64_t k = base + threadIdx.x;
+        double acc[3] = {0.0, 0.0, 0.0};
+        int q = -1;
+        if (k < K) {
+            q = bv.eprob[k];
+            for (int j = 0; j < N; ++j) {
+                const int64_t i = j * K + k;
+                const T bi = b[i];
+                const T ri = y ? bi - y[i] : bi;
+                r[i] = ri;
+                T wgt = T(1);
+                if (reweight) {
+                    const uint32_t h = (uint32_t)(i * 2654435761ull) >> 8;
+                    wgt = T(0.5) + T(h & 0xffff) / T(65536);
+                }
+                r0[i] = ri * wgt;
+                p[i] = T(0);
+                v[i] = T(0);
+                acc[0] += (double)ri * (double)ri;
+                acc[1] += (double)bi * (double)bi;
+                acc[2] += (double)(ri * wgt) * (double)ri;
+            }
+        }
+        batch_add<3>(bv, q, acc);
+    }
+}
+
+// per-problem scalars at the start of a batch solve (one block); tolq: relative tolerances
+__global__ void k_fin_init_b(KScal *sc, BatchView bv, const double *tolq) {
+    int open = 0;
+    for (int q = threadIdx.x; q < bv.nprob; q += blockDim.x) {
+        const double r2 = bv.acc[q], b2 = bv.acc[bv.nprob + q], r0r = bv.acc[2 * bv.nprob + q];
+        bv.acc[q] = bv.acc[bv.nprob + q] = bv.acc[2 * bv.nprob + q] = 0.0;
+        KScal e{};
+        e.r2 = e.r2_0 = e.ss = r2;
+        e.b2 = b2;
+        e.tol2 = tolq[q] * tolq[q];
+        e.rho = r0r;
+        e.alpha = e.omega = 1.0;
+        e.first = 1;
+        e.done = (r2 <= e.tol2 * b2) ? 1 : 0;
+        sc[q] = e;
+        open |= !e.done;
+    }
+    const int any = __syncthreads_or(open);
+    if (threadIdx.x == 0) *bv.alldone = any ? 0 : 1;
+}
+
+// per-problem (b - y, b - y) and (b, b) into acc[q], acc[nprob + q]
+template <typename T>
+__global__ void k_residual_b(int64_t K, int N, const T *b, const T *y, BatchView bv) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < K; base += stride) {
+        const int64_t k = base + threadIdx.x;
+        double acc[2] = {0.0, 0.0};
+        int q = -1;
+        if (k < K) {
+            q = bv.eprob[k];
+            for (int j = 0; j < N; ++j) {
+                const double bi = (double)b[j * K + k], ri = bi - (double)y[j * K + k];
+                acc[0] += ri * ri;
+                acc[1] += bi * bi;
+            }
+        }
+        batch_add<2>(bv, q, acc);
+    }
+}
+
 struct BatchGroup {
     festung_ctx *u = nullptr;       // union context
     std::vector<int> members;       // problem indices
@@ -1692,9 +1869,26 @@ struct BatchGroup {
     MemberPtrs *dmem = nullptr;     // device table of member arrays
     double *dacc = nullptr, *hacc = nullptr;      // 2 per member: residual sums
     double *dscale = nullptr, *hscale = nullptr;  // 1 per member
+    // the members' own BiCGStab iterations on the union
+    KScal *sc = nullptr, *hsc = nullptr;  // per-member scalars (device / pinned host)
+    double *kacc = nullptr;               // 4 x members reduction sums
+    int *alldone = nullptr;               // device flag: every member's iteration is done
+    int *halldone = nullptr;              // its pinned host copy
+    double *dtol = nullptr, *htol = nullptr;  // members' relative tolerances of the sweep (device / pinned)
+    cudaGraphExec_t exec = nullptr;       // CHUNK iterations
+    double g_tau = 0.0;
+    int g_useP = -1;
 };
 
 void free_group(BatchGroup &g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    cudaFree(g.sc);
+    if (g.hsc) cudaFreeHost(g.hsc);
+    cudaFree(g.kacc);
+    cudaFree(g.alldone);
+    if (g.halldone) cudaFreeHost(g.halldone);
+    cudaFree(g.dtol);
+    if (g.htol) cudaFreeHost(g.htol);
     if (g.u) festung_destroy(g.u);
     cudaFree(g.eprob);
     cudaFree(g.dmem);
@@ -1780,7 +1974,16 @@ int build_group(festung_batch *b, BatchGroup &g) {
         (e = cudaMalloc(&g.dacc, 2 * nm * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc(&g.dscale, nm * sizeof(double))) != cudaSuccess ||
         (e = cudaMallocHost(&g.hacc, 2 * nm * sizeof(double))) != cudaSuccess ||
-        (e = cudaMallocHost(&g.hscale, nm * sizeof(double))) != cudaSuccess) {
+        (e = cudaMallocHost(&g.hscale, nm * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&g.sc, nm * sizeof(KScal))) != cudaSuccess ||
+        (e = cudaMallocHost(&g.hsc, nm * sizeof(KScal))) != cudaSuccess ||
+        (e = cudaMalloc(&g.kacc, 4 * nm * sizeof(double))) != cudaSuccess ||
+        (e = cudaMemset(g.kacc, 0, 4 * nm * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&g.alldone, sizeof(int))) != cudaSuccess ||
+        (e = cudaMallocHost(&g.halldone, sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(g.alldone, 0, sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&g.dtol, nm * sizeof(double))) != cudaSuccess ||
+        (e = cudaMallocHost(&g.htol, nm * sizeof(double))) != cudaSuccess) {
         b->err = std::string("CUDA: ") + cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? FESTUNG_ENOMEM : FESTUNG_ECUDA;
     }
@@ -1790,6 +1993,111 @@ int build_group(festung_batch *b, BatchGroup &g) {
         b->err = u->err;
         return rc;
     }
+    return FESTUNG_OK;
+}
+
+// The members' own BiCGStab iterations on the union (FP32, vectors w.f): every member
+// stops at its relative tolerance tolq[m] (a member with tolq <= 0 or a zero right-hand
+// side is done at once).  Returns per-member true ||b - S x||^2, ||b||^2 and the largest
+// iteration count; members whose recursion drifted or broke down are restarted (all
+// running members restart together, at most 8 times).
+int krylov_solve_batch(BatchGroup &g, double tau, const std::vector<double> &tolq, int max_iter, int *iters,
+                       std::vector<double> &r2, std::vector<double> &b2, bool reweight) {
+    festung_ctx *c = g.u;
+    Workspace &w = *c->ws;
+    Vecs<float> &V = w.f;
+    const int nm = (int)g.members.size();
+    const int64_t K = c->K;
+    const int N = c->N, gb = w.nblk;
+    cudaStream_t st = c->stream;
+    BatchView bv;
+    bv.eprob = g.eprob;
+    bv.acc = g.kacc;
+    bv.alldone = g.alldone;
+    bv.nprob = nm;
+    FCK(cudaStreamSynchronize(st));  // htol may still feed an earlier copy
+    for (int m = 0; m < nm; ++m) g.htol[m] = tolq[m];
+    FCK(cudaMemcpyAsync(g.dtol, g.htol, nm * sizeof(double), cudaMemcpyHostToDevice, st));
+    const __nv_bfloat16 *P = w.use_P ? w.Pb : nullptr;
+    int total = 0;
+    r2.assign(nm, 0.0);
+    b2.assign(nm, 0.0);
+    for (int restart = 0; restart < 8; ++restart) {
+        if (restart == 0) {
+            k_kr_init_b<float><<<gb, RED_THREADS, 0, st>>>(K, N, V.b, nullptr, V.r, V.r0, V.p, V.v, bv,
+                                                           reweight ? 1 : 0);
+        } else {
+            launch_apply<float>(c, V.x, V.t, V.Z1, V.Z2, (float)tau, nullptr, st);
+            k_kr_init_b<float><<<gb, RED_THREADS, 0, st>>>(K, N, V.b, V.t, V.r, V.r0, V.p, V.v, bv, 1);
+        }
+        k_fin_init_b<<<1, 1024, 0, st>>>(g.sc, bv, g.dtol);
+        c->launches += 2;
+        FCK(cudaGetLastError());
+        if (!g.exec || g.g_tau != tau || g.g_useP != (int)w.use_P) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+            cudaStream_t cs;
+            FCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            cudaGraph_t graph;
+            const int64_t saved = c->launches;
+            FCK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            for (int it = 0; it < CHUNK; ++it) {
+                dispatch(c->N, c->R2, c->R1, [&](auto n_, auto, auto) {
+                    constexpr int NN = decltype(n_)::value;
+                    k_bicg_next_b<float, NN><<<gb, RED_THREADS, 0, cs>>>((int)K, V.x, V.ph, V.sh, V.s, V.t, V.r, V.p,
+                                                                        V.v, P, V.inv, g.sc, bv);
+                });
+                launch_apply_bicg<float>(c, V.ph, V.v, (float)tau, FUSED_EPI_ALPHA, V.r0, nullptr, w.part, g.sc,
+                                         w.counter, g.alldone, cs, bv);
+                dispatch(c->N, c->R2, c->R1, [&](auto n_, auto, auto) {
+                    constexpr int NN = decltype(n_)::value;
+                    k_bicg_s_b<float, NN><<<gb, RED_THREADS, 0, cs>>>((int)K, V.r, V.s, V.v, V.sh, P, V.inv, g.sc,
+                                                                     bv, w.counter);
+                });
+                launch_apply_bicg<float>(c, V.sh, V.t, (float)tau, FUSED_EPI_OMEGA, V.s, V.r0, w.part, g.sc,
+                                         w.counter, g.alldone, cs, bv);
+            }
+            FCK(cudaStreamEndCapture(cs, &graph));
+            c->launches = saved;
+            FCK(cudaGraphInstantiate(&g.exec, graph, 0));
+            cudaGraphDestroy(graph);
+            cudaStreamDestroy(cs);
+            g.g_tau = tau;
+            g.g_useP = (int)w.use_P;
+        }
+        int hmax = 0;
+        bool again = false;
+        while (true) {
+            FCK(cudaMemcpyAsync(g.hsc, g.sc, nm * sizeof(KScal), cudaMemcpyDeviceToHost, st));
+            FCK(cudaMemcpyAsync(g.halldone, g.alldone, sizeof(int), cudaMemcpyDeviceToHost, st));
+            FCK(cudaStreamSynchronize(st));
+            const int alldone = *g.halldone;
+            hmax = 0;
+            for (int m = 0; m < nm; ++m) hmax = std::max(hmax, g.hsc[m].iter);
+            if (alldone || total + hmax >= max_iter) break;
+            FCK(cudaGraphLaunch(g.exec, st));
+            c->launches += 4 * CHUNK;
+        }
+        total += hmax;
+        k_bicg_finish_b<float><<<gb, RED_THREADS, 0, st>>>((int)K, N, V.x, V.ph, V.sh, g.sc, bv);
+        ++c->launches;
+        // true residuals per member
+        launch_apply<float>(c, V.x, V.t, V.Z1, V.Z2, (float)tau, nullptr, st);
+        k_residual_b<float><<<gb, RED_THREADS, 0, st>>>(K, N, V.b, V.t, bv);
+        ++c->launches;
+        FCK(cudaGetLastError());
+        FCK(cudaMemcpyAsync(g.hacc, g.kacc, 2 * nm * sizeof(double), cudaMemcpyDeviceToHost, st));
+        FCK(cudaMemsetAsync(g.kacc, 0, 2 * nm * sizeof(double), st));
+        FCK(cudaStreamSynchronize(st));
+        for (int m = 0; m < nm; ++m) {
+            r2[m] = g.hacc[m];
+            b2[m] = g.hacc[nm + m];
+            const double t2 = tolq[m] * tolq[m];
+            if (tolq[m] > 0.0 && (g.hsc[m].breakdown || r2[m] > 100.0 * t2 * b2[m])) again = true;
+        }
+        if (!again || total >= max_iter || restart >= 3) break;
+    }
+    *iters = total;
     return FESTUNG_OK;
 }
 
@@ -1819,7 +2127,7 @@ int solve_group(festung_batch *b, BatchGroup &g, double dt, const festung_step_o
     Workspace &w = *c->ws;
     Vecs<double> &V = w.d;
     Vecs<float> &F = w.f;
-    const int solver = o.solver ? o.solver : (c->symmetric ? FESTUNG_SOLVER_CG : FESTUNG_SOLVER_BICGSTAB);
+    const int solver = FESTUNG_SOLVER_BICGSTAB;  // the members' iterations on the union
     std::vector<double> rn(nm), bn(nm), rel(nm), rel0(nm, -1.0), prev(nm, -1.0), last(nm, 0.0);
     // state of a member: 0 open, 1 converged, 2 left to its own single-problem solve
     std::vector<int> state(nm, 0), outer_of(nm, 0), fails(nm, 0);
@@ -1880,32 +2188,23 @@ int solve_group(festung_batch *b, BatchGroup &g, double dt, const festung_step_o
         int open = 0;
         for (int m = 0; m < nm; ++m) open += state[m] == 0;
         if (open == 0 || iters >= o.max_iter) break;
-        // normalised residuals of the open members.  Each open member has unit norm, so a
-        // union reduction by target / sqrt(open) reduces every member by target: inner_tol,
-        // or less when every open member needs less
-        double target = 0.5;
-        for (int m = 0; m < nm; ++m) {
-            g.hscale[m] = state[m] ? 0.0 : 1.0 / rn[m];
-            if (!state[m]) target = std::min(target, std::max(o.inner_tol, 0.5 * o.tol / rel[m]));
-        }
+        // normalised residuals of the open members
+        for (int m = 0; m < nm; ++m) g.hscale[m] = state[m] ? 0.0 : 1.0 / rn[m];
         FCK(cudaMemcpyAsync(g.dscale, g.hscale, nm * sizeof(double), cudaMemcpyHostToDevice, st));
         k_scale_batch<<<small_grid(K, c), 256, 0, st>>>(K, c->N, V.r, F.b, g.eprob, g.dscale);
         ++c->launches;
         FCK(cudaMemsetAsync(F.x, 0, KN * sizeof(float), st));
+        // every open member runs its own BiCGStab on the union to its own target
+        std::vector<double> tolq(nm, 0.0), ir2, ib2;
+        for (int m = 0; m < nm; ++m)
+            if (!state[m]) tolq[m] = std::min(0.5, std::max(o.inner_tol, 0.5 * o.tol / rel[m]));
         int it = 0;
-        bool cin = false;
-        double ir2, ib2;
-        rc = krylov_solve<float>(c, solver, dt, target / std::sqrt((double)open), o.max_iter - iters, true, &it, &ir2,
-                                 &ib2, &cin, reweight);
+        rc = krylov_solve_batch(g, dt, tolq, o.max_iter - iters, &it, ir2, ib2, reweight);
         if (rc) return rc;
         iters += it;
         reweight = any_undo;
-        if (!(ir2 < ib2)) {
-            // no progress in FP32: the open members are left to the single-problem solve
-            for (int m = 0; m < nm; ++m)
-                if (state[m] == 0) state[m] = 2;
-            break;
-        }
+        for (int m = 0; m < nm; ++m)
+            if (!state[m] && !(ir2[m] < ib2[m])) state[m] = 2;  // no progress in FP32: single solve
         std::vector<double> sc(nm, 0.0);
         for (int m = 0; m < nm; ++m)
             if (state[m] == 0) {

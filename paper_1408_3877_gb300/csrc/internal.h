@@ -128,6 +128,8 @@ struct festung_ctx {
     double *dCprev = nullptr, *dCprev2 = nullptr;  // C^{n-1}, C^{n-2} for the extrapolated initial guess
     int hist = 0;                                  // number of valid previous states (0..2)
     uint64_t state_gen = 0;                        // bumped whenever C changes (batches detect outside changes)
+    double *dGuess = nullptr;                      // N x K correction of the next step's initial guess
+    bool has_guess = false;                        // dGuess holds a guess for the next step
     double dt_prev = 0.0, dt_prev2 = 0.0;
     float *fD = nullptr;
     // double-float copies for the residual of the mixed-precision refinement

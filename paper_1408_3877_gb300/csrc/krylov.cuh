@@ -21,6 +21,16 @@ struct KScal {
 
 constexpr int RED_THREADS = 256;
 
+// Per-problem view of the union of a batch of problems (krylov_solve_batch): every
+// problem runs its own Krylov iteration with its own KScal; reductions are summed per
+// problem.  eprob == nullptr: a single problem (block partials, one KScal).
+struct BatchView {
+    const int32_t *eprob = nullptr;  // K: problem of each element
+    double *acc = nullptr;           // 4 x nprob sums, zero between reductions
+    int *alldone = nullptr;          // 1 once every problem's iteration is done
+    int nprob = 1;
+};
+
 // Reductions of a BiCGStab step fused into the end of an operator apply y = S x:
 //   FUSED_EPI_NONE   none;
 //   FUSED_EPI_ALPHA  y = v:  (r0, v) -> alpha;

@@ -117,6 +117,46 @@ __device__ __forceinline__ void bicg_omega_scalars(double ts, double tt, double 
     }
 }
 
+// Per-problem sums of a batch: all 32 lanes of the warp call this (q < 0: no
+// contribution).  A warp whose lanes belong to one problem adds one atomic per value.
+template <int ND>
+__device__ __forceinline__ void batch_add(const BatchView &bv, int q, double (&v)[ND]) {
+    const unsigned full = 0xffffffffu;
+    const int q0 = __shfl_sync(full, q, 0);
+    if (__all_sync(full, q == q0 || q < 0)) {
+#pragma unroll
+        for (int p = 0; p < ND; ++p) {
+            double a = v[p];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(full, a, o);
+            if ((threadIdx.x & 31) == 0 && q0 >= 0) atomicAdd(bv.acc + p * bv.nprob + q0, a);
+        }
+    } else if (q >= 0) {
+#pragma unroll
+        for (int p = 0; p < ND; ++p) atomicAdd(bv.acc + p * bv.nprob + q, v[p]);
+    }
+}
+
+// In the last block of a batch reduction: for every problem whose iteration is still
+// running, f(q, sums) updates its scalars; the sums are reset to zero, and alldone is
+// set once no problem is running.  Called by all threads of the block.
+template <int ND, typename Fn>
+__device__ __forceinline__ void batch_finish(const BatchView &bv, KScal *sc, Fn f) {
+    int open = 0;
+    for (int q = threadIdx.x; q < bv.nprob; q += blockDim.x) {
+        double sum[ND];
+#pragma unroll
+        for (int p = 0; p < ND; ++p) {
+            sum[p] = __ldcg(bv.acc + p * bv.nprob + q);
+            bv.acc[p * bv.nprob + q] = 0.0;
+        }
+        if (!sc[q].done) f(q, sum);
+        open |= !sc[q].done;
+    }
+    const int any = __syncthreads_or(open);
+    if (threadIdx.x == 0) *bv.alldone = any ? 0 : 1;
+}
+
 // Sum of slot p of the partials of a grid of nblk blocks, read past L1 (the partials
 // were written by other SMs); called by all threads of one block.
 __device__ __forceinline__ double sum_partials_cg(const double *part, int p, int nblk) {
@@ -317,6 +357,124 @@ __global__ void __launch_bounds__(RED_THREADS) k_bicg_finish(int64_t n, T *__res
     const T alpha = (T)sc->alpha, omega = (T)sc->omega;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         x[i] += alpha * ph[i] + omega * sh[i];
+}
+
+// ---------------------------------------------------------------------------
+// BiCGStab on the union of a batch: the kernels above with per-problem scalars.
+// ---------------------------------------------------------------------------
+
+// k_bicg_next for a batch; the elements of problems whose iteration is done are left alone
+template <typename T, int N>
+__global__ void __launch_bounds__(RED_THREADS) k_bicg_next_b(int K, T *__restrict__ x, T *ph,
+                                                             const T *__restrict__ sh, const T *__restrict__ s,
+                                                             const T *__restrict__ t, T *__restrict__ r,
+                                                             T *__restrict__ pv, const T *__restrict__ v,
+                                                             const __nv_bfloat16 *__restrict__ P,
+                                                             const T *__restrict__ inv, const KScal *sc,
+                                                             BatchView bv) {
+    if (*bv.alldone) return;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+        const KScal &q = sc[bv.eprob[k]];
+        if (q.done) continue;
+        const bool first = q.first != 0;
+        const T alpha = (T)q.alpha, omega = (T)q.omega, beta = (T)q.beta;
+        T z[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const int i = j * K + k;
+            T ri;
+            if (first) {
+                ri = r[i];
+            } else {
+                x[i] += alpha * ph[i] + omega * sh[i];
+                ri = s[i] - omega * t[i];
+                r[i] = ri;
+            }
+            z[j] = ri + beta * (pv[i] - omega * v[i]);
+            pv[i] = z[j];
+        }
+        if (P) {
+            T y[N];
+            block_matvec<T, N>(P, K, k, z, y);
+#pragma unroll
+            for (int i = 0; i < N; ++i) ph[i * K + k] = y[i];
+        } else {
+            const T iv = inv[k];
+#pragma unroll
+            for (int i = 0; i < N; ++i) ph[i * K + k] = z[i] * iv;
+        }
+    }
+}
+
+// k_bicg_s for a batch: s = r - alpha_q v; sh = P^{-1} s; (s, s) per problem
+template <typename T, int N>
+__global__ void __launch_bounds__(RED_THREADS) k_bicg_s_b(int K, const T *__restrict__ r, T *__restrict__ s,
+                                                          const T *__restrict__ v, T *__restrict__ sh,
+                                                          const __nv_bfloat16 *__restrict__ P,
+                                                          const T *__restrict__ inv, KScal *sc, BatchView bv,
+                                                          unsigned int *counter) {
+    if (*bv.alldone) return;
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = blockIdx.x * blockDim.x; base < K; base += stride) {
+        const int k = base + threadIdx.x;
+        int q = -1;
+        double acc[1] = {0.0};
+        if (k < K && !sc[bv.eprob[k]].done) {
+            q = bv.eprob[k];
+            const T alpha = (T)sc[q].alpha;
+            T z[N];
+            Acc<T> a = Acc<T>(0);
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                const int i = j * K + k;
+                z[j] = r[i] - alpha * v[i];
+                s[i] = z[j];
+                a += (Acc<T>)z[j] * (Acc<T>)z[j];
+            }
+            acc[0] = (double)a;
+            if (P) {
+                T y[N];
+                block_matvec<T, N>(P, K, k, z, y);
+#pragma unroll
+                for (int i = 0; i < N; ++i) sh[i * K + k] = y[i];
+            } else {
+                const T iv = inv[k];
+#pragma unroll
+                for (int i = 0; i < N; ++i) sh[i * K + k] = z[i] * iv;
+            }
+        }
+        batch_add<1>(bv, q, acc);
+    }
+    if (last_block(counter)) {
+        batch_finish<1>(bv, sc, [&](int q, const double *sum) {
+            KScal &e = sc[q];
+            e.ss = sum[0];
+            if (sum[0] <= e.tol2 * e.b2) {
+                e.sconv = 1;
+                e.r2 = sum[0];
+                e.iter += 1;
+                e.done = 1;
+            }
+        });
+        if (threadIdx.x == 0) *counter = 0;
+    }
+}
+
+// After the iterations of a batch: each problem's owed update (x += alpha ph once it
+// converged on s, else x += alpha ph + omega sh when pending)
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_bicg_finish_b(int K, int N, T *__restrict__ x,
+                                                               const T *__restrict__ ph, const T *__restrict__ sh,
+                                                               const KScal *sc, BatchView bv) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+        const KScal &q = sc[bv.eprob[k]];
+        const T alpha = (T)q.alpha, omega = (T)q.omega;
+        if (q.sconv) {
+            for (int j = 0; j < N; ++j) x[j * K + k] += alpha * ph[j * K + k];
+        } else if (q.pending) {
+            for (int j = 0; j < N; ++j) x[j * K + k] += alpha * ph[j * K + k] + omega * sh[j * K + k];
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
     const int32_t *__restrict__ halo, const int16_t *__restrict__ halo_slot, int64_t K, int TE, int NS, T tau,
     T eta, T mass, const T *__restrict__ tabg, const int *__restrict__ skip, const T *__restrict__ e1 = nullptr,
     const T *__restrict__ e2 = nullptr, double *part = nullptr, KScal *sc = nullptr,
-    unsigned int *counter = nullptr) {
+    unsigned int *counter = nullptr, BatchView bv = BatchView()) {
     constexpr bool kBigVolume = R2 * N > 150;
     constexpr int NP = ((N * (int)sizeof(T) + 15) / 16) * 16 / (int)sizeof(T);
     constexpr int VOL = kBigVolume ? 3 * R2 * NP : 4;
@@ -405,8 +405,18 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
         }
     }
     const int start = blockIdx.x * TE;
-    const int cnt = (Ki - start) < TE ? (Ki - start) : TE;
-    const int h0 = halo_ptr[blockIdx.x], nh = halo_ptr[blockIdx.x + 1] - h0;
+    int cnt = (Ki - start) < TE ? (Ki - start) : TE;
+    const int h0 = halo_ptr[blockIdx.x];
+    int nh = halo_ptr[blockIdx.x + 1] - h0;
+    if constexpr (EPI != FUSED_EPI_NONE) {
+        if (bv.eprob && cnt > 0) {
+            // a batch: a tile whose problems have all finished their iterations does no
+            // work (it still takes part in the reduction)
+            bool idle = true;
+            for (int q = bv.eprob[start]; q <= bv.eprob[start + cnt - 1]; ++q) idle = idle && sc[q].done;
+            if (idle) cnt = nh = 0;
+        }
+    }
     const int i = threadIdx.x;
     const int hstride = blockDim.x - TE;
     T z1[N], z2[N], d[N];
@@ -474,6 +484,23 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
         }
     }
     if constexpr (EPI != FUSED_EPI_NONE) {
+        if (bv.eprob) {
+            // a batch: sums per problem, scalars of every running problem in the last block
+            double dd[ND];
+#pragma unroll
+            for (int q = 0; q < ND; ++q) dd[q] = (double)dots[q];
+            batch_add<ND>(bv, i < cnt ? bv.eprob[start + i] : -1, dd);
+            if (last_block(counter)) {
+                batch_finish<ND>(bv, sc, [&](int q, const double *sum) {
+                    if constexpr (EPI == FUSED_EPI_ALPHA)
+                        bicg_alpha_scalars(sum[0], sc + q);
+                    else
+                        bicg_omega_scalars(sum[0], sum[1], sum[2], sum[3], sc + q);
+                });
+                if (threadIdx.x == 0) *counter = 0;
+            }
+            return;
+        }
         block_partials_any<ND>(dots, part);
         if (last_block(counter)) {
             double sum[ND];

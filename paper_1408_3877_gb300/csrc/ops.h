@@ -21,9 +21,12 @@ void launch_apply(const festung_ctx *c, const T *x, T *y, T *Z1, T *Z2, T tau, c
 // (r0, s), (r0, y) -> omega, rho, beta.  FP32: fused into the end of the apply (part
 // holds 4 partials per tile); FP64: a reduction pass of its own after the apply (part
 // holds 4 partials per block of that pass).
+// bv: the union of a batch (per-problem scalars sc[q] and sums; FP32 only), or the
+// default view of a single problem.
 template <typename T>
 void launch_apply_bicg(const festung_ctx *c, const T *x, T *y, T tau, int epi, const T *e1, const T *e2,
-                       double *part, KScal *sc, unsigned int *counter, const int *skip, cudaStream_t st);
+                       double *part, KScal *sc, unsigned int *counter, const int *skip, cudaStream_t st,
+                       const BatchView &bv = BatchView());
 
 // y = S x in double-float arithmetic (dfloat.cuh) from the double-float copies of D,
 // the geometry and the tables (c->xD, c->xB, c->xTab); x, y: N x K double-floats.

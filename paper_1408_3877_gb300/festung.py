@@ -24,7 +24,10 @@ EXPORTS = [
     "festung_get_state", "festung_apply", "festung_apply_noalloc", "festung_step", "festung_solve_stationary",
     "festung_l2_error", "festung_get_flux",
     "festung_element_order", "festung_launch_count", "festung_set_stream", "festung_last_error", "festung_destroy",
-    "festung_autotune", "festung_batch_create", "festung_batch_set_stream", "festung_batch_step", "festung_batch_launch_count",
+    "festung_autotune", "festung_warmstart_features", "festung_set_guess",
+    "festung_mlp_create", "festung_mlp_sizes", "festung_mlp_set_stream", "festung_mlp_forward", "festung_mlp_grad",
+    "festung_mlp_adam", "festung_mlp_get", "festung_mlp_set", "festung_mlp_last_error", "festung_mlp_destroy",
+    "festung_batch_create", "festung_batch_set_stream", "festung_batch_step", "festung_batch_launch_count",
     "festung_batch_last_error", "festung_batch_destroy",
 ]
 
@@ -83,6 +86,20 @@ def load(path=None):
     lib.festung_destroy.argtypes = [vp]
     lib.festung_destroy.restype = None
     lib.festung_autotune.argtypes = [vp, ctypes.POINTER(cint)]
+    lib.festung_warmstart_features.argtypes = [vp, dbl, vp, ctypes.POINTER(dbl)]
+    lib.festung_set_guess.argtypes = [vp, vp, cint]
+    lib.festung_mlp_create.argtypes = [cint, cint, ctypes.c_uint64, ctypes.POINTER(vp)]
+    lib.festung_mlp_sizes.argtypes = [vp, ctypes.POINTER(cint), ctypes.POINTER(cint), ctypes.POINTER(cint)]
+    lib.festung_mlp_set_stream.argtypes = [vp, vp]
+    lib.festung_mlp_forward.argtypes = [vp, vp, vp, i64]
+    lib.festung_mlp_grad.argtypes = [vp, vp, vp, i64, ctypes.POINTER(dbl)]
+    lib.festung_mlp_adam.argtypes = [vp, dbl]
+    lib.festung_mlp_get.argtypes = [vp, vp, vp]
+    lib.festung_mlp_set.argtypes = [vp, vp]
+    lib.festung_mlp_last_error.argtypes = []
+    lib.festung_mlp_last_error.restype = ctypes.c_char_p
+    lib.festung_mlp_destroy.argtypes = [vp]
+    lib.festung_mlp_destroy.restype = None
     lib.festung_batch_create.argtypes = [vp, cint, ctypes.POINTER(vp)]
     lib.festung_batch_set_stream.argtypes = [vp, vp]
     lib.festung_batch_step.argtypes = [vp, dbl, ctypes.POINTER(StepOpts), vp]
@@ -93,7 +110,7 @@ def load(path=None):
     lib.festung_batch_destroy.restype = None
     for name in EXPORTS:
         if name not in ("festung_last_error", "festung_destroy", "festung_batch_last_error",
-                        "festung_batch_destroy"):
+                        "festung_batch_destroy", "festung_mlp_last_error", "festung_mlp_destroy"):
             getattr(lib, name).restype = cint
     if path is None:
         _lib = lib
@@ -231,6 +248,18 @@ class Solver:
         self._check(self.lib.festung_autotune(self.h, ctypes.byref(t)))
         return t.value
 
+    def warmstart_features(self, dt, X):
+        """Features of the learned warm start into the device tensor X (K x (3 + 4N), FP32,
+        internal order); returns the residual scale rs."""
+        sc = ctypes.c_double()
+        self._check(self.lib.festung_warmstart_features(self.h, dt, ctypes.c_void_p(X.data_ptr()), ctypes.byref(sc)))
+        return sc.value
+
+    def set_guess(self, delta):
+        """The next step starts from C^n + delta (K x N, caller order; None clears it)."""
+        p, loc, keep = _ptr(delta, np.float64)
+        self._check(self.lib.festung_set_guess(self.h, p, loc))
+
     def get_flux(self):
         """Z^1, Z^2 (each K x N, caller order) of the flux unknown z_h = -grad c_h from the current state."""
         Z = np.empty((2, self.K, self.N))
@@ -286,6 +315,63 @@ class Batch:
     def close(self):
         if self.h:
             self.lib.festung_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MLP:
+    """The warm-start network (festung_mlp_*): in -> 64 -> 64 -> out, BF16 weights."""
+
+    def __init__(self, n_in, n_out, seed=0):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        rc = self.lib.festung_mlp_create(n_in, n_out, seed, ctypes.byref(h))
+        if rc:
+            raise FestungError(rc, self.lib.festung_mlp_last_error().decode())
+        self.h = h
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self.lib.festung_mlp_sizes(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+        self.n_in, self.n_out, self.n_params = a.value, b.value, c.value
+
+    def _check(self, rc):
+        if rc:
+            raise FestungError(rc, self.lib.festung_mlp_last_error().decode())
+
+    def set_stream(self, stream):
+        raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self._check(self.lib.festung_mlp_set_stream(self.h, ctypes.c_void_p(raw)))
+
+    def forward(self, X, Y):
+        self._check(self.lib.festung_mlp_forward(self.h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()),
+                                                 X.shape[0]))
+
+    def grad(self, X, T):
+        loss = ctypes.c_double()
+        self._check(self.lib.festung_mlp_grad(self.h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(T.data_ptr()),
+                                              X.shape[0], ctypes.byref(loss)))
+        return loss.value
+
+    def adam(self, lr):
+        self._check(self.lib.festung_mlp_adam(self.h, lr))
+
+    def get(self):
+        p = np.empty(self.n_params, dtype=np.float32)
+        g = np.empty(self.n_params, dtype=np.float32)
+        self._check(self.lib.festung_mlp_get(self.h, p.ctypes.data, g.ctypes.data))
+        return p, g
+
+    def set(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        self._check(self.lib.festung_mlp_set(self.h, p.ctypes.data))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.festung_mlp_destroy(self.h)
             self.h = None
 
     def __del__(self):
