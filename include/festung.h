@@ -258,11 +258,12 @@ void festung_mlp_destroy(festung_mlp *net);
  * Many problems (each its own context, set up, with its own mesh, order, coefficient,
  * source and boundary data) advance by one implicit-Euler step together.  Problems of
  * the same p, quadrature and eta form a group whose meshes are joined into one internal
- * mesh: each kernel of the step runs over all problems of the group at once.  The
- * Krylov iteration runs on the block-diagonal union system; refinement and convergence
- * are per problem (each problem's residual is normalised on its own, and every problem
- * reaches tol on its own residual).  The paper has no counterpart: it solves one
- * problem at a time.
+ * mesh: each kernel of the step runs over all problems of the group at once.  Every
+ * problem runs its own BiCGStab iteration (its own scalars, reductions summed per
+ * problem) and its own refinement, and reaches tol on its own residual; tiles of
+ * problems that have finished do no work.  A problem the group cannot finish is stepped
+ * on its own (the single-problem path with its FP64 fallback).  The paper has no
+ * counterpart: it solves one problem at a time.
  *
  * festung_batch_create: problems[0..nprob) stay owned by the caller and must outlive the
  * batch; they must not be set up again while in it.  Their data are set with the usual

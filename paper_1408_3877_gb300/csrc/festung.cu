@@ -2002,7 +2002,8 @@ int build_group(festung_batch *b, BatchGroup &g) {
 // iteration count; members whose recursion drifted or broke down are restarted (all
 // running members restart together, at most 8 times).
 int krylov_solve_batch(BatchGroup &g, double tau, const std::vector<double> &tolq, int max_iter, int *iters,
-                       std::vector<double> &r2, std::vector<double> &b2, bool reweight) {
+                       std::vector<double> &r2, std::vector<double> &b2, std::vector<char> &finished,
+                       bool reweight) {
     festung_ctx *c = g.u;
     Workspace &w = *c->ws;
     Vecs<float> &V = w.f;
@@ -2065,16 +2066,25 @@ int krylov_solve_batch(BatchGroup &g, double tau, const std::vector<double> &tol
             g.g_tau = tau;
             g.g_useP = (int)w.use_P;
         }
-        int hmax = 0;
+        int hmax = 0, it90 = -1, open0 = 0;
         bool again = false;
+        for (int m = 0; m < nm; ++m) open0 += tolq[m] > 0.0;
         while (true) {
             FCK(cudaMemcpyAsync(g.hsc, g.sc, nm * sizeof(KScal), cudaMemcpyDeviceToHost, st));
             FCK(cudaMemcpyAsync(g.halldone, g.alldone, sizeof(int), cudaMemcpyDeviceToHost, st));
             FCK(cudaStreamSynchronize(st));
             const int alldone = *g.halldone;
             hmax = 0;
-            for (int m = 0; m < nm; ++m) hmax = std::max(hmax, g.hsc[m].iter);
+            int done = 0;
+            for (int m = 0; m < nm; ++m) {
+                hmax = std::max(hmax, g.hsc[m].iter);
+                done += tolq[m] > 0.0 && g.hsc[m].done;
+            }
             if (alldone || total + hmax >= max_iter) break;
+            // stragglers: once 90 % of the members are done, the rest get as many iterations
+            // again (and one chunk) before they are left to their own solves
+            if (it90 < 0 && 10 * done >= 9 * open0) it90 = hmax;
+            if (it90 >= 0 && hmax >= 2 * it90 + CHUNK) break;
             FCK(cudaGraphLaunch(g.exec, st));
             c->launches += 4 * CHUNK;
         }
@@ -2089,11 +2099,13 @@ int krylov_solve_batch(BatchGroup &g, double tau, const std::vector<double> &tol
         FCK(cudaMemcpyAsync(g.hacc, g.kacc, 2 * nm * sizeof(double), cudaMemcpyDeviceToHost, st));
         FCK(cudaMemsetAsync(g.kacc, 0, 2 * nm * sizeof(double), st));
         FCK(cudaStreamSynchronize(st));
+        finished.assign(nm, 1);
         for (int m = 0; m < nm; ++m) {
             r2[m] = g.hacc[m];
             b2[m] = g.hacc[nm + m];
             const double t2 = tolq[m] * tolq[m];
-            if (tolq[m] > 0.0 && (g.hsc[m].breakdown || r2[m] > 100.0 * t2 * b2[m])) again = true;
+            if (tolq[m] > 0.0 && !g.hsc[m].done) finished[m] = 0;  // cut off as a straggler
+            else if (tolq[m] > 0.0 && (g.hsc[m].breakdown || r2[m] > 100.0 * t2 * b2[m])) again = true;
         }
         if (!again || total >= max_iter || restart >= 3) break;
     }
@@ -2199,12 +2211,13 @@ int solve_group(festung_batch *b, BatchGroup &g, double dt, const festung_step_o
         for (int m = 0; m < nm; ++m)
             if (!state[m]) tolq[m] = std::min(0.5, std::max(o.inner_tol, 0.5 * o.tol / rel[m]));
         int it = 0;
-        rc = krylov_solve_batch(g, dt, tolq, o.max_iter - iters, &it, ir2, ib2, reweight);
+        std::vector<char> finished;
+        rc = krylov_solve_batch(g, dt, tolq, o.max_iter - iters, &it, ir2, ib2, finished, reweight);
         if (rc) return rc;
         iters += it;
         reweight = any_undo;
         for (int m = 0; m < nm; ++m)
-            if (!state[m] && !(ir2[m] < ib2[m])) state[m] = 2;  // no progress in FP32: single solve
+            if (!state[m] && (!finished[m] || !(ir2[m] < ib2[m]))) state[m] = 2;  // left to a single solve
         std::vector<double> sc(nm, 0.0);
         for (int m = 0; m < nm; ++m)
             if (state[m] == 0) {
