@@ -584,8 +584,9 @@ def run_learned(args):
             info_p, t_p = timed_step(np.zeros((K, N)))
             s.set_state(C0)
             info_l, t_l = timed_step(delta)
-            res["plain"].append((info_p["iterations"], t_p, info_p["rel_residual"]))
-            res["learned"].append((info_l["iterations"], t_l + infer_s, info_l["rel_residual"]))
+            res["plain"].append((info_p["iterations"], t_p, info_p["rel_residual"], info_p["initial_rel_residual"]))
+            res["learned"].append((info_l["iterations"], t_l + infer_s, info_l["rel_residual"],
+                                   info_l["initial_rel_residual"]))
     net.close()
     it_p = float(np.mean([r[0] for r in res["plain"]]))
     it_l = float(np.mean([r[0] for r in res["learned"]]))
@@ -601,6 +602,8 @@ def run_learned(args):
             "iterations_plain": it_p, "iterations_learned": it_l, "s_per_step_plain": sp,
             "s_per_step_learned_incl_inference": sl, "speedup": sp / sl,
             "rel_residual_max": float(max(r[2] for v in res.values() for r in v)),
+            "initial_rel_residual_median_plain": float(np.median([r[3] for r in res["plain"]])),
+            "initial_rel_residual_median_learned": float(np.median([r[3] for r in res["learned"]])),
             "train_loss_first_last": [losses[0], float(np.mean(losses[-20:]))],
             "data_generation_s": gen_s, "training_s": train_s}
 
