@@ -526,25 +526,28 @@ def run_learned(args):
         s.set_bc(None, None)
         s.set_state(W.random_state(K, N, 20_000 + seed))
 
-    def features():
+    def features(weights=False):
         X = torch.empty(K, nf, dtype=torch.float32, device="cuda")
-        return X, s.warmstart_features(dt, X)
+        Wt = torch.empty(K, N, dtype=torch.float32, device="cuda") if weights else None
+        rs = s.warmstart_features(dt, X, Wt)
+        return (X, rs, Wt) if weights else (X, rs)
 
     t0 = time.perf_counter()
-    Xs, Ts = [], []
+    Xs, Ts, Ws = [], [], []
     plain_iters_train = []
     for seed in range(args.train_seeds):
         start(seed)
         for _ in range(steps):
-            X, rs = features()
+            X, rs, Wt = features(weights=True)
             C0 = s.get_state()
             info = s.step(dt, tol=tol, prec=F.MIXED)
             plain_iters_train.append(info["iterations"])
             T = (s.get_state() - C0)[order] / rs
             Xs.append(X)
+            Ws.append(Wt)
             Ts.append(torch.tensor(T, dtype=torch.float32, device="cuda"))
-    X_all, T_all = torch.cat(Xs), torch.cat(Ts)
-    del Xs, Ts
+    X_all, T_all, W_all = torch.cat(Xs), torch.cat(Ts), torch.cat(Ws)
+    del Xs, Ts, Ws
     gen_s = time.perf_counter() - t0
     net = F.MLP(nf, N, seed=7)
     rng = np.random.default_rng(0)
@@ -553,19 +556,20 @@ def run_learned(args):
     losses = []
     for it in range(args.train_iters):
         idx = torch.tensor(rng.integers(0, X_all.shape[0], batch), device="cuda")
-        losses.append(net.grad(X_all[idx].contiguous(), T_all[idx].contiguous()))
+        losses.append(net.grad(X_all[idx].contiguous(), T_all[idx].contiguous(),
+                               W_all[idx].contiguous() if args.weighted_loss else None))
         net.adam(2e-3 if it < args.train_iters // 2 else 5e-4)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     # evaluation on held-out seeds
     res = {"plain": [], "learned": []}
 
-    def timed_step(delta):
+    def timed_step(delta, prec=F.MIXED):
         s.set_guess(delta)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         a.record()
-        info = s.step(dt, tol=tol, prec=F.MIXED)
+        info = s.step(dt, tol=tol, prec=prec, max_iter=100000)
         b.record()
         torch.cuda.synchronize()
         return info, a.elapsed_time(b) / 1e3
@@ -581,9 +585,23 @@ def run_learned(args):
             delta = np.empty((K, N))
             delta[order] = rs * Y.double().cpu().numpy()
             infer_s = time.perf_counter() - a
-            info_p, t_p = timed_step(np.zeros((K, N)))
-            s.set_state(C0)
-            info_l, t_l = timed_step(delta)
+            if seed == args.train_seeds:  # the plain FP64 solve from the C^n guess, first held-out seed
+                try:
+                    info_f, t_f = timed_step(np.zeros((K, N)), F.FP64)
+                    res.setdefault("fp64", []).append((info_f["iterations"], t_f, info_f["rel_residual"],
+                                                       info_f["initial_rel_residual"]))
+                except F.FestungError:
+                    res.setdefault("fp64_failed", []).append(1)
+                s.set_state(C0)
+            try:
+                info_p, t_p = timed_step(np.zeros((K, N)))
+                s.set_state(C0)
+                info_l, t_l = timed_step(delta)
+            except F.FestungError:
+                # a step that neither guess finishes within the iteration bound: counted, skipped
+                res.setdefault("failed", []).append(1)
+                s.set_state(C0)  # the failed step leaves C^n; the seed goes on from it
+                continue
             res["plain"].append((info_p["iterations"], t_p, info_p["rel_residual"], info_p["initial_rel_residual"]))
             res["learned"].append((info_l["iterations"], t_l + infer_s, info_l["rel_residual"],
                                    info_l["initial_rel_residual"]))
@@ -598,10 +616,17 @@ def run_learned(args):
             "config": {"workload": "learned_grf128_p3", "triangles": K, "dofs": K * N, "dt": dt, "tol": tol,
                        "train_seeds": args.train_seeds, "eval_seeds": args.eval_seeds, "steps_per_seed": steps,
                        "train_rows": int(X_all.shape[0]), "train_iters": args.train_iters, "batch_rows": batch,
-                       "network": "%d-64-64-%d ReLU, BF16 weights, FP32 accumulate, Adam" % (nf, N)},
+                       "network": "%d-64-64-%d ReLU, BF16 weights, FP32 accumulate, Adam" % (nf, N),
+                       "loss": "weighted by sqrt(diag S / 2|T|)" if args.weighted_loss else "unweighted"},
             "iterations_plain": it_p, "iterations_learned": it_l, "s_per_step_plain": sp,
             "s_per_step_learned_incl_inference": sl, "speedup": sp / sl,
-            "rel_residual_max": float(max(r[2] for v in res.values() for r in v)),
+            "s_per_step_plain_fp64_first_heldout_seed": (float(np.mean([r[1] for r in res["fp64"]]))
+                                                         if res.get("fp64") else None),
+            "iterations_plain_fp64_first_heldout_seed": (float(np.mean([r[0] for r in res["fp64"]]))
+                                                         if res.get("fp64") else None),
+            "plain_fp64_steps_not_converged_in_100000_iterations": len(res.get("fp64_failed", [])),
+            "steps_skipped_not_converged": len(res.get("failed", [])),
+            "rel_residual_max": float(max(r[2] for k in ("plain", "learned") for r in res[k])),
             "initial_rel_residual_median_plain": float(np.median([r[3] for r in res["plain"]])),
             "initial_rel_residual_median_learned": float(np.median([r[3] for r in res["learned"]])),
             "train_loss_first_last": [losses[0], float(np.mean(losses[-20:]))],
@@ -623,6 +648,8 @@ def main():
     ap.add_argument("--train-seeds", type=int, default=24, help="learned: training trajectories")
     ap.add_argument("--eval-seeds", type=int, default=8, help="learned: held-out trajectories")
     ap.add_argument("--train-iters", type=int, default=600, help="learned: Adam steps")
+    ap.add_argument("--weighted-loss", type=int, default=1,
+                    help="learned: weight the loss by sqrt(diag S / 2|T|) (1) or not (0)")
     ap.add_argument("--workload", default=None, choices=["batched512", "learned"],
                     help="run another workload than the default step benchmark; prints one line")
     ap.add_argument("--nprob", type=int, default=None, help="batched512: number of problems (default 512)")

@@ -224,11 +224,13 @@ int festung_autotune(festung_ctx *ctx, int *tile);
  * d_h modes 0..2 over the mean of mode 0, then M^{-1} r of k and of its neighbours across
  * local edges 0, 1, 2 (zeros on the boundary), divided by rs = RMS of M^{-1} r over all
  * coefficients; *scale = rs.  A network output y (K x N rows) then means the correction
- * rs y.  Synchronises the context's stream.
+ * rs y.  Wt (device, K x N FP32, or NULL): loss weights sqrt(S_kk[j][j] / 2|T_k|) from the
+ * diagonal blocks of S, large for the stiff modes that a wrong correction turns into
+ * residual.  Synchronises the context's stream.
  * festung_set_guess: the next festung_step starts from C^n + delta (delta K x N in the
  * caller's order like the state, host or device; NULL clears it).  Used once; set_state
  * and setup clear it. */
-int festung_warmstart_features(festung_ctx *ctx, double dt, float *X, double *scale);
+int festung_warmstart_features(festung_ctx *ctx, double dt, float *X, float *Wt, double *scale);
 int festung_set_guess(festung_ctx *ctx, const double *delta, int loc);
 
 /* The network: in -> 64 -> 64 -> out, ReLU after the hidden layers, BF16 weights with an
@@ -236,8 +238,9 @@ int festung_set_guess(festung_ctx *ctx, const double *delta, int loc);
  * b1 (64), W2 (64 x 64), b2, W3 (out x 64), b3 (out).  Weights start Glorot-uniform from
  * a seeded generator, biases at 0.  in <= 96, out <= 32.
  *   forward: Y = net(X) for rows x in inputs (device FP32, row-major; Y rows x out);
- *   grad:    gradient of (1 / 2 rows) sum (net(X) - T)^2 over the rows into the net's
- *            gradient buffer (replacing it), the loss into *loss (may be NULL);
+ *   grad:    gradient of (1 / 2 rows) sum (Wt (net(X) - T))^2 over the rows into the
+ *            net's gradient buffer (replacing it), the loss into *loss (may be NULL); Wt:
+ *            rows x out weights (device) or NULL for 1;
  *   adam:    one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr on the
  *            FP32 master, then the BF16 copy;
  *   get/set: the FP32 master parameters (and the last gradient) on the host.
@@ -247,7 +250,7 @@ int festung_mlp_create(int n_in, int n_out, uint64_t seed, festung_mlp **out);
 int festung_mlp_sizes(const festung_mlp *net, int *n_in, int *n_out, int *n_params);
 int festung_mlp_set_stream(festung_mlp *net, void *cuda_stream);
 int festung_mlp_forward(festung_mlp *net, const float *X, float *Y, int64_t rows);
-int festung_mlp_grad(festung_mlp *net, const float *X, const float *T, int64_t rows, double *loss);
+int festung_mlp_grad(festung_mlp *net, const float *X, const float *T, const float *Wt, int64_t rows, double *loss);
 int festung_mlp_adam(festung_mlp *net, double lr);
 int festung_mlp_get(const festung_mlp *net, float *params, float *grad);
 int festung_mlp_set(festung_mlp *net, const float *params);

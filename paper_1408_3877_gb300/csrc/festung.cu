@@ -386,6 +386,18 @@ __global__ void k_ws_features(int64_t K, int N, const double *r, const double *D
     }
 }
 
+// loss weights of the learned warm start: sqrt(S_kk[j][j] / 2|T_k|) from the FP32 diagonal
+// blocks P[(i N + j) K + k]
+__global__ void k_ws_weights(int64_t K, int N, const float *P, const double *Bg, float *Wt) {
+    ELEM_LOOP(k) {
+        const double det = Bg[k] * Bg[3 * K + k] - Bg[K + k] * Bg[2 * K + k];
+        for (int j = 0; j < N; ++j) {
+            const double q = (double)P[((int64_t)j * N + j) * K + k] / det;
+            Wt[k * N + j] = (float)std::sqrt(q > 0.0 ? q : 0.0);
+        }
+    }
+}
+
 // x = C + a (C - C_prev)
 __global__ void k_extrapolate(int64_t n, const double *C, const double *Cp, double *x, double a) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -1590,7 +1602,7 @@ int festung_get_flux(const festung_ctx *cc, double *Z, int loc) {
     return FESTUNG_OK;
 }
 
-int festung_warmstart_features(festung_ctx *c, double dt, float *X, double *scale) {
+int festung_warmstart_features(festung_ctx *c, double dt, float *X, float *Wt, double *scale) {
     if (!ready(c)) return c ? FESTUNG_ESTATE : FESTUNG_EINVAL;
     if (!X || !(dt > 0.0)) {
         c->err = "X is NULL or dt <= 0";
@@ -1617,6 +1629,14 @@ int festung_warmstart_features(festung_ctx *c, double dt, float *X, double *scal
     const double inv_rs = rs > 0.0 ? 1.0 / rs : 0.0, inv_d = dm != 0.0 ? 1.0 / dm : 1.0;
     k_ws_features<<<small_grid(K, c), 256, 0, st>>>(K, c->N, V.r, c->dD, c->dB, c->dNbr, inv_rs, inv_d, X);
     ++c->launches;
+    if (Wt) {
+        // diagonal blocks of S (FP32) for the loss weights
+        if (!w.P) FCK(cudaMalloc(&w.P, (size_t)c->N * c->N * c->K * sizeof(float)));
+        if (!w.Pb) FCK(cudaMalloc(&w.Pb, (size_t)((c->N * c->N + 7) / 8) * c->K * 16));
+        launch_blockjacobi(c, w.P, w.Pb, dt, w.d_flags, st);
+        k_ws_weights<<<small_grid(K, c), 256, 0, st>>>(K, c->N, w.P, c->dB, Wt);
+        ++c->launches;
+    }
     FCK(cudaGetLastError());
     FCK(cudaStreamSynchronize(st));
     if (scale) *scale = rs;

@@ -11,6 +11,7 @@
 // The flux unknowns never leave the chip, and every trace is evaluated once per slot.
 #pragma once
 
+#include "dfloat.cuh"
 #include "dispatch.h"
 #include "krylov_kernels.cuh"
 #include "ldg_kernels.cuh"
@@ -139,13 +140,43 @@ __device__ __forceinline__ void tr_load(const T *tr, int f, int n, int slot, int
 
 // Phase A1 for triangle e at shared-memory slot `slot`: loads x and d_h of e and stores
 // their traces on the three edges.
+// Double-float arithmetic is 10-20 instructions per multiply-add: fully unrolled, its
+// trace loops alone would not fit the instruction cache.  Its traces are therefore
+// computed with the point loop rolled and stored point by point.
+template <typename T>
+constexpr bool kCompactCode = std::is_same<T, dfloat>::value;
+
+// trace of c on own edge n into field f of the slot's shared-memory traces (compact code)
+template <typename T, int N, int R2, int R1, int n>
+__device__ __forceinline__ void trace_store(const T (&c)[N], T *tr, int f, int NS, int slot) {
+    {
+        using L = TraceLayout<T, R1>;
+        const CTab<T, N, R2, R1> &t = c_tab<T, N, R2, R1>;
+#pragma unroll 1
+        for (int r = 0; r < R1; ++r) {
+            T v = T(0);
+#pragma unroll
+            for (int j = 0; j < N; ++j) v += t.phiE[(n * R1 + r) * N + j] * c[j];
+            if constexpr (L::vec)
+                tr[((size_t)(f * 3 + n) * NS + slot) * L::RP + r] = v;
+            else
+                tr[((size_t)(f * 3 + n) * R1 + r) * NS + slot] = v;
+        }
+    }
+}
+
 template <typename T, int N, int R2, int R1, int n>
 __device__ __forceinline__ void a1_edge(const T (&x)[N], const T (&d)[N], T *tr, int NS, int slot) {
-    T xt[R1], dt[R1];
-    ctrace<T, N, R2, R1, n>(x, xt);
-    ctrace<T, N, R2, R1, n>(d, dt);
-    tr_store<T, R1>(tr, 0, n, slot, NS, xt);
-    tr_store<T, R1>(tr, 1, n, slot, NS, dt);
+    if constexpr (kCompactCode<T>) {
+        trace_store<T, N, R2, R1, n>(x, tr, 0, NS, slot);
+        trace_store<T, N, R2, R1, n>(d, tr, 1, NS, slot);
+    } else {
+        T xt[R1], dt[R1];
+        ctrace<T, N, R2, R1, n>(x, xt);
+        ctrace<T, N, R2, R1, n>(d, dt);
+        tr_store<T, R1>(tr, 0, n, slot, NS, xt);
+        tr_store<T, R1>(tr, 1, n, slot, NS, dt);
+    }
 }
 
 template <typename T, int N, int R2, int R1>
@@ -189,23 +220,41 @@ __device__ __forceinline__ void a2_edge(const T *phiE_s, const T *__restrict__ X
     }
     T nx, ny;
     edge_normal(n, b11, b12, b21, b22, nx, ny);
+    if constexpr (kCompactCode<T>) {
+#pragma unroll 1
+        for (int r = 0; r < R1; ++r) {
+            const T fx = nx * f[r], fy = ny * f[r];
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-        T v = T(0);
+            for (int i = 0; i < N; ++i) {
+                const T w = t.wphiE[(n * R1 + r) * N + i];
+                a1[i] += w * fx;
+                a2[i] += w * fy;
+            }
+        }
+    } else {
 #pragma unroll
-        for (int r = 0; r < R1; ++r) v += t.wphiE[(n * R1 + r) * N + i] * f[r];
-        a1[i] += nx * v;
-        a2[i] += ny * v;
+        for (int i = 0; i < N; ++i) {
+            T v = T(0);
+#pragma unroll
+            for (int r = 0; r < R1; ++r) v += t.wphiE[(n * R1 + r) * N + i] * f[r];
+            a1[i] += nx * v;
+            a2[i] += ny * v;
+        }
     }
 }
 
 template <typename T, int N, int R2, int R1, int n>
 __device__ __forceinline__ void slot_ztrace(const T (&z1)[N], const T (&z2)[N], T *tr, int NS, int slot) {
-    T t1[R1], t2[R1];
-    ctrace<T, N, R2, R1, n>(z1, t1);
-    ctrace<T, N, R2, R1, n>(z2, t2);
-    tr_store<T, R1>(tr, 2, n, slot, NS, t1);
-    tr_store<T, R1>(tr, 3, n, slot, NS, t2);
+    if constexpr (kCompactCode<T>) {
+        trace_store<T, N, R2, R1, n>(z1, tr, 2, NS, slot);
+        trace_store<T, N, R2, R1, n>(z2, tr, 3, NS, slot);
+    } else {
+        T t1[R1], t2[R1];
+        ctrace<T, N, R2, R1, n>(z1, t1);
+        ctrace<T, N, R2, R1, n>(z2, t2);
+        tr_store<T, R1>(tr, 2, n, slot, NS, t1);
+        tr_store<T, R1>(tr, 3, n, slot, NS, t2);
+    }
 }
 
 // Phase A2 for triangle e at slot `slot`: Z^m = -M^{-1} B_m x, and the traces of z^1,
@@ -215,21 +264,41 @@ __device__ __forceinline__ void slot_a2(const T *phiE_s, const T *__restrict__ X
                                         const int32_t *__restrict__ nbr, int Ki, int e, const int (&nsl)[3],
                                         T *tr, int NS, int slot, T (&z1)[N], T (&z2)[N]) {
     const CTab<T, N, R2, R1> &t = c_tab<T, N, R2, R1>;
-    T x[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) x[j] = X[j * Ki + e];
     const T b11 = Bg[e], b12 = Bg[Ki + e], b21 = Bg[2 * Ki + e], b22 = Bg[3 * Ki + e];
+    // -H^m x with H^1 = B22 H^_1 - B21 H^_2, H^2 = -B12 H^_1 + B11 H^_2 (Sec. 3.6.2)
+    if constexpr (kCompactCode<T>) {
+        T h1[N], h2[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-        T h1 = T(0), h2 = T(0);
-#pragma unroll
+        for (int i = 0; i < N; ++i) h1[i] = h2[i] = T(0);
+#pragma unroll 1
         for (int j = 0; j < N; ++j) {
-            h1 += t.H1[i * N + j] * x[j];
-            h2 += t.H2[i * N + j] * x[j];
+            const T xj = X[j * Ki + e];
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                h1[i] += t.H1[i * N + j] * xj;
+                h2[i] += t.H2[i * N + j] * xj;
+            }
         }
-        // -H^m x with H^1 = B22 H^_1 - B21 H^_2, H^2 = -B12 H^_1 + B11 H^_2 (Sec. 3.6.2)
-        z1[i] = -(b22 * h1 - b21 * h2);
-        z2[i] = -(b11 * h2 - b12 * h1);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            z1[i] = -(b22 * h1[i] - b21 * h2[i]);
+            z2[i] = -(b11 * h2[i] - b12 * h1[i]);
+        }
+    } else {
+        T x[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) x[j] = X[j * Ki + e];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            T h1 = T(0), h2 = T(0);
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                h1 += t.H1[i * N + j] * x[j];
+                h2 += t.H2[i * N + j] * x[j];
+            }
+            z1[i] = -(b22 * h1 - b21 * h2);
+            z2[i] = -(b11 * h2 - b12 * h1);
+        }
     }
     const int c0 = nbr[e], c1 = nbr[Ki + e], c2 = nbr[2 * Ki + e];
     a2_edge<T, N, R2, R1, 0>(phiE_s, X, Ki, c0, nsl[0], tr, NS, slot, b11, b12, b21, b22, z1, z2);
@@ -277,12 +346,21 @@ __device__ __forceinline__ void tile_edge(int code, int sl, const T *tr, int NS,
 #pragma unroll
         for (int r = 0; r < R1; ++r) g[r] = dm[r] * (nx * am[r] + ny * bm[r]) + eta * xm[r];
     }
+    if constexpr (kCompactCode<T>) {
+#pragma unroll 1
+        for (int r = 0; r < R1; ++r) {
+            const T gr = g[r];
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-        T v = T(0);
+            for (int j = 0; j < N; ++j) acc[j] += t.wphiE[(n * R1 + r) * N + j] * gr;
+        }
+    } else {
 #pragma unroll
-        for (int r = 0; r < R1; ++r) v += t.wphiE[(n * R1 + r) * N + j] * g[r];
-        acc[j] += v;
+        for (int j = 0; j < N; ++j) {
+            T v = T(0);
+#pragma unroll
+            for (int r = 0; r < R1; ++r) v += t.wphiE[(n * R1 + r) * N + j] * g[r];
+            acc[j] += v;
+        }
     }
 }
 

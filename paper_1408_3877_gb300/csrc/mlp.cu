@@ -7,7 +7,7 @@
 // backward pass keeps each thread's hidden activations in shared memory and adds the
 // weight gradients of its rows into a shared-memory copy of the gradient, which each
 // block then adds to the global gradient.  Loss: (1 / 2R) sum over rows and outputs of
-// (y - t)^2.
+// (w (y - t))^2, with per-output row weights w (1 when none are given).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -91,8 +91,8 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_forward(Dims d, const __nv_
 
 // gradient of the loss over rows; grad (d.total FP32) and loss (double) are accumulated
 __global__ void __launch_bounds__(MLP_THREADS) k_mlp_grad(Dims d, const __nv_bfloat16 *wb, const float *master,
-                                                          const float *X, const float *T, int64_t rows,
-                                                          float *grad, double *loss) {
+                                                          const float *X, const float *T, const float *Wt,
+                                                          int64_t rows, float *grad, double *loss) {
     extern __shared__ float smem[];
     float *sp = smem;
     float *sg = sp + d.total;                           // block's gradient
@@ -107,11 +107,12 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_grad(Dims d, const __nv_bfl
         for (int j = 0; j < d.in; ++j) x[j] = X[r * d.in + j];
         float *h1 = h, *h2 = h + HID, *dl = h + 2 * HID;
         forward_row(d, sp, x, h1, h2, y);
-        // output layer: e = y - t; dW3 = e h2^T / R, db3 = e / R
+        // output layer: e = w (y - t); dW3 = w e h2^T / R, db3 = w e / R
         for (int o = 0; o < d.out; ++o) {
-            const float e = y[o] - T[r * d.out + o];
+            const float w = Wt ? Wt[r * d.out + o] : 1.0f;
+            const float e = w * (y[o] - T[r * d.out + o]);
             lsum += 0.5 * (double)e * (double)e;
-            y[o] = e * inv_rows;
+            y[o] = w * e * inv_rows;
             atomicAdd(sg + d.b3 + o, y[o]);
             for (int j = 0; j < HID; ++j) atomicAdd(sg + d.w3 + o * HID + j, y[o] * h2[j]);
         }
@@ -275,15 +276,15 @@ int festung_mlp_forward(festung_mlp *n, const float *X, float *Y, int64_t rows) 
     return e == cudaSuccess ? FESTUNG_OK : mlp_fail(n, e);
 }
 
-int festung_mlp_grad(festung_mlp *n, const float *X, const float *T, int64_t rows, double *loss) {
+int festung_mlp_grad(festung_mlp *n, const float *X, const float *T, const float *Wt, int64_t rows, double *loss) {
     if (!n || !X || !T || rows < 1) return FESTUNG_EINVAL;
     cudaError_t e;
     if ((e = cudaMemsetAsync(n->grad, 0, n->d.total * sizeof(float), n->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(n->loss, 0, sizeof(double), n->stream)) != cudaSuccess)
         return mlp_fail(n, e);
     const int grid = (int)std::min<int64_t>((rows + MLP_THREADS - 1) / MLP_THREADS, (int64_t)n->sms * 2);
-    k_mlp_grad<<<grid, MLP_THREADS, grad_smem(n->d), n->stream>>>(n->d, n->wb, n->master, X, T, rows, n->grad,
-                                                                  n->loss);
+    k_mlp_grad<<<grid, MLP_THREADS, grad_smem(n->d), n->stream>>>(n->d, n->wb, n->master, X, T, Wt, rows,
+                                                                  n->grad, n->loss);
     if ((e = cudaGetLastError()) != cudaSuccess) return mlp_fail(n, e);
     if (loss) {
         if ((e = cudaMemcpyAsync(n->hloss, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->stream)) !=

@@ -86,13 +86,13 @@ def load(path=None):
     lib.festung_destroy.argtypes = [vp]
     lib.festung_destroy.restype = None
     lib.festung_autotune.argtypes = [vp, ctypes.POINTER(cint)]
-    lib.festung_warmstart_features.argtypes = [vp, dbl, vp, ctypes.POINTER(dbl)]
+    lib.festung_warmstart_features.argtypes = [vp, dbl, vp, vp, ctypes.POINTER(dbl)]
     lib.festung_set_guess.argtypes = [vp, vp, cint]
     lib.festung_mlp_create.argtypes = [cint, cint, ctypes.c_uint64, ctypes.POINTER(vp)]
     lib.festung_mlp_sizes.argtypes = [vp, ctypes.POINTER(cint), ctypes.POINTER(cint), ctypes.POINTER(cint)]
     lib.festung_mlp_set_stream.argtypes = [vp, vp]
     lib.festung_mlp_forward.argtypes = [vp, vp, vp, i64]
-    lib.festung_mlp_grad.argtypes = [vp, vp, vp, i64, ctypes.POINTER(dbl)]
+    lib.festung_mlp_grad.argtypes = [vp, vp, vp, vp, i64, ctypes.POINTER(dbl)]
     lib.festung_mlp_adam.argtypes = [vp, dbl]
     lib.festung_mlp_get.argtypes = [vp, vp, vp]
     lib.festung_mlp_set.argtypes = [vp, vp]
@@ -248,11 +248,13 @@ class Solver:
         self._check(self.lib.festung_autotune(self.h, ctypes.byref(t)))
         return t.value
 
-    def warmstart_features(self, dt, X):
+    def warmstart_features(self, dt, X, Wt=None):
         """Features of the learned warm start into the device tensor X (K x (3 + 4N), FP32,
-        internal order); returns the residual scale rs."""
+        internal order), optionally the loss weights into Wt (K x N); returns the residual scale rs."""
         sc = ctypes.c_double()
-        self._check(self.lib.festung_warmstart_features(self.h, dt, ctypes.c_void_p(X.data_ptr()), ctypes.byref(sc)))
+        wp = ctypes.c_void_p(Wt.data_ptr()) if Wt is not None else None
+        self._check(self.lib.festung_warmstart_features(self.h, dt, ctypes.c_void_p(X.data_ptr()), wp,
+                                                        ctypes.byref(sc)))
         return sc.value
 
     def set_guess(self, delta):
@@ -350,10 +352,11 @@ class MLP:
         self._check(self.lib.festung_mlp_forward(self.h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()),
                                                  X.shape[0]))
 
-    def grad(self, X, T):
+    def grad(self, X, T, Wt=None):
         loss = ctypes.c_double()
+        wp = ctypes.c_void_p(Wt.data_ptr()) if Wt is not None else None
         self._check(self.lib.festung_mlp_grad(self.h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(T.data_ptr()),
-                                              X.shape[0], ctypes.byref(loss)))
+                                              wp, X.shape[0], ctypes.byref(loss)))
         return loss.value
 
     def adam(self, lr):

@@ -37,8 +37,8 @@ def _unpack(p, n_in, n_out):
             _bf16(W3.astype(np.float32)).astype(np.float64), b3]
 
 
-def _reference(params, X, T):
-    """Loss (1 / 2R) sum (y - t)^2 and its gradient in FP64 (BF16-valued weights)."""
+def _reference(params, X, T, Wt=None):
+    """Loss (1 / 2R) sum (w (y - t))^2 and its gradient in FP64 (BF16-valued weights)."""
     W1, b1, W2, b2, W3, b3 = params
     X = X.astype(np.float64)
     a1 = X @ W1.T + b1
@@ -47,8 +47,9 @@ def _reference(params, X, T):
     h2 = np.maximum(a2, 0)
     Y = h2 @ W3.T + b3
     R = X.shape[0]
-    E = (Y - T) / R
-    loss = 0.5 * np.sum((Y - T) ** 2) / R
+    w = np.ones_like(Y) if Wt is None else Wt.astype(np.float64)
+    E = w * w * (Y - T) / R
+    loss = 0.5 * np.sum((w * (Y - T)) ** 2) / R
     gW3, gb3 = E.T @ h2, E.sum(0)
     d2 = (E @ W3) * (a2 > 0)
     gW2, gb2 = d2.T @ h1, d2.sum(0)
@@ -78,6 +79,13 @@ def test_mlp_forward_and_gradient_match_fp64_reference():
     assert np.max(np.abs(Y.cpu().numpy() - Yr)) <= 1e-5 * np.max(np.abs(Yr))
     assert abs(loss - lr_) <= 1e-5 * lr_
     assert np.linalg.norm(g - gr) <= 1e-4 * np.linalg.norm(gr), np.linalg.norm(g - gr) / np.linalg.norm(gr)
+    # with per-output weights
+    Wt = rng.uniform(0.5, 3.0, size=(rows, n_out)).astype(np.float32)
+    loss_w = net.grad(Xd, Td, torch.tensor(Wt, device="cuda"))
+    _, gw = net.get()
+    _, lw_ref, gw_ref = _reference(_unpack(p, n_in, n_out), X, T.astype(np.float64), Wt)
+    assert abs(loss_w - lw_ref) <= 1e-5 * lw_ref
+    assert np.linalg.norm(gw - gw_ref) <= 1e-4 * np.linalg.norm(gw_ref)
     net.close()
 
 
@@ -130,8 +138,9 @@ def test_features_match_oracle_residual():
     s.set_bc(edge_samples(s, lambda x, y: man.c(t, x, y)), edge_samples(s, lambda x, y: man.gN(t, x, y)))
     K, N = s.K, s.N
     X = torch.empty(K, 3 + 4 * N, dtype=torch.float32, device="cuda")
-    rs = s.warmstart_features(tau, X)
-    X = X.cpu().numpy()
+    Wt = torch.empty(K, N, dtype=torch.float32, device="cuda")
+    rs = s.warmstart_features(tau, X, Wt)
+    X, Wt = X.cpu().numpy(), Wt.cpu().numpy()
     L = LDG(cV, V0T, bdr, p)
     D = L.project(smooth_d)
     C0 = L.project(lambda x, y: man.c(0.0, x, y))
@@ -146,6 +155,9 @@ def test_features_match_oracle_residual():
     assert np.max(np.abs(own - (q[order] / rs_ref))) <= 1e-5 * np.max(np.abs(q / rs_ref))
     dmean = np.mean(D[:, 0])
     assert np.max(np.abs(X[:, 0:3] - D[order, 0:3] / dmean)) <= 1e-5
+    # loss weights: sqrt of the diagonal of S over 2|T_k| (FP32 blocks)
+    dS = L.operator(D, tau).diagonal().reshape(K, N) / (2 * L.g.areaT)[:, None]
+    assert np.max(np.abs(Wt - np.sqrt(dS[order])) / np.sqrt(dS[order])) <= 1e-4
     s.close()
 
 
