@@ -648,7 +648,7 @@ def main():
     ap.add_argument("--train-seeds", type=int, default=24, help="learned: training trajectories")
     ap.add_argument("--eval-seeds", type=int, default=8, help="learned: held-out trajectories")
     ap.add_argument("--train-iters", type=int, default=600, help="learned: Adam steps")
-    ap.add_argument("--weighted-loss", type=int, default=1,
+    ap.add_argument("--weighted-loss", type=int, default=0,
                     help="learned: weight the loss by sqrt(diag S / 2|T|) (1) or not (0)")
     ap.add_argument("--workload", default=None, choices=["batched512", "learned"],
                     help="run another workload than the default step benchmark; prints one line")
