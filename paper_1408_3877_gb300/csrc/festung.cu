@@ -1,6 +1,7 @@
-// C ABI of the GB300 LDG solver: context, data upload, operator apply and the
+// C ABI of the GB300 LDG solver: context, data upload, operator apply, the
 // implicit-Euler step (BiCGStab / CG with device-resident scalars, optionally FP32
-// inner iterations under FP64 residual refinement).
+// inner iterations refined on residuals evaluated in double-float arithmetic), the
+// stationary problem, flux recovery, batches of problems and the learned warm start.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -1409,7 +1410,7 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
     double r2 = 0, b2 = 0;
     bool conv = false;
     double relres = 0.0, relres0 = -1.0;
-    // FP64 residual r = b - S x and its norms (rn, bn)
+    // residual r = b - S x (FP64 vectors) and its norms (rn, bn)
     // (FESTUNG_MIXED: S x in double-float arithmetic, about 48 significant bits)
     const bool df_residual = o.prec == FESTUNG_MIXED;
     auto residual64 = [&](double *rn, double *bn) -> int {
@@ -1431,9 +1432,9 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
     };
     bool fp64 = (o.prec == FESTUNG_FP64);
     if (!fp64) {
-        // mixed precision: FP64 residual, FP32 inner solve of S d = r / ||r||, C += ||r|| d.
-        // An inner solve that does not lower the FP64 residual is undone and the step
-        // finishes in FP64.
+        // mixed precision: residual with S x in double-float arithmetic, FP32 inner solve of
+        // S d = r / ||r||, C += ||r|| d.  An inner solve that does not lower the residual is
+        // undone; after two such sweeps the step finishes in FP64.
         Vecs<float> &F = w.f;
         double prev_rn = -1.0, last_scale = 0.0;
         int failures = 0;
@@ -1448,7 +1449,7 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
                 break;
             }
             if (applied && !(rn < prev_rn)) {
-                // the last sweep did not lower the FP64 residual: undo it
+                // the last sweep did not lower the residual: undo it
                 k_add_f32<<<small_grid(KN, c), 256, 0, st>>>(KN, V.x, F.x, -last_scale); ++c->launches;
                 applied = false;
                 if (++failures >= 2) {

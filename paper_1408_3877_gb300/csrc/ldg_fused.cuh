@@ -498,6 +498,17 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
     const int i = threadIdx.x;
     const int hstride = blockDim.x - TE;
     T z1[N], z2[N], d[N];
+    if constexpr (EPI != FUSED_EPI_NONE) {
+        // the epilogue's vectors: start their loads into L1 now, so that their latency
+        // hides behind phases A and B
+        if (i < cnt) {
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(e1 + j * Ki + start + i));
+                if constexpr (EPI == FUSED_EPI_OMEGA) asm volatile("prefetch.global.L1 [%0];" ::"l"(e2 + j * Ki + start + i));
+            }
+        }
+    }
     // A1: traces of x and d_h of every slot (tile triangles keep d_h in registers)
     if (i < TE) {
         if (i < cnt) slot_a1<T, N, R2, R1>(X, Dc, Ki, start + i, tr, NS, i, d);
