@@ -323,6 +323,13 @@ def run_festung(args):
             "frac": apply_main["fp32"]["tflops"] / fp32_peak, "traffic": measured_traffic(),
             "traffic_note": "ncu dram bytes per launch, back-to-back launches (the 27 MB working set is L2-resident)",
             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock (derived; not in the measured peaks)"}
+    try:  # the multiply-add ceiling measured on this device in the same run (festung_fma_peak)
+        fma32, fma64 = F.fma_peak(F.FP32), F.fma_peak(F.FP64)
+        roof["fma_peak_measured"] = {"fp32_tflops": fma32, "fp64_tflops": fma64,
+                                     "frac_of_fp32": apply_main["fp32"]["tflops"] / fma32,
+                                     "frac_of_fp64_for_the_fp64_apply": apply_main["fp64"]["tflops"] / fma64}
+    except F.FestungError:
+        pass
     line = {
         "metric": METRIC, "value": sec_per_step, "unit": "s/step", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sec_per_step * 1e3 * world, "higher_is_better": False,

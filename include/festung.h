@@ -257,6 +257,11 @@ int festung_mlp_set(festung_mlp *net, const float *params);
 const char *festung_mlp_last_error(void);
 void festung_mlp_destroy(festung_mlp *net);
 
+/* Multiply-add throughput of the current device in TFLOP/s (FP32 or FP64 by prec): 8
+ * independent chains per thread, 8 blocks of 256 threads per SM, best of 5 launches.
+ * The ALU ceiling the operator kernels are compared with; the paper has no counterpart. */
+int festung_fma_peak(int prec, double *tflops);
+
 /* ---- Batches of independent problems -------------------------------------------
  * Many problems (each its own context, set up, with its own mesh, order, coefficient,
  * source and boundary data) advance by one implicit-Euler step together.  Problems of

@@ -24,7 +24,7 @@ EXPORTS = [
     "festung_get_state", "festung_apply", "festung_apply_noalloc", "festung_step", "festung_solve_stationary",
     "festung_l2_error", "festung_get_flux",
     "festung_element_order", "festung_launch_count", "festung_set_stream", "festung_last_error", "festung_destroy",
-    "festung_autotune", "festung_warmstart_features", "festung_set_guess",
+    "festung_autotune", "festung_fma_peak", "festung_warmstart_features", "festung_set_guess",
     "festung_mlp_create", "festung_mlp_sizes", "festung_mlp_set_stream", "festung_mlp_forward", "festung_mlp_grad",
     "festung_mlp_adam", "festung_mlp_get", "festung_mlp_set", "festung_mlp_last_error", "festung_mlp_destroy",
     "festung_batch_create", "festung_batch_set_stream", "festung_batch_step", "festung_batch_launch_count",
@@ -86,6 +86,7 @@ def load(path=None):
     lib.festung_destroy.argtypes = [vp]
     lib.festung_destroy.restype = None
     lib.festung_autotune.argtypes = [vp, ctypes.POINTER(cint)]
+    lib.festung_fma_peak.argtypes = [cint, ctypes.POINTER(dbl)]
     lib.festung_warmstart_features.argtypes = [vp, dbl, vp, vp, ctypes.POINTER(dbl)]
     lib.festung_set_guess.argtypes = [vp, vp, cint]
     lib.festung_mlp_create.argtypes = [cint, cint, ctypes.c_uint64, ctypes.POINTER(vp)]
@@ -382,3 +383,13 @@ class MLP:
             self.close()
         except Exception:
             pass
+
+
+def fma_peak(prec=FP32):
+    """Measured multiply-add throughput of the current device (TFLOP/s)."""
+    lib = load()
+    t = ctypes.c_double()
+    rc = lib.festung_fma_peak(prec, ctypes.byref(t))
+    if rc:
+        raise FestungError(rc, "festung_fma_peak failed")
+    return t.value

@@ -214,3 +214,27 @@ def test_errors_leave_state_unchanged():
         s.step(-1.0)
     assert e.value.code == F.EINVAL
     s.close()
+
+
+@pytest.mark.parametrize("p", [0, 2, 4])
+def test_single_triangle_step(p):
+    """The smallest mesh: one triangle, Dirichlet on two edges and Neumann on one (no
+    interior edge, one tile of one triangle, no halo)."""
+    from oracle.solve import LDG
+    from paper_1408_3877_gb300 import festung as F
+    cV = np.array([[0.0, 0.0], [1.0, 0.0], [0.2, 0.9]])
+    V0T = np.array([[0, 1, 2]])
+    bdr = np.array([[1, 2, 1]])
+    man = W.Manufactured(W.d_config2)
+    tau, t = 0.01, 0.01
+    L = LDG(cV, V0T, bdr, p)
+    s = gpu_solver(cV, V0T, bdr, p)
+    s.set_state(samples(s, lambda x, y: man.c(0.0, x, y)), is_samples=True)
+    _load_step_data(s, man, t)
+    for prec, tol, bound in ((F.FP64, 1e-13, 1e-11), (F.MIXED, 1e-12, 1e-9)):
+        s.set_state(samples(s, lambda x, y: man.c(0.0, x, y)), is_samples=True)
+        info = s.step(tau, tol=tol, prec=prec)
+        C = s.get_state()
+        Co = _oracle_step(L, man, L.project(lambda x, y: man.c(0.0, x, y)), t, tau)
+        assert np.linalg.norm(C - Co) <= bound * np.linalg.norm(Co), (prec, info)
+    s.close()
