@@ -155,6 +155,18 @@ def cpu_baseline(cfg, full_dofs, budget_s=15.0):
                       % (n_s, n_s, dofs, sec, full_dofs)}
 
 
+def job_seconds_per_step(t_local, steps, world, dist=None, device="cpu"):
+    """Whole-job seconds per step of `world` replicas that each ran `steps` steps in t_local
+    seconds: the slowest rank's time (a MAX reduction) over all steps of all ranks."""
+    import torch
+    t = float(t_local)
+    if dist is not None and world > 1:
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return t / (steps * world)
+
+
 def step_inputs(s, cfg, man, t, to_dev):
     xy, exy = s.quad_points()
     X, Y = xy[..., 0], xy[..., 1]
@@ -220,12 +232,7 @@ def run_festung(args):
     clk = clocks.stop()
     launches = s.launch_count() - l0
     per_step = [a.elapsed_time(b) / 1e3 for a, b in ev]
-    t_total = float(sum(per_step))
-    if dist is not None:
-        tt = torch.tensor([t_total], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
-    sec_per_step = t_total / (args.steps * world)
+    sec_per_step = job_seconds_per_step(float(sum(per_step)), args.steps, world, dist, "cuda")
 
     # ---- end to end through host buffers (pinned), state read back every step ----
     pin = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64).pin_memory()
@@ -250,12 +257,7 @@ def run_festung(args):
         s.step(dt, tol=tol, prec=F.MIXED, inner_tol=1e-2)
         s._check(s.lib.festung_get_state(s.h, out.data_ptr(), F.HOST))
     barrier()
-    e2e = (time.perf_counter() - t0) / args.steps
-    if dist is not None:
-        tt = torch.tensor([e2e], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = float(tt.item())
-    e2e /= world
+    e2e = job_seconds_per_step(time.perf_counter() - t0, args.steps, world, dist, "cuda")
 
     # ---- operator apply alone: this workload (L2 flushed between launches) ----
     pk, pk_kind = peaks()

@@ -18,7 +18,7 @@ void launch_apply_df(const festung_ctx *c, const dfloat *x, dfloat *y, double ta
         const size_t smem = fused_smem<dfloat, R1>(c->nslot);
         static const bool smem_ok = allow_max_smem(k_apply_fused<dfloat, N, R2, R1>);
         (void)smem_ok;
-        k_apply_fused<dfloat, N, R2, R1><<<tiles, FUSED_THREADS, smem, st>>>(
+        k_apply_fused<dfloat, N, R2, R1><<<tiles, c->fthreads, smem, st>>>(
             x, y, c->xD, c->xB, c->dNbr, c->dSlot, c->dHaloPtr, c->dHalo, c->dHaloSlot, c->K, c->TE, c->nslot,
             dfloat(tau), dfloat(c->eta), dfloat(c->mass), c->xTab, nullptr);
     });

@@ -19,7 +19,7 @@ void launch_apply<float>(const festung_ctx *c, const float *x, float *y, float *
         const size_t smem = fused_smem<float, R1>(c->nslot);
         static const bool smem_ok = allow_max_smem(k_apply_fused<float, N, R2, R1>);
         (void)smem_ok;
-        k_apply_fused<float, N, R2, R1><<<tiles, FUSED_THREADS, smem, st>>>(x, y, c->fD, c->fB, c->dNbr, c->dSlot, c->dHaloPtr,
+        k_apply_fused<float, N, R2, R1><<<tiles, c->fthreads, smem, st>>>(x, y, c->fD, c->fB, c->dNbr, c->dSlot, c->dHaloPtr,
                                                                 c->dHalo, c->dHaloSlot, c->K, c->TE, c->nslot, tau, (float)c->eta, (float)c->mass,
                                                                 c->fTab, skip);
     });
@@ -31,7 +31,7 @@ int fused_resident_blocks(const festung_ctx *c, int nslot) {
         constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
         static const bool smem_ok = allow_max_smem(k_apply_fused<float, N, R2, R1>);
         (void)smem_ok;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_apply_fused<float, N, R2, R1>, FUSED_THREADS,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_apply_fused<float, N, R2, R1>, c->fthreads,
                                                           fused_smem<float, R1>(nslot)) != cudaSuccess)
             nb = 0;
     });

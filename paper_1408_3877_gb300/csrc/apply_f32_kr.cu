@@ -21,7 +21,7 @@ void launch_apply_bicg<float>(const festung_ctx *c, const float *x, float *y, fl
         (void)smem_o;
         auto kern = epi == FUSED_EPI_ALPHA ? k_apply_fused<float, N, R2, R1, FUSED_EPI_ALPHA>
                                            : k_apply_fused<float, N, R2, R1, FUSED_EPI_OMEGA>;
-        kern<<<tiles, FUSED_THREADS, smem, st>>>(x, y, c->fD, c->fB, c->dNbr, c->dSlot, c->dHaloPtr, c->dHalo,
+        kern<<<tiles, c->fthreads, smem, st>>>(x, y, c->fD, c->fB, c->dNbr, c->dSlot, c->dHaloPtr, c->dHalo,
                                                  c->dHaloSlot, c->K, c->TE, c->nslot, tau, (float)c->eta,
                                                  (float)c->mass, c->fTab, skip, e1, e2, part, sc, counter, bv);
     });

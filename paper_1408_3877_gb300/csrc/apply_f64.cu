@@ -17,7 +17,7 @@ void launch_apply<double>(const festung_ctx *c, const double *x, double *y, doub
         const size_t smem = fused_smem<double, R1>(c->nslot);
         static const bool smem_ok = allow_max_smem(k_apply_fused<double, N, R2, R1>);
         (void)smem_ok;
-        k_apply_fused<double, N, R2, R1><<<tiles, FUSED_THREADS, smem, st>>>(x, y, c->dD, c->dB, c->dNbr, c->dSlot, c->dHaloPtr,
+        k_apply_fused<double, N, R2, R1><<<tiles, c->fthreads, smem, st>>>(x, y, c->dD, c->dB, c->dNbr, c->dSlot, c->dHaloPtr,
                                                                 c->dHalo, c->dHaloSlot, c->K, c->TE, c->nslot, tau, (double)c->eta, (double)c->mass,
                                                                 c->dTab, skip);
     });

@@ -878,6 +878,10 @@ cudaError_t retile(festung_ctx *c, int te) {
     c->TE = te;
     c->max_halo = mo.max_halo;
     c->nslot = te + mo.max_halo;
+    // halo threads: whole warps for the largest halo, at least one warp, at most the
+    // kernels' 320 threads in all (more halo slots are taken in turns)
+    const int hw = std::min(std::max(32, ((mo.max_halo + 31) / 32) * 32), 320 - te);
+    c->fthreads = te + std::max(32, hw);
     return cudaSuccess;
 }
 
@@ -1102,6 +1106,9 @@ int festung_setup(festung_ctx *c, int p, int quad_order, double eta) {
     c->symmetric = true;
     c->source_zero = true;
     c->bc_zero = true;
+    // large meshes: the tile size by measurement (a few applies; smaller meshes keep the
+    // occupancy model's choice, which is deterministic)
+    if (c->K >= 65536 && (rc = autotune_tiles(c, nullptr))) return rc;
     return FESTUNG_OK;
 }
 

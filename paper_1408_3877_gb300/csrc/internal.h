@@ -106,6 +106,7 @@ struct festung_ctx {
     std::vector<int32_t> perm;  // internal index -> caller's triangle index
     int32_t *dPerm = nullptr;   // device copy of perm
     int TE = 0, max_halo = 0, nslot = 0;
+    int fthreads = 320;  // threads of a fused-apply block: TE plus whole warps for the halo
     std::vector<int32_t> hNbrInt;  // 3 x K neighbour codes in internal order (for re-tiling)
     int32_t *dHaloPtr = nullptr, *dHalo = nullptr;
     int16_t *dSlot = nullptr;   // 3 x K

@@ -364,7 +364,9 @@ __device__ __forceinline__ void tile_edge(int code, int sl, const T *tr, int NS,
     }
 }
 
-constexpr int FUSED_THREADS = 320;  // a tile of up to 256 triangles plus at least 64 halo threads
+// The most threads of a fused-apply block: a tile of up to 256 triangles and whole warps
+// of halo threads (a block is launched with its tile's size plus the warps its halo needs).
+constexpr int FUSED_THREADS = 320;
 constexpr int FUSED_MAX_TE = 256;
 
 // Minimum resident blocks per SM asked of the register allocator: two for the FP32
