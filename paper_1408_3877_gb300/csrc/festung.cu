@@ -1334,12 +1334,23 @@ int prepare_solve(festung_ctx *c, double dt, bool stationary, bool mixed) {
     double *W1 = w.scratch64, *W2 = w.scratch64 + KN;
     launch_rhs(c, W1, W2, V.b, dt, st);
     FCK(cudaGetLastError());
-    // block-Jacobi preconditioner: inverse diagonal blocks of S for this D and dt
+    // block-Jacobi preconditioner: inverse diagonal blocks of S for this D and dt, built on
+    // a second stream while this one forms the guess and the first residual
+    // (finish_precond joins it)
     if (!w.P) FCK(cudaMalloc(&w.P, (size_t)c->N * c->N * c->K * sizeof(float)));
     if (!w.Pb) FCK(cudaMalloc(&w.Pb, (size_t)((c->N * c->N + 7) / 8) * c->K * 16));
-    FCK(cudaMemsetAsync(w.d_flags, 0, sizeof(int), st));
-    launch_blockjacobi(c, w.P, w.Pb, dt, w.d_flags, st);
+    if (!c->side) {
+        FCK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+        FCK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+        FCK(cudaEventCreateWithFlags(&c->ev_P, cudaEventDisableTiming));
+    }
+    FCK(cudaEventRecord(c->ev_in, st));
+    FCK(cudaStreamWaitEvent(c->side, c->ev_in, 0));
+    FCK(cudaMemsetAsync(w.d_flags, 0, sizeof(int), c->side));
+    launch_blockjacobi(c, w.P, w.Pb, dt, w.d_flags, c->side);
     FCK(cudaGetLastError());
+    FCK(cudaEventRecord(c->ev_P, c->side));
+    c->P_pending = true;
     // initial guess: C^n plus a correction given with festung_set_guess, else
     // extrapolation in time from the previous states when they exist, else C^n (the
     // result does not depend on it beyond the tolerance)
@@ -1361,9 +1372,20 @@ int prepare_solve(festung_ctx *c, double dt, bool stationary, bool mixed) {
     } else {
         FCK(cudaMemcpyAsync(V.x, c->dC, KN * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
+    return FESTUNG_OK;
+}
+
+// Join the preconditioner build of prepare_solve: the main stream waits for it, and the
+// blocks are used unless one was singular.
+int finish_precond(festung_ctx *c) {
+    if (!c->P_pending) return FESTUNG_OK;
+    Workspace &w = *c->ws;
+    cudaStream_t st = c->stream;
+    FCK(cudaStreamWaitEvent(st, c->ev_P, 0));
     FCK(cudaMemcpyAsync(w.h_flags, w.d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     FCK(cudaStreamSynchronize(st));
     w.use_P = (w.h_flags[0] == 0);
+    c->P_pending = false;
     return FESTUNG_OK;
 }
 
@@ -1449,6 +1471,7 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
         for (outer = 1; outer <= o.max_outer; ++outer) {
             double rn, bn;
             if ((rc = residual64(&rn, &bn))) return rc;
+            if ((rc = finish_precond(c))) return rc;
             relres = bn > 0 ? rn / bn : rn;
             if (relres0 < 0.0) relres0 = relres;
             if (relres <= o.tol || rn == 0.0) {
@@ -1499,6 +1522,7 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
     }
     if (fp64) {
         // FP64 Krylov; verified with the true residual and restarted if the recursion drifted
+        if ((rc = finish_precond(c))) return rc;
         for (int sweep = 1; sweep <= o.max_outer; ++sweep, ++outer) {
             int it = 0;
             double rr0 = -1.0;
@@ -1697,6 +1721,12 @@ const char *festung_last_error(const festung_ctx *c) {
 void festung_destroy(festung_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+        cudaEventDestroy(c->ev_in);
+        cudaEventDestroy(c->ev_P);
+    }
     free_ctx_device(c);
     void *mesh_ptrs[] = {c->dB, c->fB, c->dNbr, c->dPerm, c->dSlot, c->dHaloPtr, c->dHalo, c->dHaloSlot, c->dLift};
     for (void *q : mesh_ptrs)
@@ -2201,6 +2231,7 @@ int solve_group(festung_batch *b, BatchGroup &g, double dt, const festung_step_o
     bool reweight = false;
     for (outer = 1; outer <= o.max_outer; ++outer) {
         if ((rc = residuals())) return rc;
+        if ((rc = finish_precond(c))) return rc;
         // members whose last sweep did not lower their residual: undo it; after two such
         // sweeps a member is left to the single-problem solve
         std::vector<double> undo(nm, 0.0);

@@ -146,6 +146,9 @@ struct festung_ctx {
     // workspace
     festung::Workspace *ws = nullptr;
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;         // the preconditioner build overlaps the right-hand side and residual
+    cudaEvent_t ev_in = nullptr, ev_P = nullptr;
+    bool P_pending = false;              // the block-Jacobi build runs on `side` until ev_P
     int num_sms = 0;
     mutable int64_t launches = 0;  // kernels launched on behalf of this context (graph nodes counted)
     std::string err;
