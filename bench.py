@@ -259,6 +259,21 @@ def run_festung(args):
     barrier()
     e2e = job_seconds_per_step(time.perf_counter() - t0, args.steps, world, dist, "cuda")
 
+    # ---- the same step with the plain FP64 solve (the form the mixed one is measured against) ----
+    fp64_steps = []
+    for j in range(2):
+        d, f, cD, gN = inputs[nsteps - 1]
+        s.set_coeff(d)
+        s.set_source(f)
+        s.set_bc(cD, gN)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        a.record(stream)
+        info64 = s.step(dt, tol=tol, prec=F.FP64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        fp64_steps.append((a.elapsed_time(b) / 1e3, info64["iterations"]))
+
     # ---- operator apply alone: this workload (L2 flushed between launches) ----
     pk, pk_kind = peaks()
 
@@ -344,6 +359,8 @@ def run_festung(args):
         "outer_per_step": float(np.mean([i["outer"] for i in infos])),
         "rel_residual_max": float(max(i["rel_residual"] for i in infos)),
         "initial_rel_residual_median": float(np.median([i["initial_rel_residual"] for i in infos])),
+        "plain_fp64_step": {"value": fp64_steps[-1][0], "unit": "s/step", "iterations": fp64_steps[-1][1],
+                            "note": "the same workload stepped with FESTUNG_FP64 (FP64 Krylov and residual)"},
         "apply": apply_main, "apply_large": apply_big,
         "roofline": roof,
         "e2e": {"value": e2e, "unit": "s/step", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
