@@ -207,10 +207,10 @@ int festung_l2_error(const festung_ctx *ctx, const double *c_samples, double *er
 int festung_get_flux(const festung_ctx *ctx, double *Z, int loc);
 
 /* Tile size by measurement: times the FP32 operator apply for tiles of 96..256
- * triangles (multiples of 32) and keeps the fastest.  festung_setup calls it itself for
- * meshes of 65,536 triangles or more, and picks smaller meshes' tiles from an occupancy
- * model.  Results do not depend on the tiling beyond rounding.  tile may be NULL.
- * Synchronises the context's stream. */
+ * triangles (multiples of 32) and keeps the fastest (festung_setup picks the tiles from
+ * an occupancy model, deterministically; batches run this for every group).  Results do
+ * not depend on the tiling beyond rounding.  tile may be NULL.  Synchronises the
+ * context's stream. */
 int festung_autotune(festung_ctx *ctx, int *tile);
 
 /* ---- Learned warm start -----------------------------------------------------------

@@ -1106,9 +1106,6 @@ int festung_setup(festung_ctx *c, int p, int quad_order, double eta) {
     c->symmetric = true;
     c->source_zero = true;
     c->bc_zero = true;
-    // large meshes: the tile size by measurement (a few applies; smaller meshes keep the
-    // occupancy model's choice, which is deterministic)
-    if (c->K >= 65536 && (rc = autotune_tiles(c, nullptr))) return rc;
     return FESTUNG_OK;
 }
 
