@@ -262,7 +262,8 @@ def run_festung(args):
     # ---- the same step with the plain FP64 solve (the form the mixed one is measured against) ----
     fp64_steps = []
     for j in range(2):
-        d, f, cD, gN = inputs[nsteps - 1]
+        # the next time levels after the end-to-end steps, so that the state and the data match
+        d, f, cD, gN = step_inputs(s, cfg, man, (nsteps + args.steps + j + 1) * dt, dev)
         s.set_coeff(d)
         s.set_source(f)
         s.set_bc(cD, gN)
