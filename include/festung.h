@@ -278,10 +278,14 @@ int festung_fma_peak(int prec, double *tflops);
  * batch; they must not be set up again while in it.  Their data are set with the usual
  * calls (festung_set_coeff, _source, _bc, _state) before each festung_batch_step, which
  * reads them, steps all problems (FESTUNG_MIXED only; opts as festung_step) and writes
- * every C back (festung_get_state reads it).  infos: nprob entries or NULL.  Groups are
- * stepped one after the other; on an error the problems of the failing group and of the
- * groups after it keep their C.  The extrapolated initial guess of a group restarts when
- * one of its problems' state was set from outside since the last batch step. */
+ * every C back (festung_get_state reads it).  infos: nprob entries or NULL.  The groups
+ * are stepped concurrently, each on a stream of its own and a host thread of its own,
+ * after the work queued on the batch's stream (festung_batch_set_stream; default the
+ * legacy default stream), which then waits for all of them; the call returns once every
+ * group has finished.  On an error the problems of a failing group keep their C, the
+ * other groups complete their step, and the first failing group's code is returned.  The
+ * extrapolated initial guess of a group restarts when one of its problems' state was set
+ * from outside since the last batch step. */
 typedef struct festung_batch festung_batch;
 int festung_batch_create(festung_ctx *const *problems, int nprob, festung_batch **out);
 int festung_batch_set_stream(festung_batch *batch, void *cuda_stream);

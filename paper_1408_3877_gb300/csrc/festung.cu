@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -1933,9 +1934,13 @@ struct BatchGroup {
     cudaGraphExec_t exec = nullptr;       // CHUNK iterations
     double g_tau = 0.0;
     int g_useP = -1;
+    cudaStream_t stream = nullptr;        // the group's own stream (groups run concurrently)
+    cudaEvent_t done_ev = nullptr;
+    std::string err;                      // message of the group's last failure
 };
 
 void free_group(BatchGroup &g) {
+    if (g.stream) cudaStreamSynchronize(g.stream);
     if (g.exec) cudaGraphExecDestroy(g.exec);
     cudaFree(g.sc);
     if (g.hsc) cudaFreeHost(g.hsc);
@@ -1945,6 +1950,8 @@ void free_group(BatchGroup &g) {
     cudaFree(g.dtol);
     if (g.htol) cudaFreeHost(g.htol);
     if (g.u) festung_destroy(g.u);
+    if (g.done_ev) cudaEventDestroy(g.done_ev);
+    if (g.stream) cudaStreamDestroy(g.stream);
     cudaFree(g.eprob);
     cudaFree(g.dmem);
     cudaFree(g.dacc);
@@ -1960,6 +1967,8 @@ struct festung_batch {
     std::vector<festung_ctx *> probs;
     std::vector<BatchGroup> groups;
     cudaStream_t stream = nullptr;
+    cudaEvent_t start_ev = nullptr;
+    int device = 0;
     std::string err;
 };
 
@@ -2043,6 +2052,12 @@ int build_group(festung_batch *b, BatchGroup &g) {
         return e == cudaErrorMemoryAllocation ? FESTUNG_ENOMEM : FESTUNG_ECUDA;
     }
     g.gen.assign(nm, ~0ull);
+    if ((e = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&g.done_ev, cudaEventDisableTiming)) != cudaSuccess) {
+        b->err = std::string("CUDA: ") + cudaGetErrorString(e);
+        return FESTUNG_ECUDA;
+    }
+    festung_set_stream(u, g.stream);
     int te = 0;
     if ((rc = autotune_tiles(u, &te))) {
         b->err = u->err;
@@ -2307,7 +2322,7 @@ int solve_group(festung_batch *b, BatchGroup &g, double dt, const festung_step_o
         festung_step_info in{};
         rc = solve_system(p, dt, 1.0, &o, &in);
         if (rc) {
-            b->err = "problem " + std::to_string(g.members[m]) + ": " + p->err;
+            g.err = "problem " + std::to_string(g.members[m]) + ": " + p->err;
             return rc;
         }
         if (infos) {
@@ -2365,6 +2380,12 @@ int festung_batch_create(festung_ctx *const *problems, int nprob, festung_batch 
     festung_batch *b = new (std::nothrow) festung_batch();
     if (!b) return FESTUNG_ENOMEM;
     b->probs.assign(problems, problems + nprob);
+    if (cudaGetDevice(&b->device) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->start_ev, cudaEventDisableTiming) != cudaSuccess) {
+        g_create_err = "CUDA: cannot create the batch's event";
+        delete b;
+        return FESTUNG_ECUDA;
+    }
     for (int q = 0; q < nprob; ++q) {
         const festung_ctx *c = problems[q];
         BatchGroup *hit = nullptr;
@@ -2392,8 +2413,7 @@ int festung_batch_create(festung_ctx *const *problems, int nprob, festung_batch 
 
 int festung_batch_set_stream(festung_batch *b, void *stream) {
     if (!b) return FESTUNG_EINVAL;
-    b->stream = (cudaStream_t)stream;
-    for (auto &g : b->groups) festung_set_stream(g.u, stream);
+    b->stream = (cudaStream_t)stream;  // the groups run on their own streams, ordered after this one
     return FESTUNG_OK;
 }
 
@@ -2404,13 +2424,36 @@ int festung_batch_step(festung_batch *b, double dt, const festung_step_opts *opt
         b->err = "bad batch step arguments (FESTUNG_MIXED only)";
         return FESTUNG_EINVAL;
     }
-    for (auto &g : b->groups) {
-        int rc = solve_group(b, g, dt, o, infos);
-        if (rc) {
-            if (b->err.empty() || rc == FESTUNG_ECUDA) b->err = g.u->err;
-            return rc;
-        }
+    // the groups run concurrently, each on its own stream and host thread, after the work
+    // already queued on the batch's stream; the batch's stream then waits for all of them
+    const size_t ng = b->groups.size();
+    std::vector<int> rcs(ng, FESTUNG_OK);
+    if (cudaEventRecord(b->start_ev, b->stream) != cudaSuccess) {
+        b->err = "CUDA: cannot record on the batch's stream";
+        return FESTUNG_ECUDA;
     }
+    for (auto &g : b->groups) {
+        g.err.clear();
+        cudaStreamWaitEvent(g.stream, b->start_ev, 0);
+    }
+    auto run = [&](size_t i) {
+        cudaSetDevice(b->device);
+        rcs[i] = solve_group(b, b->groups[i], dt, o, infos);
+    };
+    std::vector<std::thread> threads;
+    for (size_t i = 1; i < ng; ++i) threads.emplace_back(run, i);
+    run(0);
+    for (auto &t : threads) t.join();
+    for (auto &g : b->groups) {
+        cudaEventRecord(g.done_ev, g.stream);
+        cudaStreamWaitEvent(b->stream, g.done_ev, 0);
+    }
+    for (size_t i = 0; i < ng; ++i)
+        if (rcs[i]) {
+            BatchGroup &g = b->groups[i];
+            b->err = !g.err.empty() && rcs[i] != FESTUNG_ECUDA ? g.err : g.u->err;
+            return rcs[i];
+        }
     return FESTUNG_OK;
 }
 
@@ -2426,6 +2469,7 @@ const char *festung_batch_last_error(const festung_batch *b) { return b ? b->err
 void festung_batch_destroy(festung_batch *b) {
     if (!b) return;
     for (auto &g : b->groups) free_group(g);
+    if (b->start_ev) cudaEventDestroy(b->start_ev);
     delete b;
 }
 
