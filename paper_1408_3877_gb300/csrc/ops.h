@@ -63,9 +63,10 @@ cudaError_t upload_tables_f32_kr(const festung_ctx *c);
 cudaError_t upload_tables_df(const festung_ctx *c);
 
 // Block-Jacobi preconditioner: Pinv <- inverse of the N x N diagonal blocks of S (E1),
-// built in FP32 (scratch P) from the FP32 copies of geometry, tables and D, inverted in
-// FP64 and stored in BF16; layout [(i N + j) K + k].  flags (device int) gets bit 0 set
-// if a block is singular.
+// built in FP32 (scratch P, layout [(i N + j) K + k]) from the FP32 copies of geometry,
+// tables and D, inverted in FP32 (Gauss-Jordan, partial pivoting, one warp per block) and
+// stored in BF16 (16-byte chunks [q][K]).  flags (device int) gets bit 0 set if a block
+// is singular.
 void launch_blockjacobi(const festung_ctx *c, float *P, __nv_bfloat16 *Pinv, double tau, int *flags,
                         cudaStream_t st);
 
