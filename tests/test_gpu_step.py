@@ -1,6 +1,6 @@
 """Parity of the CUDA implicit-Euler step with the oracle's sparse direct solve of the
 3KN system (Sec. 2.5).  FP64 path at Krylov tolerance 1e-13: relative L2 difference
-<= 1e-11 per step.  Mixed path (FP32 inner, FP64 refinement) at tolerance 1e-12:
+<= 1e-11 per step.  Mixed path (FP32 inner solve, refinement on double-float residuals) at tolerance 1e-12:
 <= 1e-9.  The solution error of an iterative solve is at most cond(S) * tol; the
 meshes here have cond(S) <= ~1e2 after the mass scaling."""
 import numpy as np
