@@ -493,6 +493,29 @@ def run_batched(args):
             batch_s.append(sec)
             infos.append(info)
     launches = batch.launch_count()
+    # the same batch with every problem stepped on its own, several workers at a time
+    concurrent = {}
+
+    def concurrent_step():
+        try:
+            return batch.step(dt, tol=tol, inner_tol=1e-2)
+        except F.FestungError as e:
+            if e.code != F.ENOCONV:
+                raise
+            return e.infos  # a problem that did not converge keeps C^n, as one by one
+
+    for workers in (4, 8, 16):
+        batch.set_mode(F.BATCH_CONCURRENT, workers)
+        secs, its_c, failed = [], [], 0
+        for k in range(1 + args.steps):
+            step += 1
+            load(step * dt)
+            sec, info = timed(concurrent_step)
+            if k >= 1:
+                secs.append(sec)
+                its_c += [i["iterations"] for i in info]
+                failed += sum(1 for i in info if not i["rel_residual"] <= tol)
+        concurrent[workers] = (float(np.mean(secs)), float(np.mean(its_c)), failed)
     batch.close()
     # the same problems one after the other: single-problem mixed solve, then plain FP64
     single = {}
@@ -524,6 +547,9 @@ def run_batched(args):
             "rel_residual_max": float(max(i["rel_residual"] for step_info in infos for i in step_info)),
             "input_loading_s_per_step": float(np.mean(load_s)), "host_preparation_s": prep,
             "gpu_launches_per_step": launches / (args.warmup + args.steps),
+            "concurrent_mode": {str(w): {"value": v, "unit": "s/step", "iterations_per_step_mean": it,
+                                         "speedup_over_union": value / v, "failed_solves": f}
+                                for w, (v, it, f) in concurrent.items()},
             "same_problems_one_by_one": {k: {"value": v, "unit": "s/step", "speedup_of_batch": v / value,
                                              "failed_solves": f} for k, (v, f) in single.items()}}
 

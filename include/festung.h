@@ -73,6 +73,9 @@ extern "C" {
 #define FESTUNG_SOLVER_CG        1
 #define FESTUNG_SOLVER_BICGSTAB  2
 
+#define FESTUNG_BATCH_UNION       0   /* one joined mesh per group (the default)            */
+#define FESTUNG_BATCH_CONCURRENT  1   /* every problem its own step, several at a time      */
+
 typedef struct festung_ctx festung_ctx;
 
 typedef struct festung_step_opts {
@@ -285,10 +288,22 @@ int festung_fma_peak(int prec, double *tflops);
  * group has finished.  On an error the problems of a failing group keep their C, the
  * other groups complete their step, and the first failing group's code is returned.  The
  * extrapolated initial guess of a group restarts when one of its problems' state was set
- * from outside since the last batch step. */
+ * from outside since the last batch step.
+ *
+ * festung_batch_set_mode: FESTUNG_BATCH_UNION (the joined meshes above, the default) or
+ * FESTUNG_BATCH_CONCURRENT: each problem takes its own single-problem step (festung_step
+ * with opts, FP64 fallback included), `workers` problems at a time (0: 8; at most 64),
+ * each worker on a stream and host thread of its own; a problem's step runs after the
+ * work queued on its own stream and on the batch's stream, and the batch's stream waits
+ * for every worker.  The problems' own streams are left as they were.  On an error the
+ * failing problems keep their C, the others complete their step, and the code of the
+ * first failing problem (by index) is returned.
+ * festung_batch_launch_count: kernels launched by the batch's steps, those on the
+ * problems' own contexts included. */
 typedef struct festung_batch festung_batch;
 int festung_batch_create(festung_ctx *const *problems, int nprob, festung_batch **out);
 int festung_batch_set_stream(festung_batch *batch, void *cuda_stream);
+int festung_batch_set_mode(festung_batch *batch, int mode, int workers);
 int festung_batch_step(festung_batch *batch, double dt, const festung_step_opts *opts, festung_step_info *infos);
 int festung_batch_launch_count(const festung_batch *batch, int64_t *n);
 /* Message of the last failed batch call (batch = NULL: of the last failed create). */

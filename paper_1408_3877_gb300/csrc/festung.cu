@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -1969,6 +1970,13 @@ struct festung_batch {
     cudaStream_t stream = nullptr;
     cudaEvent_t start_ev = nullptr;
     int device = 0;
+    int mode = FESTUNG_BATCH_UNION;
+    int workers = 8;
+    // FESTUNG_BATCH_CONCURRENT: one stream and two events per worker
+    std::vector<cudaStream_t> wstreams;
+    std::vector<cudaEvent_t> wev, wdone;
+    // kernels launched on the problems' own contexts during batch steps
+    std::atomic<int64_t> member_launches{0};
     std::string err;
 };
 
@@ -2320,7 +2328,9 @@ int solve_group(festung_batch *b, BatchGroup &g, double dt, const festung_step_o
         if (state[m] != 2) continue;
         festung_ctx *p = b->probs[g.members[m]];
         festung_step_info in{};
+        const int64_t l0 = p->launches;
         rc = solve_system(p, dt, 1.0, &o, &in);
+        b->member_launches += p->launches - l0;
         if (rc) {
             g.err = "problem " + std::to_string(g.members[m]) + ": " + p->err;
             return rc;
@@ -2352,6 +2362,75 @@ int solve_group(festung_batch *b, BatchGroup &g, double dt, const festung_step_o
     }
     // a member solved on its own differs from the union's C: the union's history restarts
     if (any_single) c->hist = 0;
+    return FESTUNG_OK;
+}
+
+// FESTUNG_BATCH_CONCURRENT: every problem takes its own single-problem step (mixed
+// precision with the FP64 fallback), `workers` problems at a time, each worker on a
+// stream and host thread of its own.  A problem's step runs on the worker's stream after
+// the work queued on the problem's own stream and on the batch's stream; the batch's
+// stream then waits for every worker.
+int batch_step_concurrent(festung_batch *b, double dt, const festung_step_opts &o, festung_step_info *infos) {
+    const int nprob = (int)b->probs.size();
+    const int nw = std::max(1, std::min(b->workers, nprob));
+    while ((int)b->wstreams.size() < nw) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t e1 = nullptr, e2 = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e2, cudaEventDisableTiming) != cudaSuccess) {
+            if (st) cudaStreamDestroy(st);
+            if (e1) cudaEventDestroy(e1);
+            b->err = "CUDA: cannot create the streams of the batch's workers";
+            return FESTUNG_ECUDA;
+        }
+        b->wstreams.push_back(st);
+        b->wev.push_back(e1);
+        b->wdone.push_back(e2);
+    }
+    if (cudaEventRecord(b->start_ev, b->stream) != cudaSuccess) {
+        b->err = "CUDA: cannot record on the batch's stream";
+        return FESTUNG_ECUDA;
+    }
+    std::vector<int> rcs(nprob, FESTUNG_OK);
+    std::vector<std::string> errs(nprob);
+    std::atomic<int> next{0};
+    auto work = [&](int wi) {
+        cudaSetDevice(b->device);
+        cudaStream_t ws = b->wstreams[wi];
+        cudaStreamWaitEvent(ws, b->start_ev, 0);
+        for (int q = next.fetch_add(1); q < nprob; q = next.fetch_add(1)) {
+            festung_ctx *c = b->probs[q];
+            cudaStream_t own = c->stream;
+            festung_step_info in{};
+            if (cudaEventRecord(b->wev[wi], own) != cudaSuccess || cudaStreamWaitEvent(ws, b->wev[wi], 0) != cudaSuccess) {
+                rcs[q] = FESTUNG_ECUDA;
+                errs[q] = "CUDA: cannot order the problem's stream before its step";
+                continue;
+            }
+            const int64_t l0 = c->launches;
+            c->stream = ws;
+            rcs[q] = solve_system(c, dt, 1.0, &o, &in);
+            if (rcs[q]) {
+                cudaStreamSynchronize(ws);  // a failed step may leave work in flight
+                errs[q] = c->err;
+            }
+            c->stream = own;
+            b->member_launches += c->launches - l0;
+            if (infos) infos[q] = in;
+        }
+        cudaEventRecord(b->wdone[wi], ws);
+    };
+    std::vector<std::thread> threads;
+    for (int wi = 1; wi < nw; ++wi) threads.emplace_back(work, wi);
+    work(0);
+    for (auto &t : threads) t.join();
+    for (int wi = 0; wi < nw; ++wi) cudaStreamWaitEvent(b->stream, b->wdone[wi], 0);
+    for (int q = 0; q < nprob; ++q)
+        if (rcs[q]) {
+            b->err = "problem " + std::to_string(q) + ": " + errs[q];
+            return rcs[q];
+        }
     return FESTUNG_OK;
 }
 
@@ -2424,6 +2503,7 @@ int festung_batch_step(festung_batch *b, double dt, const festung_step_opts *opt
         b->err = "bad batch step arguments (FESTUNG_MIXED only)";
         return FESTUNG_EINVAL;
     }
+    if (b->mode == FESTUNG_BATCH_CONCURRENT) return batch_step_concurrent(b, dt, o, infos);
     // the groups run concurrently, each on its own stream and host thread, after the work
     // already queued on the batch's stream; the batch's stream then waits for all of them
     const size_t ng = b->groups.size();
@@ -2459,8 +2539,19 @@ int festung_batch_step(festung_batch *b, double dt, const festung_step_opts *opt
 
 int festung_batch_launch_count(const festung_batch *b, int64_t *n) {
     if (!b || !n) return FESTUNG_EINVAL;
-    *n = 0;
+    *n = b->member_launches.load();
     for (const auto &g : b->groups) *n += g.u->launches;
+    return FESTUNG_OK;
+}
+
+int festung_batch_set_mode(festung_batch *b, int mode, int workers) {
+    if (!b) return FESTUNG_EINVAL;
+    if ((mode != FESTUNG_BATCH_UNION && mode != FESTUNG_BATCH_CONCURRENT) || workers < 0 || workers > 64) {
+        b->err = "bad batch mode or worker count";
+        return FESTUNG_EINVAL;
+    }
+    b->mode = mode;
+    b->workers = workers ? workers : 8;
     return FESTUNG_OK;
 }
 
@@ -2469,6 +2560,12 @@ const char *festung_batch_last_error(const festung_batch *b) { return b ? b->err
 void festung_batch_destroy(festung_batch *b) {
     if (!b) return;
     for (auto &g : b->groups) free_group(g);
+    for (size_t i = 0; i < b->wstreams.size(); ++i) {
+        cudaStreamSynchronize(b->wstreams[i]);
+        cudaStreamDestroy(b->wstreams[i]);
+        cudaEventDestroy(b->wev[i]);
+        cudaEventDestroy(b->wdone[i]);
+    }
     if (b->start_ev) cudaEventDestroy(b->start_ev);
     delete b;
 }

@@ -16,6 +16,7 @@ OK, EINVAL, EMESH, ENOMEM, ECUDA, ENOCONV, ESTATE, EDATA = 0, -1, -2, -3, -4, -5
 HOST, DEVICE = 0, 1
 FP64, FP32, MIXED, DFLOAT = 0, 1, 2, 3
 SOLVER_CG, SOLVER_BICGSTAB = 1, 2
+BATCH_UNION, BATCH_CONCURRENT = 0, 1
 BDR_INTERIOR, BDR_DIRICHLET, BDR_NEUMANN = 0, 1, 2
 
 EXPORTS = [
@@ -27,7 +28,8 @@ EXPORTS = [
     "festung_autotune", "festung_fma_peak", "festung_warmstart_features", "festung_set_guess",
     "festung_mlp_create", "festung_mlp_sizes", "festung_mlp_set_stream", "festung_mlp_forward", "festung_mlp_grad",
     "festung_mlp_adam", "festung_mlp_get", "festung_mlp_set", "festung_mlp_last_error", "festung_mlp_destroy",
-    "festung_batch_create", "festung_batch_set_stream", "festung_batch_step", "festung_batch_launch_count",
+    "festung_batch_create", "festung_batch_set_stream", "festung_batch_set_mode", "festung_batch_step",
+    "festung_batch_launch_count",
     "festung_batch_last_error", "festung_batch_destroy",
 ]
 
@@ -103,6 +105,7 @@ def load(path=None):
     lib.festung_mlp_destroy.restype = None
     lib.festung_batch_create.argtypes = [vp, cint, ctypes.POINTER(vp)]
     lib.festung_batch_set_stream.argtypes = [vp, vp]
+    lib.festung_batch_set_mode.argtypes = [vp, cint, cint]
     lib.festung_batch_step.argtypes = [vp, dbl, ctypes.POINTER(StepOpts), vp]
     lib.festung_batch_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
     lib.festung_batch_last_error.argtypes = [vp]
@@ -304,10 +307,19 @@ class Batch:
         raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
         self._check(self.lib.festung_batch_set_stream(self.h, ctypes.c_void_p(raw)))
 
+    def set_mode(self, mode, workers=0):
+        """BATCH_UNION (joined meshes per group) or BATCH_CONCURRENT (each problem its own
+        step, `workers` at a time; 0: 8)."""
+        self._check(self.lib.festung_batch_set_mode(self.h, mode, workers))
+
     def step(self, dt, tol=1e-10, max_iter=20000, inner_tol=1e-2, max_outer=50, solver=0):
         o = StepOpts(tol, max_iter, MIXED, inner_tol, max_outer, solver)
         infos = (StepInfo * len(self.solvers))()
-        self._check(self.lib.festung_batch_step(self.h, dt, ctypes.byref(o), infos))
+        rc = self.lib.festung_batch_step(self.h, dt, ctypes.byref(o), infos)
+        if rc:
+            err = FestungError(rc, self.lib.festung_batch_last_error(self.h).decode())
+            err.infos = [_info_dict(i) for i in infos]  # what each problem's step reported
+            raise err
         return [_info_dict(i) for i in infos]
 
     def launch_count(self):

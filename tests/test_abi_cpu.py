@@ -34,6 +34,15 @@ def test_exports_every_declared_symbol(lib):
         assert hasattr(lib, n), n
 
 
+def test_binding_constants_match_the_header():
+    from paper_1408_3877_gb300 import festung as F
+    txt = open(os.path.join(ROOT, "include", "festung.h")).read()
+    defs = dict(re.findall(r"#define\s+FESTUNG_([A-Z0-9_]+)\s+(-?\d+)\b", txt))
+    assert len(defs) >= 20
+    for name, value in defs.items():
+        assert getattr(F, name) == int(value), name
+
+
 def _create(lib, cV, V0T, bdr):
     cV = np.ascontiguousarray(cV, dtype=np.float64)
     V0T = np.ascontiguousarray(V0T, dtype=np.int32)

@@ -1,6 +1,8 @@
 """Batches of independent problems (festung_batch_*): every problem of a batch step must
 match the same problem stepped alone (FP64 path, itself pinned to the oracle's solve of
-eq. fullSystem) and meet the tolerance on its own residual."""
+eq. fullSystem) and meet the tolerance on its own residual, with the problems joined
+into one mesh per group (FESTUNG_BATCH_UNION) or stepped one each by several workers
+(FESTUNG_BATCH_CONCURRENT)."""
 import numpy as np
 import pytest
 
@@ -40,7 +42,10 @@ def _load(s, man, t):
     s.set_bc(edge_samples(s, lambda x, y: man.c(t, x, y)), None)
 
 
-def test_batch_matches_single_problem_steps():
+@pytest.mark.parametrize("mode,workers,user_stream", [("BATCH_UNION", 0, False), ("BATCH_CONCURRENT", 3, False),
+                                                     ("BATCH_CONCURRENT", 0, True)])
+def test_batch_matches_single_problem_steps(mode, workers, user_stream):
+    import torch
     from paper_1408_3877_gb300 import festung as F
     tau, steps = 0.005, 3
     probs = [_make(n, p, a, b, seed=10 + q) for q, (n, p, a, b) in enumerate(PROBLEMS)]
@@ -51,11 +56,19 @@ def test_batch_matches_single_problem_steps():
             s.set_state(samples(s, lambda x, y: man.c(0.0, x, y)), is_samples=True)
             lst.append(s)
     batch = F.Batch(bs)
+    batch.set_mode(getattr(F, mode), workers)
+    stream = torch.cuda.Stream() if user_stream else None
+    if stream is not None:
+        batch.set_stream(stream)
     for k in range(1, steps + 1):
         t = k * tau
         for s, (_, _, _, man) in zip(bs, probs):
             _load(s, man, t)
+        l0 = batch.launch_count()
         infos = batch.step(tau, tol=1e-12, inner_tol=1e-2)
+        if stream is not None:
+            stream.synchronize()
+        assert batch.launch_count() > l0
         for q, (s, (_, _, _, man)) in enumerate(zip(ss, probs)):
             _load(s, man, t)
             s.step(tau, tol=1e-13, prec=F.FP64)
@@ -109,5 +122,11 @@ def test_batch_rejects_bad_members():
     with pytest.raises(F.FestungError) as e:
         F.Batch([s, s])
     assert e.value.code == F.EINVAL
+    b = F.Batch([s])
+    for mode, workers in ((2, 0), (F.BATCH_CONCURRENT, -1), (F.BATCH_CONCURRENT, 65)):
+        with pytest.raises(F.FestungError) as e:
+            b.set_mode(mode, workers)
+        assert e.value.code == F.EINVAL
+    b.close()
     s.close()
     raw.close()
