@@ -435,9 +435,10 @@ def profile_apply(args):
 
 def run_batched(args):
     """The batched workload: independent problems of uneven size and order advanced together
-    (festung_batch_step), against the same problems stepped one after the other with the
-    plain FP64 solve and with the single-problem mixed solve.  Timed: the solves only; the
-    per-step loading of sources and boundary data is reported apart."""
+    (festung_batch_step in its default mode, then in the others), against the same problems
+    stepped one after the other with the plain FP64 solve and with the single-problem mixed
+    solve.  Timed: the solves only; the per-step loading of sources and boundary data is
+    reported apart.  A problem whose step does not converge keeps C^n and is counted."""
     import torch
     from paper_1408_3877_gb300 import festung as F
     cfg = W.CONFIGS["batched512"]
@@ -459,9 +460,16 @@ def run_batched(args):
         dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
         data.append((dev(man.f(0.0, X, Y)), dev(man.c(0.0, exy[..., 0], exy[..., 1]))))
         solvers.append(s)
+    # every mode below starts from this state and solves the same time levels
+    C0 = [torch.tensor(s.get_state(), device="cuda") for s in solvers]
     prep = time.perf_counter() - t0
     K = sum(s.K for s in solvers)
     dofs = sum(s.K * s.N for s in solvers)
+
+    def reset():
+        for s, c in zip(solvers, C0):
+            s.set_state(c)
+        torch.cuda.synchronize()
 
     def load(t):
         a = time.perf_counter()
@@ -482,21 +490,7 @@ def run_batched(args):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / 1e3, out
 
-    batch = F.Batch(solvers)
-    step = 0
-    load_s, batch_s, infos = [], [], []
-    for k in range(args.warmup + args.steps):
-        step += 1
-        load_s.append(load(step * dt))
-        sec, info = timed(lambda: batch.step(dt, tol=tol, inner_tol=1e-2))
-        if k >= args.warmup:
-            batch_s.append(sec)
-            infos.append(info)
-    launches = batch.launch_count()
-    # the same batch with every problem stepped on its own, several workers at a time
-    concurrent = {}
-
-    def concurrent_step():
+    def batch_step():
         try:
             return batch.step(dt, tol=tol, inner_tol=1e-2)
         except F.FestungError as e:
@@ -504,26 +498,41 @@ def run_batched(args):
                 raise
             return e.infos  # a problem that did not converge keeps C^n, as one by one
 
-    for workers in (4, 8, 16):
-        batch.set_mode(F.BATCH_CONCURRENT, workers)
-        secs, its_c, failed = [], [], 0
-        for k in range(1 + args.steps):
-            step += 1
-            load(step * dt)
-            sec, info = timed(concurrent_step)
-            if k >= 1:
+    def run_mode(nwarm, nsteps):
+        reset()
+        secs, its, failed, infos, loads = [], [], 0, [], []
+        for k in range(nwarm + nsteps):
+            loads.append(load((k + 1) * dt))
+            sec, info = timed(batch_step)
+            if k >= nwarm:
                 secs.append(sec)
-                its_c += [i["iterations"] for i in info]
+                infos.append(info)
+                its += [i["iterations"] for i in info]
                 failed += sum(1 for i in info if not i["rel_residual"] <= tol)
-        concurrent[workers] = (float(np.mean(secs)), float(np.mean(its_c)), failed)
+        return float(np.mean(secs)), float(np.mean(its)), failed, infos, float(np.mean(loads))
+
+    # the batch in its default mode (every problem its own step, 16 workers at a time)
+    batch = F.Batch(solvers)
+    l0 = batch.launch_count()
+    value, its_mean, failed_batch, infos, load_mean = run_mode(args.warmup, args.steps)
+    launches = batch.launch_count() - l0
+    # the other modes of the same batch
+    others = {}
+    for name, mode, workers in (("union", F.BATCH_UNION, 0), ("concurrent_8_workers", F.BATCH_CONCURRENT, 8),
+                                ("concurrent_4_workers", F.BATCH_CONCURRENT, 4)):
+        batch.set_mode(mode, workers)
+        v, it, f, _, _ = run_mode(args.warmup, args.steps)
+        others[name] = {"value": v, "unit": "s/step", "iterations_per_step_mean": it, "failed_solves": f,
+                        "speedup_of_default": v / value}
     batch.close()
     # the same problems one after the other: single-problem mixed solve, then plain FP64
+    # (the same state and time levels; the last step is timed)
     single = {}
-    for name, prec, nsteps in (("mixed_per_problem", F.MIXED, 3), ("fp64_per_problem", F.FP64, 2)):
+    for name, prec in (("mixed_per_problem", F.MIXED), ("fp64_per_problem", F.FP64)):
         secs, failed = [], 0
-        for k in range(nsteps):
-            step += 1
-            load(step * dt)
+        reset()
+        for k in range(args.warmup + 1):
+            load((k + 1) * dt)
 
             def one_by_one():
                 nonlocal failed
@@ -535,21 +544,19 @@ def run_batched(args):
             sec, _ = timed(one_by_one)
             secs.append(sec)
         single[name] = (secs[-1], failed)
-    value = float(np.mean(batch_s))
-    its = [i["iterations"] for step_info in infos for i in step_info]
     return {"metric": "sec per implicit step of the whole batch at 1e-10 rel. residual per problem",
             "value": value, "unit": "s/step", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": False, "dtype": "f32+dfloat+f64", "data": "synthetic (seeded meshes, fields)",
             "config": {"workload": "batched512", "problems": len(solvers), "triangles": K, "dofs": dofs,
                        "orders": {str(p): sum(1 for sp in specs if sp["p"] == p) for p in (1, 2, 3)},
-                       "dt": dt, "tol": tol, "groups": "one union mesh per order, one Krylov per group"},
-            "dof_per_s": dofs / value, "iterations_per_step_mean": float(np.mean(its)),
-            "rel_residual_max": float(max(i["rel_residual"] for step_info in infos for i in step_info)),
-            "input_loading_s_per_step": float(np.mean(load_s)), "host_preparation_s": prep,
+                       "dt": dt, "tol": tol,
+                       "mode": "concurrent: every problem its own mixed step, 16 workers on their own streams"},
+            "dof_per_s": dofs / value, "iterations_per_step_mean": its_mean, "failed_solves": failed_batch,
+            "rel_residual_max_converged": float(max((i["rel_residual"] for step_info in infos for i in step_info
+                                                     if i["rel_residual"] <= tol), default=0.0)),
+            "input_loading_s_per_step": load_mean, "host_preparation_s": prep,
             "gpu_launches_per_step": launches / (args.warmup + args.steps),
-            "concurrent_mode": {str(w): {"value": v, "unit": "s/step", "iterations_per_step_mean": it,
-                                         "speedup_over_union": value / v, "failed_solves": f}
-                                for w, (v, it, f) in concurrent.items()},
+            "other_modes": others,
             "same_problems_one_by_one": {k: {"value": v, "unit": "s/step", "speedup_of_batch": v / value,
                                              "failed_solves": f} for k, (v, f) in single.items()}}
 

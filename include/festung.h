@@ -73,8 +73,9 @@ extern "C" {
 #define FESTUNG_SOLVER_CG        1
 #define FESTUNG_SOLVER_BICGSTAB  2
 
-#define FESTUNG_BATCH_UNION       0   /* one joined mesh per group (the default)            */
-#define FESTUNG_BATCH_CONCURRENT  1   /* every problem its own step, several at a time      */
+#define FESTUNG_BATCH_UNION       0   /* one joined mesh per group                          */
+#define FESTUNG_BATCH_CONCURRENT  1   /* every problem its own step, several at a time (the
+                                         default)                                           */
 
 typedef struct festung_ctx festung_ctx;
 
@@ -268,36 +269,36 @@ int festung_fma_peak(int prec, double *tflops);
 
 /* ---- Batches of independent problems -------------------------------------------
  * Many problems (each its own context, set up, with its own mesh, order, coefficient,
- * source and boundary data) advance by one implicit-Euler step together.  Problems of
- * the same p, quadrature and eta form a group whose meshes are joined into one internal
- * mesh: each kernel of the step runs over all problems of the group at once.  Every
- * problem runs its own BiCGStab iteration (its own scalars, reductions summed per
- * problem) and its own refinement, and reaches tol on its own residual; tiles of
- * problems that have finished do no work.  A problem the group cannot finish is stepped
- * on its own (the single-problem path with its FP64 fallback).  The paper has no
- * counterpart: it solves one problem at a time.
+ * source and boundary data) advance by one implicit-Euler step together.  The paper has
+ * no counterpart: it solves one problem at a time.  Two modes:
+ *
+ * FESTUNG_BATCH_CONCURRENT (the default): each problem takes its own single-problem step
+ * (festung_step with opts, FP64 fallback included), `workers` problems at a time, each
+ * worker on a CUDA stream and host thread of its own, so that the kernels of small
+ * problems share the GPU.  A problem's step runs after the work queued on its own stream
+ * and on the batch's stream; the problems' own streams are left as they were.
+ *
+ * FESTUNG_BATCH_UNION: problems of the same p, quadrature and eta form a group whose
+ * meshes are joined into one internal mesh, and each kernel of the step runs over all
+ * problems of the group at once.  Every problem runs its own BiCGStab iteration (its own
+ * scalars, reductions summed per problem) and its own refinement, and reaches tol on its
+ * own residual; tiles of problems that have finished do no work.  A problem the group
+ * cannot finish is stepped on its own (the single-problem path).  The groups run
+ * concurrently, each on a stream and host thread of its own.  The extrapolated initial
+ * guess of a group restarts when one of its problems' state was set from outside since
+ * the last batch step.
  *
  * festung_batch_create: problems[0..nprob) stay owned by the caller and must outlive the
  * batch; they must not be set up again while in it.  Their data are set with the usual
  * calls (festung_set_coeff, _source, _bc, _state) before each festung_batch_step, which
  * reads them, steps all problems (FESTUNG_MIXED only; opts as festung_step) and writes
- * every C back (festung_get_state reads it).  infos: nprob entries or NULL.  The groups
- * are stepped concurrently, each on a stream of its own and a host thread of its own,
- * after the work queued on the batch's stream (festung_batch_set_stream; default the
- * legacy default stream), which then waits for all of them; the call returns once every
- * group has finished.  On an error the problems of a failing group keep their C, the
- * other groups complete their step, and the first failing group's code is returned.  The
- * extrapolated initial guess of a group restarts when one of its problems' state was set
- * from outside since the last batch step.
- *
- * festung_batch_set_mode: FESTUNG_BATCH_UNION (the joined meshes above, the default) or
- * FESTUNG_BATCH_CONCURRENT: each problem takes its own single-problem step (festung_step
- * with opts, FP64 fallback included), `workers` problems at a time (0: 8; at most 64),
- * each worker on a stream and host thread of its own; a problem's step runs after the
- * work queued on its own stream and on the batch's stream, and the batch's stream waits
- * for every worker.  The problems' own streams are left as they were.  On an error the
- * failing problems keep their C, the others complete their step, and the code of the
- * first failing problem (by index) is returned.
+ * every C back (festung_get_state reads it).  infos: nprob entries or NULL.  The step
+ * starts after the work queued on the batch's stream (festung_batch_set_stream; default
+ * the legacy default stream), which then waits for all of it; the call returns once every
+ * problem is done.  On an error the failing problems keep their C, the others complete
+ * their step, and the code of the first failure (by problem, or by group) is returned.
+ * festung_batch_set_mode: mode and workers (0: the default, 16 or the host's thread count
+ * if lower; at most 64; the union mode ignores it).
  * festung_batch_launch_count: kernels launched by the batch's steps, those on the
  * problems' own contexts included. */
 typedef struct festung_batch festung_batch;

@@ -1970,8 +1970,8 @@ struct festung_batch {
     cudaStream_t stream = nullptr;
     cudaEvent_t start_ev = nullptr;
     int device = 0;
-    int mode = FESTUNG_BATCH_UNION;
-    int workers = 8;
+    int mode = FESTUNG_BATCH_CONCURRENT;
+    int workers = 16;
     // FESTUNG_BATCH_CONCURRENT: one stream and two events per worker
     std::vector<cudaStream_t> wstreams;
     std::vector<cudaEvent_t> wev, wdone;
@@ -2365,6 +2365,12 @@ int solve_group(festung_batch *b, BatchGroup &g, double dt, const festung_step_o
     return FESTUNG_OK;
 }
 
+// Workers of FESTUNG_BATCH_CONCURRENT by default: 16, or fewer on a host with fewer threads.
+int default_workers() {
+    const unsigned hw = std::thread::hardware_concurrency();
+    return hw ? (int)std::min(16u, hw) : 16;
+}
+
 // FESTUNG_BATCH_CONCURRENT: every problem takes its own single-problem step (mixed
 // precision with the FP64 fallback), `workers` problems at a time, each worker on a
 // stream and host thread of its own.  A problem's step runs on the worker's stream after
@@ -2459,6 +2465,7 @@ int festung_batch_create(festung_ctx *const *problems, int nprob, festung_batch 
     festung_batch *b = new (std::nothrow) festung_batch();
     if (!b) return FESTUNG_ENOMEM;
     b->probs.assign(problems, problems + nprob);
+    b->workers = default_workers();
     if (cudaGetDevice(&b->device) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->start_ev, cudaEventDisableTiming) != cudaSuccess) {
         g_create_err = "CUDA: cannot create the batch's event";
@@ -2551,7 +2558,7 @@ int festung_batch_set_mode(festung_batch *b, int mode, int workers) {
         return FESTUNG_EINVAL;
     }
     b->mode = mode;
-    b->workers = workers ? workers : 8;
+    b->workers = workers ? workers : default_workers();
     return FESTUNG_OK;
 }
 

@@ -308,8 +308,8 @@ class Batch:
         self._check(self.lib.festung_batch_set_stream(self.h, ctypes.c_void_p(raw)))
 
     def set_mode(self, mode, workers=0):
-        """BATCH_UNION (joined meshes per group) or BATCH_CONCURRENT (each problem its own
-        step, `workers` at a time; 0: 8)."""
+        """BATCH_CONCURRENT (the default: each problem its own step, `workers` at a time;
+        0: 16, or the host's thread count if lower) or BATCH_UNION (joined meshes per group)."""
         self._check(self.lib.festung_batch_set_mode(self.h, mode, workers))
 
     def step(self, dt, tol=1e-10, max_iter=20000, inner_tol=1e-2, max_outer=50, solver=0):

@@ -82,7 +82,8 @@ def test_batch_matches_single_problem_steps(mode, workers, user_stream):
         s.close()
 
 
-def test_batch_restarts_history_after_outside_state_change():
+@pytest.mark.parametrize("mode", ["BATCH_UNION", "BATCH_CONCURRENT"])
+def test_batch_restarts_history_after_outside_state_change(mode):
     from paper_1408_3877_gb300 import festung as F
     tau = 0.005
     (n, p, a, b) = PROBLEMS[1]
@@ -94,6 +95,7 @@ def test_batch_restarts_history_after_outside_state_change():
     for s, m in ((s1, man), (s2, man2), (ref, man)):
         s.set_state(samples(s, lambda x, y: m.c(0.0, x, y)), is_samples=True)
     batch = F.Batch([s1, s2])
+    batch.set_mode(getattr(F, mode))
     for k in (1, 2):
         _load(s1, man, k * tau), _load(s2, man2, k * tau)
         batch.step(tau, tol=1e-12)
