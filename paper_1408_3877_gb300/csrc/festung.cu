@@ -2428,8 +2428,15 @@ int batch_step_concurrent(festung_batch *b, double dt, const festung_step_opts &
         cudaEventRecord(b->wdone[wi], ws);
     };
     std::vector<std::thread> threads;
-    for (int wi = 1; wi < nw; ++wi) threads.emplace_back(work, wi);
+    int started = 1;
+    try {
+        for (; started < nw; ++started) threads.emplace_back(work, started);
+    } catch (...) {
+        // no more host threads: the workers that did not start run here, after worker 0
+        // has drained the queue (they only order their streams)
+    }
     work(0);
+    for (int wi = started; wi < nw; ++wi) work(wi);
     for (auto &t : threads) t.join();
     for (int wi = 0; wi < nw; ++wi) cudaStreamWaitEvent(b->stream, b->wdone[wi], 0);
     for (int q = 0; q < nprob; ++q)
@@ -2528,8 +2535,14 @@ int festung_batch_step(festung_batch *b, double dt, const festung_step_opts *opt
         rcs[i] = solve_group(b, b->groups[i], dt, o, infos);
     };
     std::vector<std::thread> threads;
-    for (size_t i = 1; i < ng; ++i) threads.emplace_back(run, i);
+    size_t started = 1;
+    try {
+        for (; started < ng; ++started) threads.emplace_back(run, started);
+    } catch (...) {
+        // no more host threads: the groups that did not start are stepped here in turn
+    }
     run(0);
+    for (size_t i = started; i < ng; ++i) run(i);
     for (auto &t : threads) t.join();
     for (auto &g : b->groups) {
         cudaEventRecord(g.done_ev, g.stream);
