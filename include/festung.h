@@ -284,7 +284,9 @@ int festung_fma_peak(int prec, double *tflops);
  * scalars, reductions summed per problem) and its own refinement, and reaches tol on its
  * own residual; tiles of problems that have finished do no work.  A problem the group
  * cannot finish is stepped on its own (the single-problem path).  The groups run
- * concurrently, each on a stream and host thread of its own.  The extrapolated initial
+ * concurrently, each on a stream and host thread of its own.  The joined meshes are built
+ * at the first union-mode step, which then also reports the errors of building them
+ * (EINVAL for a group with K N >= 2^31, ENOMEM).  The extrapolated initial
  * guess of a group restarts when one of its problems' state was set from outside since
  * the last batch step.
  *

@@ -1918,6 +1918,7 @@ __global__ void k_residual_b(int64_t K, int N, const T *b, const T *y, BatchView
 }
 
 struct BatchGroup {
+    bool built = false;             // the union below exists (built at the first union-mode step)
     festung_ctx *u = nullptr;       // union context
     std::vector<int> members;       // problem indices
     std::vector<int64_t> off;       // element offset of each member (members + 1 entries)
@@ -2071,7 +2072,21 @@ int build_group(festung_batch *b, BatchGroup &g) {
         b->err = u->err;
         return rc;
     }
+    g.built = true;
     return FESTUNG_OK;
+}
+
+// The union of a group, built when the union mode first needs it; a failed build leaves
+// the group as it was.
+int ensure_built(festung_batch *b, BatchGroup &g) {
+    if (g.built) return FESTUNG_OK;
+    const int rc = build_group(b, g);
+    if (rc) {
+        const std::vector<int> members = g.members;
+        free_group(g);
+        g.members = members;
+    }
+    return rc;
 }
 
 // The members' own BiCGStab iterations on the union (FP32, vectors w.f): every member
@@ -2492,14 +2507,6 @@ int festung_batch_create(festung_ctx *const *problems, int nprob, festung_batch 
         }
         hit->members.push_back(q);
     }
-    for (auto &g : b->groups) {
-        int rc = build_group(b, g);
-        if (rc) {
-            g_create_err = b->err;
-            festung_batch_destroy(b);
-            return rc;
-        }
-    }
     *out = b;
     return FESTUNG_OK;
 }
@@ -2518,6 +2525,10 @@ int festung_batch_step(festung_batch *b, double dt, const festung_step_opts *opt
         return FESTUNG_EINVAL;
     }
     if (b->mode == FESTUNG_BATCH_CONCURRENT) return batch_step_concurrent(b, dt, o, infos);
+    for (auto &g : b->groups) {
+        const int rc = ensure_built(b, g);
+        if (rc) return rc;
+    }
     // the groups run concurrently, each on its own stream and host thread, after the work
     // already queued on the batch's stream; the batch's stream then waits for all of them
     const size_t ng = b->groups.size();
@@ -2560,7 +2571,8 @@ int festung_batch_step(festung_batch *b, double dt, const festung_step_opts *opt
 int festung_batch_launch_count(const festung_batch *b, int64_t *n) {
     if (!b || !n) return FESTUNG_EINVAL;
     *n = b->member_launches.load();
-    for (const auto &g : b->groups) *n += g.u->launches;
+    for (const auto &g : b->groups)
+        if (g.u) *n += g.u->launches;
     return FESTUNG_OK;
 }
 
