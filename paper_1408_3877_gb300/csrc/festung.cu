@@ -2424,7 +2424,8 @@ int batch_step_concurrent(festung_batch *b, double dt, const festung_step_opts &
             festung_ctx *c = b->probs[q];
             cudaStream_t own = c->stream;
             festung_step_info in{};
-            if (cudaEventRecord(b->wev[wi], own) != cudaSuccess || cudaStreamWaitEvent(ws, b->wev[wi], 0) != cudaSuccess) {
+            if (cudaEventRecord(b->wev[wi], own) != cudaSuccess ||
+                cudaStreamWaitEvent(ws, b->wev[wi], 0) != cudaSuccess) {
                 rcs[q] = FESTUNG_ECUDA;
                 errs[q] = "CUDA: cannot order the problem's stream before its step";
                 continue;
