@@ -317,6 +317,16 @@ void festung_batch_destroy(festung_batch *batch);
  * the triangle stored at position i (order holds K entries, host memory). */
 int festung_element_order(const festung_ctx *ctx, int64_t *order);
 
+/* The block-Jacobi preconditioner of a step with time step dt, for inspection: blocks
+ * gets the N x N diagonal blocks S_kk of (E1) as the FP32 build computes them (from the
+ * FP32 copies of geometry, tables and D, with the context's current D), inverse the
+ * BF16 inverses the Krylov kernels apply (converted to FP64).  Each K x N x N, host
+ * memory, triangle k in the caller's order, row-major blocks (row i, column j at
+ * (k N + i) N + j); either may be NULL, not both.  The context's preconditioner is
+ * replaced (every step builds its own).  EDATA if a block is singular (the blocks are
+ * still written).  The paper has no counterpart: it solves directly. */
+int festung_precond_blocks(festung_ctx *ctx, double dt, double *blocks, double *inverse);
+
 /* Number of CUDA kernels this context has launched so far (kernels inside a replayed
  * CUDA graph count one each per replay, including those that exit early because the
  * Krylov iteration already converged).  For instrumentation; *count must not be NULL. */

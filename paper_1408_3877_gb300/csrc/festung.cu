@@ -1700,6 +1700,51 @@ int festung_element_order(const festung_ctx *c, int64_t *order) {
     return FESTUNG_OK;
 }
 
+int festung_precond_blocks(festung_ctx *c, double dt, double *blocks, double *inverse) {
+    if (!ready(c)) return c ? FESTUNG_ESTATE : FESTUNG_EINVAL;
+    if (!(dt >= 0.0) || (!blocks && !inverse)) {
+        c->err = "bad preconditioner query arguments";
+        return FESTUNG_EINVAL;
+    }
+    int rc = ensure_ws(c);
+    if (rc) return rc;
+    if ((rc = finish_precond(c))) return rc;  // a build of the last step may still run
+    Workspace &w = *c->ws;
+    const int N = c->N, NQ = (N * N + 7) / 8;
+    const int64_t K = c->K;
+    if (!w.P) FCK(cudaMalloc(&w.P, (size_t)N * N * K * sizeof(float)));
+    if (!w.Pb) FCK(cudaMalloc(&w.Pb, (size_t)NQ * K * 16));
+    cudaStream_t st = c->stream;
+    FCK(cudaMemsetAsync(w.d_flags, 0, sizeof(int), st));
+    launch_blockjacobi(c, w.P, w.Pb, dt, w.d_flags, st);
+    FCK(cudaGetLastError());
+    std::vector<float> hP(blocks ? (size_t)N * N * K : 0);
+    std::vector<uint16_t> hB(inverse ? (size_t)NQ * K * 8 : 0);
+    if (blocks) FCK(cudaMemcpyAsync(hP.data(), w.P, hP.size() * sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (inverse) FCK(cudaMemcpyAsync(hB.data(), w.Pb, hB.size() * sizeof(uint16_t), cudaMemcpyDeviceToHost, st));
+    FCK(cudaMemcpyAsync(w.h_flags, w.d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FCK(cudaStreamSynchronize(st));
+    for (int64_t k = 0; k < K; ++k) {
+        const int64_t kc = c->perm[k];
+        for (int e = 0; e < N * N; ++e) {
+            const int64_t out = kc * N * N + e;  // row i = e / N, column j = e % N
+            if (blocks) blocks[out] = hP[(size_t)e * K + k];
+            if (inverse) {
+                // BF16 chunk e / 8 of triangle k holds entries 8 (e / 8) .. 8 (e / 8) + 7
+                const uint32_t bits = (uint32_t)hB[((size_t)(e / 8) * K + k) * 8 + e % 8] << 16;
+                float f;
+                std::memcpy(&f, &bits, sizeof(f));
+                inverse[out] = f;
+            }
+        }
+    }
+    if (w.h_flags[0]) {
+        c->err = "a diagonal block is singular";
+        return FESTUNG_EDATA;
+    }
+    return FESTUNG_OK;
+}
+
 int festung_launch_count(const festung_ctx *c, int64_t *count) {
     if (!c || !count) return FESTUNG_EINVAL;
     *count = c->launches;

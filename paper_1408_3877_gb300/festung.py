@@ -24,7 +24,8 @@ EXPORTS = [
     "festung_set_coeff", "festung_set_source", "festung_set_bc", "festung_set_state",
     "festung_get_state", "festung_apply", "festung_apply_noalloc", "festung_step", "festung_solve_stationary",
     "festung_l2_error", "festung_get_flux",
-    "festung_element_order", "festung_launch_count", "festung_set_stream", "festung_last_error", "festung_destroy",
+    "festung_element_order", "festung_precond_blocks", "festung_launch_count", "festung_set_stream",
+    "festung_last_error", "festung_destroy",
     "festung_autotune", "festung_fma_peak", "festung_warmstart_features", "festung_set_guess",
     "festung_mlp_create", "festung_mlp_sizes", "festung_mlp_set_stream", "festung_mlp_forward", "festung_mlp_grad",
     "festung_mlp_adam", "festung_mlp_get", "festung_mlp_set", "festung_mlp_last_error", "festung_mlp_destroy",
@@ -83,6 +84,7 @@ def load(path=None):
     lib.festung_set_stream.argtypes = [vp, vp]
     lib.festung_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
     lib.festung_element_order.argtypes = [vp, vp]
+    lib.festung_precond_blocks.argtypes = [vp, dbl, vp, vp]
     lib.festung_last_error.argtypes = [vp]
     lib.festung_last_error.restype = ctypes.c_char_p
     lib.festung_destroy.argtypes = [vp]
@@ -231,6 +233,15 @@ class Solver:
         o = np.zeros(self.K, dtype=np.int64)
         self._check(self.lib.festung_element_order(self.h, o.ctypes.data))
         return o
+
+    def precond_blocks(self, dt):
+        """(blocks, inverse), each K x N x N in the caller's order: the diagonal blocks S_kk
+        of the step operator as the preconditioner build computes them, and the BF16
+        inverses the Krylov kernels apply."""
+        blocks = np.zeros((self.K, self.N, self.N))
+        inverse = np.zeros((self.K, self.N, self.N))
+        self._check(self.lib.festung_precond_blocks(self.h, dt, blocks.ctypes.data, inverse.ctypes.data))
+        return blocks, inverse
 
     def launch_count(self):
         n = ctypes.c_int64()
