@@ -89,3 +89,17 @@ def test_null_arguments(lib):
     assert lib.festung_mesh_create(None, 0, None, 0, None, ctypes.byref(h)) == F.EINVAL
     assert lib.festung_setup(None, 1, 0, 1.0) == F.EINVAL
     lib.festung_destroy(None)
+
+
+def test_header_is_plain_c(tmp_path):
+    """The boundary is a C ABI: the header compiles as strict C99 (no C++ or CUDA types)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "festung.h"\nint main(void) { festung_ctx *c = 0; (void)c; return 0; }\n')
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                        "-fsyntax-only", str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
