@@ -511,7 +511,8 @@ def run_batched(args):
                 failed += sum(1 for i in info if not i["rel_residual"] <= tol)
         return float(np.mean(secs)), float(np.mean(its)), failed, infos, float(np.mean(loads))
 
-    # the batch in its default mode (every problem its own step, 16 workers at a time)
+    # the batch in its default mode (every problem its own step, 16 workers at a time, or as
+    # many as the host has threads)
     batch = F.Batch(solvers)
     l0 = batch.launch_count()
     value, its_mean, failed_batch, infos, load_mean = run_mode(args.warmup, args.steps)
@@ -550,7 +551,8 @@ def run_batched(args):
             "config": {"workload": "batched512", "problems": len(solvers), "triangles": K, "dofs": dofs,
                        "orders": {str(p): sum(1 for sp in specs if sp["p"] == p) for p in (1, 2, 3)},
                        "dt": dt, "tol": tol,
-                       "mode": "concurrent: every problem its own mixed step, 16 workers on their own streams"},
+                       "mode": "concurrent: every problem its own mixed step, %d workers on their own streams"
+                               % min(16, os.cpu_count() or 16)},
             "dof_per_s": dofs / value, "iterations_per_step_mean": its_mean, "failed_solves": failed_batch,
             "rel_residual_max_converged": float(max((i["rel_residual"] for step_info in infos for i in step_info
                                                      if i["rel_residual"] <= tol), default=0.0)),
