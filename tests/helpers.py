@@ -100,3 +100,39 @@ def patch_oracle_rows(cV, V0T, bdr, p, dfun, x, tau, ks, quad_order=None, eta=1.
         out.append(y[loc[k]])
         scale.append(sc[loc[k]])
     return np.array(out), np.array(scale)
+
+
+def patch_case(p):
+    """A stationary problem whose exact solution lies in the discrete space (LDG is
+    consistent, so the discrete solution is the projection of c): for p = 1, c linear;
+    for p >= 2, c quadratic (z = -grad c is then linear).  d is constant, f = -d lap c.
+    Returns c, d, f and g_N = -grad c . nu on the sides of the unit square (outward
+    normals (0, -1) on y = 0, (1, 0) on x = 1, (0, 1) on y = 1, (-1, 0) on x = 0)."""
+    d0 = 2.5
+    if p == 1:
+        def c(x, y):
+            return 1.0 + 2.0 * x - 3.0 * y
+
+        def grad(x, y):
+            return 2.0 + 0.0 * x, -3.0 + 0.0 * y
+        lap = 0.0
+    else:
+        def c(x, y):
+            return 1.0 + 2.0 * x - 3.0 * y + 0.5 * x * x - x * y + 0.25 * y * y
+
+        def grad(x, y):
+            return 2.0 + x - y, -3.0 - x + 0.5 * y
+        lap = 1.5
+
+    def d(x, y):
+        return d0 + 0.0 * x
+
+    def f(x, y):
+        return -d0 * lap + 0.0 * x
+
+    def gN(x, y):
+        cx, cy = grad(x, y)
+        eps = 1e-12
+        return np.where(np.abs(y) < eps, cy, np.where(np.abs(y - 1) < eps, -cy,
+                                                      np.where(np.abs(x) < eps, cx, -cx)))
+    return c, d, f, gN

@@ -61,3 +61,28 @@ def test_stationary_rates_on_gpu():
             s.close()
         rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
         assert abs(rates[-1] - (p + 1)) < 0.3, (p, errs, rates, gold[p])
+
+
+@pytest.mark.parametrize("p", [1, 2, 4])
+@pytest.mark.parametrize("prec_name,bound", [("FP64", 1e-9), ("MIXED", 2e-8)])
+def test_stationary_reproduces_discrete_solutions(p, prec_name, bound):
+    """The patch test of the oracle (consistency of LDG, Sec. 2.2-2.4) on the GPU: with
+    c and z = -grad c in the discrete space the solution is the projection of c (here
+    computed by the GPU's own projection of c's samples); no oracle value enters."""
+    from helpers import patch_case
+    from paper_1408_3877_gb300 import festung as F
+    c, d, f, gN = patch_case(p)
+    cV, V0T, side = W.square_mesh(6, jitter=0.2, seed=5)
+    bdr = W.boundary_types(side, (2, 4), (1, 3))
+    s = gpu_solver(cV, V0T, bdr, p)
+    s.set_state(samples(s, c), is_samples=True)
+    Cp = s.get_state()
+    s.set_state(np.zeros_like(Cp))
+    s.set_coeff(samples(s, d))
+    s.set_source(samples(s, f))
+    s.set_bc(edge_samples(s, c), edge_samples(s, gN))
+    info = s.solve_stationary(tol=1e-13 if prec_name == "FP64" else 1e-12, prec=getattr(F, prec_name))
+    C = s.get_state()
+    err = np.linalg.norm(C - Cp) / np.linalg.norm(Cp)
+    assert err <= bound, (err, info)
+    s.close()

@@ -121,3 +121,19 @@ def test_implicit_euler_first_order_in_time():
     e = [np.linalg.norm(run(n) - ref) for n in (4, 8, 16)]
     r1, r2 = e[0] / e[1], e[1] / e[2]
     assert 1.7 < r1 < 2.6 and 1.7 < r2 < 2.6, e
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("mix", ["dirichlet", "mixed"])
+def test_stationary_reproduces_discrete_solutions(p, mix):
+    """Consistency (Sec. 2.2-2.4): when c and z = -grad c lie in the discrete space, the
+    LDG equations hold for them exactly (jumps vanish, the central fluxes are exact, the
+    Neumann flux d g_N is the true one), so the stationary solution is the projection of
+    c.  Every block and right-hand-side term enters: a dropped term, a wrong sign or a
+    transposed operand breaks it."""
+    from helpers import patch_case
+    c, d, f, gN = patch_case(p)
+    L = _ldg(4, p, mix, seed=5)
+    C = L.stationary(L.project(d), L.project(f), c, gN)
+    Cp = L.project(c)
+    assert np.linalg.norm(C - Cp) <= 1e-11 * np.linalg.norm(Cp)
