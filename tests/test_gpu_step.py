@@ -238,3 +238,32 @@ def test_single_triangle_step(p):
         Co = _oracle_step(L, man, L.project(lambda x, y: man.c(0.0, x, y)), t, tau)
         assert np.linalg.norm(C - Co) <= bound * np.linalg.norm(Co), (prec, info)
     s.close()
+
+
+@pytest.mark.parametrize("p", [1, 2, 4])
+@pytest.mark.parametrize("prec_name,tol,bound", [("FP64", 1e-13, 1e-10), ("MIXED", 1e-12, 1e-9)])
+def test_step_reproduces_discrete_solutions_linear_in_time(p, prec_name, tol, bound):
+    """The step's patch test (Sec. 2.5, consistency of LDG and of the implicit-Euler
+    quotient for c linear in t) on the GPU, against the GPU's own projection of c(t_n+1):
+    no oracle value enters."""
+    from helpers import patch_case
+    from paper_1408_3877_gb300 import festung as F
+    c0, d, f0, gN0 = patch_case(p)
+    c1, _, f1, gN1 = patch_case(1)
+    cV, V0T, side = W.square_mesh(8, jitter=0.2, seed=5)
+    bdr = W.boundary_types(side, (2, 4), (1, 3))
+    s = gpu_solver(cV, V0T, bdr, p)
+    tn, tau = 0.3, 0.05
+    t = tn + tau
+    s.set_state(samples(s, lambda x, y: c0(x, y) + t * c1(x, y)), is_samples=True)
+    Cp = s.get_state()
+    s.set_state(samples(s, lambda x, y: c0(x, y) + tn * c1(x, y)), is_samples=True)
+    s.set_coeff(samples(s, d))
+    s.set_source(samples(s, lambda x, y: c1(x, y) + f0(x, y) + t * f1(x, y)))
+    s.set_bc(edge_samples(s, lambda x, y: c0(x, y) + t * c1(x, y)),
+             edge_samples(s, lambda x, y: gN0(x, y) + t * gN1(x, y)))
+    info = s.step(tau, tol=tol, prec=getattr(F, prec_name), inner_tol=1e-3)
+    C = s.get_state()
+    err = np.linalg.norm(C - Cp) / np.linalg.norm(Cp)
+    assert err <= bound, (err, info)
+    s.close()

@@ -137,3 +137,31 @@ def test_stationary_reproduces_discrete_solutions(p, mix):
     C = L.stationary(L.project(d), L.project(f), c, gN)
     Cp = L.project(c)
     assert np.linalg.norm(C - Cp) <= 1e-11 * np.linalg.norm(Cp)
+
+
+@pytest.mark.parametrize("p", [1, 2, 4])
+@pytest.mark.parametrize("mix", ["dirichlet", "mixed"])
+def test_step_reproduces_discrete_solutions_linear_in_time(p, mix):
+    """Consistency of the implicit-Euler step (Sec. 2.5): for c(t) = c0 + t c1 with c0,
+    c1 and their gradients in the discrete space, the difference quotient of the step is
+    exact, so one step from the projection of c(t_n) gives the projection of c(t_n+1)."""
+    from helpers import patch_case
+    c0, d, f0, gN0 = patch_case(p)
+    c1, _, f1, gN1 = patch_case(1)          # a linear rate: its own Laplacian is zero
+
+    def c(t, x, y):
+        return c0(x, y) + t * c1(x, y)
+
+    def f(t, x, y):                        # dt c - div(d grad c) = c1 + f0 + t f1
+        return c1(x, y) + f0(x, y) + t * f1(x, y)
+
+    def gN(t, x, y):
+        return gN0(x, y) + t * gN1(x, y)
+
+    L = _ldg(4, p, mix, seed=5)
+    tn, tau = 0.3, 0.05
+    t = tn + tau
+    C = L.step(L.project(lambda x, y: c(tn, x, y)), L.project(d), L.project(lambda x, y: f(t, x, y)),
+               lambda x, y: c(t, x, y), lambda x, y: gN(t, x, y), tau)
+    Cp = L.project(lambda x, y: c(t, x, y))
+    assert np.linalg.norm(C - Cp) <= 1e-12 * np.linalg.norm(Cp)
