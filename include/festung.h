@@ -175,9 +175,11 @@ int festung_apply(festung_ctx *ctx, const void *x, void *y, int prec, double dt)
  * for FP32); larger meshes get FESTUNG_EINVAL.  The array exists once per device
  * for the life of the process and is shared by all contexts and calls: calls whose
  * kernels overlap on the GPU (other streams or threads) race on it and must be
- * ordered by the caller.  The first call on a device looks up the array's device
- * address; make that first call before any stream capture.  Arguments, layout and
- * errors as festung_apply(). */
+ * ordered by the caller.  Every call made outside stream capture looks up the array's
+ * device address (it changes when cudaDeviceReset replaces the device's context); a call
+ * on a stream being captured reuses the last address found, so make the first call on a
+ * device before any stream capture (ESTATE otherwise).  Arguments, layout and errors as
+ * festung_apply(). */
 int festung_apply_noalloc(festung_ctx *ctx, const void *x, void *y, int prec, double dt);
 
 /* One implicit-Euler step of size dt (Sec. 2.5): forms b of (E2) from the current

@@ -49,11 +49,21 @@ extern "C" int festung_apply_noalloc(festung_ctx *c, const void *x, void *y, int
         c->err = std::string("festung_apply_noalloc: no usable current device: ") + cudaGetErrorString(e);
         return FESTUNG_ECUDA;
     }
+    // The array's device address belongs to the device's current primary context, which a
+    // cudaDeviceReset replaces.  So it is looked up again on every call made outside stream
+    // capture (the lookup is cheap), and the last address found is used only while the
+    // context's stream is being captured.  The first call on a device must therefore come
+    // before any capture.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(c->stream, &cap);
+    if (e != cudaSuccess) {
+        c->err = std::string("festung_apply_noalloc: cudaStreamIsCapturing failed: ") + cudaGetErrorString(e);
+        return FESTUNG_ECUDA;
+    }
     void *base = nullptr;
     {
-        // first call on this device: resolve the device address of the array
         std::lock_guard<std::mutex> lock(g_scratch_mu);
-        if (!g_scratch_addr[dev]) {
+        if (cap == cudaStreamCaptureStatusNone) {
             void *ptr = nullptr;
             e = cudaGetSymbolAddress(&ptr, g_apply_scratch);
             if (e != cudaSuccess || !ptr) {
@@ -61,6 +71,9 @@ extern "C" int festung_apply_noalloc(festung_ctx *c, const void *x, void *y, int
                 return FESTUNG_ECUDA;
             }
             g_scratch_addr[dev] = ptr;
+        } else if (!g_scratch_addr[dev]) {
+            c->err = "festung_apply_noalloc: the first call on a device must come before any stream capture";
+            return FESTUNG_ESTATE;
         }
         base = g_scratch_addr[dev];
     }

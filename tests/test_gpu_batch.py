@@ -132,3 +132,35 @@ def test_batch_rejects_bad_members():
     b.close()
     s.close()
     raw.close()
+
+
+@pytest.mark.parametrize("mode", ["BATCH_UNION", "BATCH_CONCURRENT"])
+def test_batch_members_match_oracle(mode):
+    """Every member of a batch step against the oracle's sparse direct solve of its own
+    eliminated system (Sec. 2.5) from the same state: within 1e-9 relative L2 at tolerance
+    1e-12.  One member (24 x 24, 1,152 triangles) spans several tiles of its own."""
+    from oracle.solve import LDG
+    from paper_1408_3877_gb300 import festung as F
+    tau, t = 0.005, 0.005
+    specs = PROBLEMS[:4] + [(24, 2, 2.0, 3.0)]
+    probs = [_make(n, p, a, b, seed=30 + q) for q, (n, p, a, b) in enumerate(specs)]
+    bs = []
+    for (cV, V0T, bdr, man), (n, p, a, b) in zip(probs, specs):
+        s = gpu_solver(cV, V0T, bdr, p)
+        s.set_state(samples(s, lambda x, y: man.c(0.0, x, y)), is_samples=True)
+        _load(s, man, t)
+        bs.append(s)
+    batch = F.Batch(bs)
+    batch.set_mode(getattr(F, mode), 0)
+    infos = batch.step(tau, tol=1e-12, inner_tol=1e-2)
+    for q, ((cV, V0T, bdr, man), (n, p, a, b)) in enumerate(zip(probs, specs)):
+        L = LDG(cV, V0T, bdr, p)
+        Co = L.step(L.project(lambda x, y: man.c(0.0, x, y)), L.project(lambda x, y: man.d(t, x, y)),
+                    L.project(lambda x, y: man.f(t, x, y)), lambda x, y: man.c(t, x, y), None, tau)
+        Cb = bs[q].get_state()
+        err = np.linalg.norm(Cb - Co) / np.linalg.norm(Co)
+        assert err <= 1e-9, (q, err, infos[q])
+        assert infos[q]["rel_residual"] <= 1e-12, infos[q]
+    batch.close()
+    for s in bs:
+        s.close()

@@ -102,3 +102,34 @@ def test_two_triangle_projection_ranges():
         C = project.project(g, f, N, p + 2)
         vals = project.evaluate(C, np.array(nodes[N][0], float), np.array(nodes[N][1], float))
         assert abs(vals.min() - lo) < 1e-12 and abs(vals.max() - hi) < 1e-12, (N, vals.min(), vals.max())
+
+
+@pytest.mark.parametrize("p", [0, 2, 4])
+def test_l2_error_absolute_scale_closed_forms(p):
+    """Absolute scale of the L2 error (Sec. 3.5), which convergence rates cannot see:
+    on the unit square (jittered and regular meshes) ||0 - 1|| = 1, ||0 - x|| = 1/sqrt(3),
+    ||0 - xy|| = 1/3, and with c_h the projection of 1, ||c_h - (1 + x)|| = 1/sqrt(3).
+    A dropped factor 2, a missing |T_k| weight or a mis-evaluated c_h changes these."""
+    from oracle import quadrature
+    for jitter in (0.0, 0.25):
+        cV, V0T, side = W.square_mesh(5, jitter=jitter, seed=7)
+        bdr = W.boundary_types(side, dirichlet=(1, 2, 3, 4))
+        g = grid.generate_grid_data(cV, V0T, bdr)
+        N = basis.num_dofs(p)
+        Z = np.zeros((g.numT, N))
+        qT = max(4, 2 * p + 2)  # exact for the degree-4 integrand (xy)^2
+        assert project.l2_error(g, Z, lambda x, y: 1.0 + 0.0 * x, qT) == pytest.approx(1.0, rel=1e-13)
+        assert project.l2_error(g, Z, lambda x, y: x, qT) == pytest.approx(1.0 / np.sqrt(3.0), rel=1e-13)
+        assert project.l2_error(g, Z, lambda x, y: x * y, qT) == pytest.approx(1.0 / 3.0, rel=1e-13)
+        one = project.project(g, lambda x, y: 1.0 + 0.0 * x, N, max(1, 2 * p))
+        assert project.l2_error(g, one, lambda x, y: 1.0 + x, qT) == pytest.approx(1.0 / np.sqrt(3.0), rel=1e-13)
+        # a sliver of the domain: the error of c_h = 0 against the indicator-like data
+        # 1 on one triangle only is sqrt(|T_k|)
+        k = 3
+        mask = np.zeros(g.numT)
+        mask[k] = 1.0
+        q1, q2, _ = quadrature.triangle_rule(qT)
+        X, _ = grid.map_to_physical(g, q1, q2)
+        ind = np.broadcast_to(mask[:, None], X.shape)
+        err = project.l2_error(g, Z, lambda x, y: ind, qT)
+        assert err == pytest.approx(np.sqrt(g.areaT[k]), rel=1e-13)

@@ -61,9 +61,42 @@ def test_noalloc_rejects_meshes_beyond_the_fixed_scratch():
     y = torch.empty_like(x)
     assert _call(s, s.lib.festung_apply_noalloc, x, y, F.FP64, 0.01) == F.EINVAL
     assert "32" in s.lib.festung_last_error(s.h).decode() or "bytes" in s.lib.festung_last_error(s.h).decode()
-    xf = torch.zeros(s.N, s.K, dtype=torch.float32, device="cuda")
-    yf = torch.empty_like(xf)
+    # the FP32 case near the limit, on seeded random data against festung_apply
+    g = torch.Generator("cuda").manual_seed(5)
+    xf = torch.randn(s.N, s.K, dtype=torch.float32, device="cuda", generator=g)
+    yf = torch.full_like(xf, float("nan"))
+    yr = torch.empty_like(xf)
     assert _call(s, s.lib.festung_apply_noalloc, xf, yf, F.FP32, 0.01) == F.OK
+    assert _call(s, s.lib.festung_apply, xf, yr, F.FP32, 0.01) == F.OK
     torch.cuda.synchronize()
-    assert yf.abs().max().item() == 0.0
+    assert torch.isfinite(yf).all()
+    assert (yf - yr).abs().max().item() <= 64 * EPS32 * yr.abs().max().item()
+    s.close()
+
+
+def test_noalloc_first_call_on_a_fresh_context_allocates_nothing():
+    """The entry point as the very first apply of a new context (nothing has allocated the
+    context's apply workspace yet), then a second call: both match festung_apply, and the
+    second call leaves the device's free memory unchanged."""
+    import torch
+    from paper_1408_3877_gb300 import festung as F
+    cV, V0T, bdr = mesh(24, "dirichlet", seed=9)
+    s = gpu_solver(cV, V0T, bdr, 2)
+    s.set_coeff(samples(s, smooth_d))
+    g = torch.Generator("cuda").manual_seed(11)
+    x = torch.randn(s.N, s.K, dtype=torch.float64, device="cuda", generator=g)
+    y1, y2, yr = (torch.full_like(x, float("nan")) for _ in range(3))
+    assert _call(s, s.lib.festung_apply_noalloc, x, y1, F.FP64, 0.005) == F.OK
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    assert _call(s, s.lib.festung_apply_noalloc, x, y2, F.FP64, 0.005) == F.OK
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0
+    assert _call(s, s.lib.festung_apply, x, yr, F.FP64, 0.005) == F.OK
+    torch.cuda.synchronize()
+    scale = yr.abs().max().item()
+    for y in (y1, y2):
+        assert torch.isfinite(y).all()
+        assert (y - yr).abs().max().item() <= 64 * EPS64 * scale
     s.close()
