@@ -137,22 +137,65 @@ def timed_oracle_step(cfg, n_sample, p):
     return time.perf_counter() - t0, L.K * L.N
 
 
-def cpu_baseline(cfg, full_dofs, budget_s=15.0):
-    """The oracle as it stands, on a bounded sample: the largest mesh n_s x n_s whose
-    step fits the budget; seconds per step extrapolated linearly in DOFs."""
-    n_s, last = 8, None
+def cpu_model():
+    """The host CPU's model name (x86 'model name', or the Arm implementer/part fields)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model name"):
+        for line in info.splitlines():
+            if line.startswith(key):
+                return line.split(":", 1)[1].strip()
+    fields = {}
+    for line in info.splitlines():
+        if ":" in line:
+            k, v = line.split(":", 1)
+            fields.setdefault(k.strip(), v.strip())
+    return "Arm implementer %s part %s" % (fields.get("CPU implementer", "?"), fields.get("CPU part", "?"))
+
+
+def oracle_spmv_rate(cfg, n_s, p, reps=5):
+    """DOF-applications per second of the oracle's apply (its assembled CSR operator S times a
+    vector, FP64, one core) on an n_s x n_s grid of the workload; SpMV cost is linear in the
+    nonzeros, so the rate carries over to the full grid."""
+    from oracle.solve import LDG
+    cV, V0T, side = W.square_mesh(n_s, jitter=cfg["jitter"], seed=11)
+    bdr = W.boundary_types(side, cfg["dirichlet"], cfg["neumann"])
+    L = LDG(cV, V0T, bdr, p)
+    D = L.project(lambda x, y: 1.0 + 0.5 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y))
+    S = L.operator(D, cfg["dt"])
+    x = np.random.default_rng(0).standard_normal(S.shape[0])
+    S @ x
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        S @ x
+    return S.shape[0] * reps / (time.perf_counter() - t0), S.shape[0]
+
+
+def cpu_baseline(cfg, full_dofs, budget_s=30.0):
+    """The oracle as it stands, on bounded samples of the workload: one step (assembly +
+    SuperLU) on two grids n x n and 2n x 2n, the largest pair within the budget; the
+    growth exponent a of t ~ DOFs^a fitted between them extrapolates to the full grid.
+    Plus the oracle's apply rate (CSR SpMV) on the larger sample."""
+    samples, n_s = [], 8
     while True:
         sec, dofs = timed_oracle_step(cfg, n_s, cfg["p"])
-        last = (n_s, sec, dofs)
-        if sec * 4.5 > budget_s or n_s >= 64:
+        samples.append((n_s, sec, dofs))
+        if sum(x[1] for x in samples) + 5.0 * sec > budget_s or n_s >= 64:
             break
         n_s *= 2
-    n_s, sec, dofs = last
-    return {"value": sec * full_dofs / dofs, "unit": "s/step", "cores": 1, "kind": "oracle",
-            "sample": "one implicit-Euler step of the same workload on a %dx%d jittered grid (%d DOFs, "
-                      "assembly + SuperLU) took %.3f s on 1 host core; scaled linearly to %d DOFs "
-                      "(optimistic for the oracle: the direct solve grows faster than linearly)"
-                      % (n_s, n_s, dofs, sec, full_dofs)}
+    (n1, t1, d1), (n2, t2, d2) = (samples[-2], samples[-1]) if len(samples) > 1 else (samples[0], samples[0])
+    a = max(1.0, np.log(t2 / t1) / np.log(d2 / d1)) if d2 > d1 else 1.0
+    rate, _ = oracle_spmv_rate(cfg, n2, cfg["p"])
+    return {"value": t2 * (full_dofs / d2) ** a, "unit": "s/step", "cores": 1, "kind": "oracle",
+            "sample": "one implicit-Euler step of the same workload (assembly + SuperLU) on %dx%d and %dx%d "
+                      "jittered grids (%d and %d DOFs) took %.3f s and %.3f s on 1 host core; t ~ DOFs^%.2f "
+                      "between them, extrapolated to %d DOFs" % (n1, n1, n2, n2, d1, d2, t1, t2, a, full_dofs),
+            "samples_s_per_step": {"%dx%d" % (n, n): t for n, t, _ in samples},
+            "apply_dof_per_s": rate, "apply_sample": "CSR SpMV of the oracle's S on the %dx%d grid, FP64" % (n2, n2),
+            "host_threads": os.cpu_count(), "cpu_model": cpu_model()}
 
 
 def job_seconds_per_step(t_local, steps, world, dist=None, device="cpu"):
@@ -259,10 +302,10 @@ def run_festung(args):
     barrier()
     e2e = job_seconds_per_step(time.perf_counter() - t0, args.steps, world, dist, "cuda")
 
-    # ---- the same step with the plain FP64 solve (the form the mixed one is measured against) ----
+    # ---- the same step with the plain FP64 solve (the form the mixed one is measured against),
+    # continuing the trajectory, so with the same extrapolated initial guesses ----
     fp64_steps = []
     for j in range(2):
-        # the next time levels after the end-to-end steps, so that the state and the data match
         d, f, cD, gN = step_inputs(s, cfg, man, (nsteps + args.steps + j + 1) * dt, dev)
         s.set_coeff(d)
         s.set_source(f)
@@ -274,6 +317,49 @@ def run_festung(args):
         b.record(stream)
         torch.cuda.synchronize()
         fp64_steps.append((a.elapsed_time(b) / 1e3, info64["iterations"]))
+
+    # ---- accuracy of the timed form: one more mixed step (same history, so the same
+    # extrapolated guess as the timed steps) against an FP64 step at 1e-13 from the same state
+    t_next = (nsteps + args.steps + 3) * dt
+    nxt = step_inputs(s, cfg, man, t_next, dev)
+
+    def load(data):
+        s.set_coeff(data[0])
+        s.set_source(data[1])
+        s.set_bc(data[2], data[3])
+
+    C_n = s.get_state()
+    load(nxt)
+    info_chk = s.step(dt, tol=tol, prec=F.MIXED, inner_tol=1e-2)
+    C_mix = s.get_state()
+    s.set_state(C_n)
+    load(nxt)
+    s.step(dt, tol=1e-13, prec=F.FP64)
+    C_ref = s.get_state()
+    err_vs_fp64 = float(np.linalg.norm(C_mix - C_ref) / np.linalg.norm(C_ref))
+
+    # ---- every precision mode of the step from one state (C^n as initial guess: set_state
+    # restarts the time extrapolation), each against the same FP64 reference ----
+    def timed_step(prec):
+        s.set_state(C_n)
+        load(nxt)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        a.record(stream)
+        info = s.step(dt, tol=tol, prec=prec, inner_tol=1e-2)
+        b.record(stream)
+        torch.cuda.synchronize()
+        C = s.get_state()
+        return {"s": a.elapsed_time(b) / 1e3, "iterations": info["iterations"], "outer": info["outer"],
+                "fp64_iterations": info["fp64_iterations"], "rel_residual": info["rel_residual"],
+                "err_vs_fp64": float(np.linalg.norm(C - C_ref) / np.linalg.norm(C_ref))}
+
+    mode_names = (("fp64", F.FP64), ("mixed_dfloat_residual", F.MIXED), ("mixed_fp64_residual", F.MIXED64),
+                  ("bf16_tables_fp64_residual", F.BF16TAB))
+    modes = {}
+    for _ in range(2):  # the second round is timed (the first builds each mode's graphs)
+        for name, prec in mode_names:
+            modes[name] = timed_step(prec)
 
     # ---- operator apply alone: this workload (L2 flushed between launches) ----
     pk, pk_kind = peaks()
@@ -360,8 +446,15 @@ def run_festung(args):
         "outer_per_step": float(np.mean([i["outer"] for i in infos])),
         "rel_residual_max": float(max(i["rel_residual"] for i in infos)),
         "initial_rel_residual_median": float(np.median([i["initial_rel_residual"] for i in infos])),
+        "err_vs_fp64": err_vs_fp64,
+        "err_vs_fp64_note": "relative L2 difference of a mixed step (same history as the timed steps, %d "
+                            "iterations) to an FP64 step at 1e-13 from the same state" % info_chk["iterations"],
         "plain_fp64_step": {"value": fp64_steps[-1][0], "unit": "s/step", "iterations": fp64_steps[-1][1],
-                            "note": "the same workload stepped with FESTUNG_FP64 (FP64 Krylov and residual)"},
+                            "note": "the same trajectory continued with FESTUNG_FP64 (FP64 Krylov and residual, "
+                                    "the same extrapolated initial guess)"},
+        "modes_from_one_state": modes,
+        "modes_note": "one step of every precision mode from the same C^n (initial guess C^n) and data, to the "
+                      "same tolerance; err_vs_fp64 against an FP64 step at 1e-13 from that state",
         "apply": apply_main, "apply_large": apply_big,
         "roofline": roof,
         "e2e": {"value": e2e, "unit": "s/step", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -375,26 +468,37 @@ def run_festung(args):
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores: each step is one oracle step (assembly +
+    SuperLU) on the 32 x 32 sample of the workload, extrapolated to the full grid with the
+    growth exponent t ~ DOFs^a that the warm-up fits between the 16 x 16 and 32 x 32 samples."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
     cfg = W.CONFIGS[CFG_NAME]
     full = 2 * cfg["n"] ** 2 * 15
-    for _ in range(args.warmup):
-        timed_oracle_step(cfg, 16, cfg["p"])
-    vals = []
     t0 = time.perf_counter()
+    t16 = d16 = t32 = d32 = None
+    for _ in range(max(1, args.warmup - 1)):
+        t16, d16 = timed_oracle_step(cfg, 16, cfg["p"])
+    t32, d32 = timed_oracle_step(cfg, 32, cfg["p"])
+    a = max(1.0, np.log(t32 / t16) / np.log(d32 / d16))
+    secs = []
     for _ in range(args.steps):
         sec, dofs = timed_oracle_step(cfg, 32, cfg["p"])
-        vals.append(sec * full / dofs)
-    v = float(np.mean(vals))
+        secs.append(sec)
+    sample = float(np.mean(secs))
+    v = sample * (full / d32) ** a
+    cpu = {"value": v, "unit": "s/step", "cores": 1, "kind": "oracle",
+           "sample": "each step: one oracle step (assembly + SuperLU) on a 32x32 jittered grid of the workload "
+                     "(%d DOFs, %.3f s measured), extrapolated to %d DOFs with t ~ DOFs^%.2f fitted between the "
+                     "16x16 and 32x32 samples" % (d32, sample, full, a),
+           "host_threads": os.cpu_count(), "cpu_model": cpu_model()}
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "s/step", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": CFG_NAME, "triangles": 2 * cfg["n"] ** 2, "p": cfg["p"], "dofs": full},
-            "cpu_baseline": {"value": v, "unit": "s/step", "cores": 1, "kind": "oracle",
-                             "sample": "each step: one oracle step (assembly + SuperLU) on a 32x32 jittered grid "
-                                       "of the workload, scaled linearly in DOFs to the full grid"},
+            "sample_ms_per_step": sample * 1e3,
+            "cpu_baseline": cpu,
             "e2e": {"value": v, "unit": "s/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t0}
 
@@ -695,6 +799,72 @@ def run_learned(args):
             "data_generation_s": gen_s, "training_s": train_s}
 
 
+def run_grf_step(args):
+    """The 1024 x 1024 precision sweep (2,097,152 triangles, p = 2): d = exp(g) of a seeded
+    squared-exponential Gaussian field (l = 0.05, variance 1), f = 0, zero-flux boundaries,
+    C^0 from seeded normal coefficients over (1 + j), dt = 1e-4.  The same trajectory of
+    `grf_steps` implicit steps is run with the plain FP64 solve and with FP32 inner sweeps on
+    the FP32 operator and on the BF16-table operator (both refined on FP64 residuals; the
+    double-float residual mode beside them), each to 1e-10; every final state is compared
+    with an FP64 trajectory solved to 1e-12 (the FP64 rounding floor of this operator
+    lies near 1e-13).  L2 is flushed before every step (the state
+    alone is 100 MB)."""
+    import torch
+    from paper_1408_3877_gb300 import festung as F
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    c, cV, V0T, bdr = make_problem("grf1024_p2", seed=12)
+    s = F.Solver(cV, V0T, bdr).setup(c["p"])
+    stream = torch.cuda.current_stream()
+    s.set_stream(stream)
+    K, N = s.K, s.N
+    xy, _ = s.quad_points()
+    g = W.GaussianField(5, c["grf_length"])
+    s.set_coeff(np.exp(g(xy[..., 0], xy[..., 1])))
+    del xy
+    s.set_source(None)
+    s.set_bc(None, None)
+    C0 = W.random_state(K, N, 2024)
+    dt, tol, nsteps = c["dt"], 1e-10, args.grf_steps
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def trajectory(prec, tol_):
+        s.set_state(C0)
+        secs, its, outer, fb = [], [], [], 0
+        clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+        clocks.start()
+        for _ in range(nsteps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            info = s.step(dt, tol=tol_, prec=prec, inner_tol=1e-2)
+            b.record(stream)
+            torch.cuda.synchronize()
+            secs.append(a.elapsed_time(b) / 1e3)
+            its.append(info["iterations"])
+            outer.append(info["outer"])
+            fb += info["fp64_iterations"]
+        return s.get_state(), {"s_per_step": float(np.mean(secs)), "iterations_per_step": float(np.mean(its)),
+                               "outer_per_step": float(np.mean(outer)), "fp64_fallback_iterations": fb,
+                               "clocks": clocks.stop()}
+
+    C_ref, ref = trajectory(F.FP64, 1e-12)
+    out = {}
+    for name, prec in (("fp64", F.FP64), ("fp32_fp64_residual", F.MIXED64),
+                       ("bf16_tables_fp64_residual", F.BF16TAB), ("fp32_dfloat_residual", F.MIXED)):
+        C, r = trajectory(prec, tol)
+        r["err_vs_fp64_reference"] = float(np.linalg.norm(C - C_ref) / np.linalg.norm(C_ref))
+        out[name] = r
+    s.close()
+    best = min(out.values(), key=lambda r: r["s_per_step"])
+    return {"metric": "sec per implicit step at 1e-10 rel. residual, precision sweep", "value": best["s_per_step"],
+            "unit": "s/step", "n_gpus": 1, "steps": nsteps, "higher_is_better": False,
+            "dtype": "f64 / f32 / bf16-tables+f32, f64 refinement", "data": "synthetic (seeded field and state)",
+            "config": {"workload": "grf1024_p2", "triangles": K, "p": c["p"], "dofs": K * N, "dt": dt, "tol": tol,
+                       "l2": "flushed before every step"},
+            "modes": out, "fp64_reference_1e-12": ref,
+            "note": "value = the fastest mode; each mode runs the same %d steps from C^0" % nsteps}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -712,7 +882,8 @@ def main():
     ap.add_argument("--train-iters", type=int, default=600, help="learned: Adam steps")
     ap.add_argument("--weighted-loss", type=int, default=0,
                     help="learned: weight the loss by sqrt(diag S / 2|T|) (1) or not (0)")
-    ap.add_argument("--workload", default=None, choices=["batched512", "learned"],
+    ap.add_argument("--grf-steps", type=int, default=50, help="grf1024_p2: implicit steps per mode")
+    ap.add_argument("--workload", default=None, choices=["batched512", "learned", "grf1024_p2"],
                     help="run another workload than the default step benchmark; prints one line")
     ap.add_argument("--nprob", type=int, default=None, help="batched512: number of problems (default 512)")
     args = ap.parse_args()
@@ -724,6 +895,8 @@ def main():
         line = run_batched(args)
     elif args.workload == "learned":
         line = run_learned(args)
+    elif args.workload == "grf1024_p2":
+        line = run_grf_step(args)
     elif args.impl == "reference":
         line = run_reference(args)
     else:

@@ -65,6 +65,13 @@ extern "C" {
                                  double-float arithmetic (value = hi + lo, two FP32
                                  numbers, about 48 significant bits) from double-float
                                  copies of D, the geometry and the tables               */
+#define FESTUNG_BF16TAB   4   /* apply: FP32 arrays, the FP32 operator with its reference
+                                 tables (basis values, weighted gradients, H^, edge
+                                 traces) rounded to BF16, FP32 accumulation; step: FP32
+                                 inner Krylov with that operator, refinement on residuals
+                                 evaluated in FP64 (the FESTUNG_FP64 operator)          */
+#define FESTUNG_MIXED64   5   /* step only: FP32 inner Krylov, refinement on residuals
+                                 evaluated in FP64 (the FESTUNG_FP64 operator)          */
 
 #define FESTUNG_BDR_INTERIOR  0
 #define FESTUNG_BDR_DIRICHLET 1
@@ -82,7 +89,7 @@ typedef struct festung_ctx festung_ctx;
 typedef struct festung_step_opts {
     double tol;          /* stop when ||b - S C||_2 <= tol ||b||_2 (unpreconditioned, over K x N) */
     int    max_iter;     /* bound on Krylov iterations (all inner iterations in FESTUNG_MIXED)  */
-    int    prec;         /* FESTUNG_FP64 or FESTUNG_MIXED                                       */
+    int    prec;         /* FESTUNG_FP64, FESTUNG_MIXED, FESTUNG_MIXED64 or FESTUNG_BF16TAB     */
     double inner_tol;    /* FESTUNG_MIXED: relative reduction per inner FP32 solve (e.g. 1e-2)   */
     int    max_outer;    /* FESTUNG_MIXED: bound on refinement sweeps                          */
     int    solver;       /* 0: choose (CG iff S is symmetric); else FESTUNG_SOLVER_*            */
@@ -91,10 +98,11 @@ typedef struct festung_step_opts {
 typedef struct festung_step_info {
     int    iterations;   /* Krylov iterations (summed over refinement sweeps)                  */
     int    outer;        /* refinement sweeps (1 for FESTUNG_FP64)                              */
-    double rel_residual; /* final ||b - S C||_2 / ||b||_2 (FESTUNG_MIXED: S C in double-float)  */
+    double rel_residual; /* final ||b - S C||_2 / ||b||_2 (FESTUNG_MIXED: S C in double-float;
+                            the other modes: in FP64)                                        */
     int    solver;       /* FESTUNG_SOLVER_CG or FESTUNG_SOLVER_BICGSTAB                        */
     int    symmetric;    /* 1 if d_h is elementwise constant (S symmetric, Sec. 2.4.3-2.4.4)   */
-    int    fp64_iterations; /* FESTUNG_MIXED: iterations of the FP64 solve that finished the step
+    int    fp64_iterations; /* mixed modes: iterations of the FP64 solve that finished the step
                                after an FP32 sweep failed to lower the residual (else 0)            */
     double initial_rel_residual; /* ||b - S C0||_2 / ||b||_2 of the initial guess C0               */
 } festung_step_info;
@@ -155,7 +163,8 @@ int festung_get_state(const festung_ctx *ctx, double *C, int loc);
 
 /* y = S x of (E1) with the current D and time step dt (dt = 0 gives y = M x).
  *   x, y  device arrays in the N x K layout, FP64 (prec = FESTUNG_FP64 or
- *         FESTUNG_DFLOAT) or FP32 (prec = FESTUNG_FP32); x and y must not overlap;
+ *         FESTUNG_DFLOAT) or FP32 (prec = FESTUNG_FP32 or FESTUNG_BF16TAB); x and y
+ *         must not overlap;
  *         16-byte aligned.
  * FESTUNG_DFLOAT evaluates the operator in double-float arithmetic (the residual of
  * FESTUNG_MIXED steps): x is split into pairs of FP32 values, the result is rounded
@@ -186,9 +195,15 @@ int festung_apply_noalloc(festung_ctx *ctx, const void *x, void *y, int prec, do
  * C, D, f and boundary data, solves (E1) and, only on success, replaces C by C^{n+1}.
  * The initial guess extrapolates the previous states in time: quadratically through
  * C^{n-2}, C^{n-1}, C^n after two successful steps, linearly after one, else C^n;
- * festung_set_state and festung_setup reset this history.  Preconditioner: inverse N x N diagonal blocks of S.  opts may be NULL (tol 1e-10, max_iter 20000,
- * FESTUNG_MIXED, inner_tol 1e-2, max_outer 50).  info may be NULL.  Synchronises
- * the context's stream.  Errors: ENOCONV (C unchanged), EINVAL, ESTATE, ECUDA. */
+ * festung_set_state and festung_setup reset this history.  Preconditioner: inverse N x N
+ * diagonal blocks of S.  opts may be NULL (tol 1e-10, max_iter 20000, FESTUNG_MIXED,
+ * inner_tol 1e-2, max_outer 50).  opts->prec: FESTUNG_FP64 (FP64 Krylov), FESTUNG_MIXED
+ * (FP32 inner Krylov sweeps, refinement residual in double-float), FESTUNG_MIXED64 (the
+ * same with the refinement residual in FP64), FESTUNG_BF16TAB (FP32 inner Krylov on the
+ * BF16-table operator, FP64 residual).  Every mode meets tol on its own residual
+ * and falls back to FP64 Krylov sweeps when the inner sweeps stop lowering it.  info may
+ * be NULL.  Synchronises the context's stream.  Errors: ENOCONV (C unchanged), EINVAL,
+ * ESTATE, ECUDA. */
 int festung_step(festung_ctx *ctx, double dt, const festung_step_opts *opts,
                  festung_step_info *info);
 

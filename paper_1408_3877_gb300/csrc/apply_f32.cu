@@ -12,6 +12,10 @@ void launch_apply<float>(const festung_ctx *c, const float *x, float *y, float *
                           const int *skip, cudaStream_t st) {
     (void)Z1;
     (void)Z2;
+    if (c->tab_bf16) {
+        launch_apply_bf16tab(c, x, y, tau, skip, st);
+        return;
+    }
     const int tiles = (int)((c->K + c->TE - 1) / c->TE);
     c->launches += 1;
     dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {

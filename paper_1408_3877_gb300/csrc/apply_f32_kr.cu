@@ -10,6 +10,10 @@ template <>
 void launch_apply_bicg<float>(const festung_ctx *c, const float *x, float *y, float tau, int epi, const float *e1,
                               const float *e2, double *part, KScal *sc, unsigned int *counter, const int *skip,
                               cudaStream_t st, const BatchView &bv) {
+    if (c->tab_bf16) {
+        launch_apply_bicg_bf16tab(c, x, y, tau, epi, e1, e2, part, sc, counter, skip, st, bv);
+        return;
+    }
     const int tiles = (int)((c->K + c->TE - 1) / c->TE);
     c->launches += 1;
     dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {

@@ -7,8 +7,10 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
+#include <stdexcept>
 #include <string>
 #include <thread>
 #include <type_traits>
@@ -50,7 +52,7 @@ struct Vecs {
 
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
-    int solver = 0, chunk = 0, use_P = -1;
+    int solver = 0, chunk = 0, use_P = -1, tab_bf16 = 0;
     int64_t nodes = 0;
     double tau = 0.0, mass = 1.0;
     const void *x = nullptr, *b = nullptr;
@@ -497,12 +499,14 @@ void free_ctx_device(festung_ctx *c) {
         delete c->ws;
         c->ws = nullptr;
     }
-    void *ptrs[] = {c->dTab, c->fTab, c->dC, c->dD, c->dF, c->fD, c->dCD, c->dGN, c->dSamp, c->dCprev, c->dCprev2,
+    void *ptrs[] = {c->dTab, c->fTab, c->bTab, c->dC, c->dD, c->dF, c->fD, c->dCD, c->dGN, c->dSamp, c->dCprev, c->dCprev2,
                     c->xD, c->xB, c->xTab, c->dGuess};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     c->dTab = nullptr;
     c->fTab = nullptr;
+    c->bTab = nullptr;
+    c->tab_bf16 = false;
     c->xD = c->xB = c->xTab = nullptr;
     c->xD_valid = false;
     c->dGuess = nullptr;
@@ -704,7 +708,8 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
         FCK(cudaGetLastError());
         // capture (or reuse) a graph of CHUNK iterations
         GraphCache &gc = graph_of<T>(c);
-        if (!gc.exec || gc.solver != solver || gc.tau != tau || gc.use_P != (int)w.use_P || gc.mass != c->mass) {
+        if (!gc.exec || gc.solver != solver || gc.tau != tau || gc.use_P != (int)w.use_P || gc.mass != c->mass ||
+            gc.tab_bf16 != (int)c->tab_bf16) {
             if (gc.exec) cudaGraphExecDestroy(gc.exec);
             gc.exec = nullptr;
             cudaStream_t cs;
@@ -725,6 +730,7 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
             gc.tau = tau;
             gc.use_P = (int)w.use_P;
             gc.mass = c->mass;
+            gc.tab_bf16 = (int)c->tab_bf16;
         }
         bool brk = false, drift = false;
         while (true) {
@@ -1041,7 +1047,12 @@ int festung_setup(festung_ctx *c, int p, int quad_order, double eta) {
         return FESTUNG_EINVAL;
     }
     HostTables T;
-    build_tables(p, qT, T);
+    try {
+        build_tables(p, qT, T);
+    } catch (const std::exception &ex) {
+        c->err = std::string("reference tables: ") + ex.what();
+        return FESTUNG_EINVAL;
+    }
     if (!dispatch(T.N, T.R2, T.R1, [](auto, auto, auto) {})) {
         c->err = "unsupported quadrature combination";
         return FESTUNG_EINVAL;
@@ -1066,15 +1077,20 @@ int festung_setup(festung_ctx *c, int p, int quad_order, double eta) {
     std::copy(T.phiE.begin(), T.phiE.end(), h.begin() + o.phiE);
     std::copy(T.wphiE.begin(), T.wphiE.end(), h.begin() + o.wphiE);
     std::vector<float> hf(h.begin(), h.end());
+    std::vector<float> hb(h.size());
+    for (size_t i = 0; i < h.size(); ++i) hb[i] = round_to_bf16(h[i]);
     const int64_t K = c->K, N = c->N;
     FCK(cudaMalloc(&c->dTab, o.total * sizeof(double)));
     FCK(cudaMalloc(&c->fTab, o.total * sizeof(float)));
     FCK(cudaMemcpy(c->dTab, h.data(), o.total * sizeof(double), cudaMemcpyHostToDevice));
     FCK(cudaMemcpy(c->fTab, hf.data(), o.total * sizeof(float), cudaMemcpyHostToDevice));
+    FCK(cudaMalloc(&c->bTab, o.total * sizeof(float)));
+    FCK(cudaMemcpy(c->bTab, hb.data(), o.total * sizeof(float), cudaMemcpyHostToDevice));
     FCK(upload_tables_f64(c));
     FCK(upload_tables_f32(c));
     FCK(upload_tables_f32_kr(c));
     FCK(upload_tables_df(c));
+    FCK(upload_tables_bf16(c));
     {
         // double-float copies of the tables and the geometry (residual applies)
         std::vector<dfloat> hx(o.total);
@@ -1276,7 +1292,7 @@ int festung_get_state(const festung_ctx *cc, double *C, int loc) {
 int festung_apply(festung_ctx *c, const void *x, void *y, int prec, double dt) {
     if (!ready(c)) return c ? FESTUNG_ESTATE : FESTUNG_EINVAL;
     if (!x || !y || x == y || !(dt >= 0.0) ||
-        (prec != FESTUNG_FP64 && prec != FESTUNG_FP32 && prec != FESTUNG_DFLOAT)) {
+        (prec != FESTUNG_FP64 && prec != FESTUNG_FP32 && prec != FESTUNG_DFLOAT && prec != FESTUNG_BF16TAB)) {
         c->err = "bad apply arguments";
         return FESTUNG_EINVAL;
     }
@@ -1289,8 +1305,10 @@ int festung_apply(festung_ctx *c, const void *x, void *y, int prec, double dt) {
         launch_apply<double>(c, (const double *)x, (double *)y, c->ws->d.Z1, c->ws->d.Z2, dt, nullptr, c->stream);
     } else {
         if ((rc = alloc_vecs<float>(c, c->ws->f, false))) return rc;
+        c->tab_bf16 = prec == FESTUNG_BF16TAB;
         launch_apply<float>(c, (const float *)x, (float *)y, c->ws->f.Z1, c->ws->f.Z2, (float)dt, nullptr,
                             c->stream);
+        c->tab_bf16 = false;
     }
     FCK(cudaGetLastError());
     return FESTUNG_OK;
@@ -1311,7 +1329,9 @@ bool step_options(const festung_step_opts *opts, festung_step_opts &o) {
     o.max_outer = 50;
     o.solver = 0;
     if (opts) o = *opts;
-    return o.tol > 0.0 && o.max_iter >= 1 && (o.prec == FESTUNG_FP64 || o.prec == FESTUNG_MIXED) &&
+    return o.tol > 0.0 && o.max_iter >= 1 &&
+           (o.prec == FESTUNG_FP64 || o.prec == FESTUNG_MIXED || o.prec == FESTUNG_MIXED64 ||
+            o.prec == FESTUNG_BF16TAB) &&
            o.max_outer >= 1 && o.inner_tol > 0.0 && o.inner_tol < 1.0 &&
            (o.solver == 0 || o.solver == FESTUNG_SOLVER_CG || o.solver == FESTUNG_SOLVER_BICGSTAB);
 }
@@ -1417,7 +1437,10 @@ int commit_solution(festung_ctx *c, double dt, bool stationary) {
 int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts *opts, festung_step_info *info) {
     struct MassGuard {
         festung_ctx *c;
-        ~MassGuard() { c->mass = 1.0; }
+        ~MassGuard() {
+            c->mass = 1.0;
+            c->tab_bf16 = false;
+        }
     } guard{c};
     c->mass = mass;
     const bool stationary = mass == 0.0;
@@ -1426,7 +1449,7 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
         c->err = "bad step arguments";
         return FESTUNG_EINVAL;
     }
-    int rc = prepare_solve(c, dt, stationary, o.prec == FESTUNG_MIXED);
+    int rc = prepare_solve(c, dt, stationary, o.prec != FESTUNG_FP64);
     if (rc) return rc;
     Workspace &w = *c->ws;
     const int solver = o.solver ? o.solver : (c->symmetric ? FESTUNG_SOLVER_CG : FESTUNG_SOLVER_BICGSTAB);
@@ -1439,7 +1462,8 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
     bool conv = false;
     double relres = 0.0, relres0 = -1.0;
     // residual r = b - S x (FP64 vectors) and its norms (rn, bn)
-    // (FESTUNG_MIXED: S x in double-float arithmetic, about 48 significant bits)
+    // (FESTUNG_MIXED: S x in double-float arithmetic, about 48 significant bits; the other
+    // modes: S x in FP64)
     const bool df_residual = o.prec == FESTUNG_MIXED;
     auto residual64 = [&](double *rn, double *bn) -> int {
         if (df_residual) {
@@ -1500,8 +1524,10 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
             // the FP32 sweep reduces by inner_tol, or by less when less is still needed;
             // after a failure the next sweep starts from a reweighted shadow residual
             const double target = std::min(0.5, std::max(o.inner_tol, 0.5 * o.tol / relres));
+            c->tab_bf16 = o.prec == FESTUNG_BF16TAB;
             rc = krylov_solve<float>(c, solver, dt, target, o.max_iter - iters, true, &it, &ir2, &ib2, &cin,
                                      failures > 0);
+            c->tab_bf16 = false;
             if (rc) return rc;
             iters += it;
             if (!(ir2 < ib2)) {
@@ -1530,7 +1556,7 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
             if (relres0 < 0.0) relres0 = rr0;
             if (rc) return rc;
             iters += it;
-            if (o.prec == FESTUNG_MIXED) iters64 += it;
+            if (o.prec != FESTUNG_FP64) iters64 += it;
             double rn, bn;
             if ((rc = residual64(&rn, &bn))) return rc;
             relres = bn > 0 ? rn / bn : rn;
@@ -1549,7 +1575,9 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
         info->initial_rel_residual = relres0;
     }
     if (!conv) {
-        c->err = "Krylov solve did not converge (relative residual " + std::to_string(relres) + ")";
+        char msg[96];
+        std::snprintf(msg, sizeof(msg), "Krylov solve did not converge (relative residual %.3e)", relres);
+        c->err = msg;
         return FESTUNG_ENOCONV;
     }
     return commit_solution(c, dt, stationary);

@@ -44,6 +44,8 @@ struct HostTables {
     std::vector<double> wphiE;  // [3][R1][N] w_r phi_i(gamma_n(s_r))
 };
 void build_tables(int p, int qT, HostTables &T);
+// v rounded to the nearest BF16 value (8-bit significand, ties to even), as a float.
+float round_to_bf16(double v);
 
 // Mesh build (host): validates and produces SoA geometry and neighbour codes.
 // nbr code of local edge (k, n): interior (k+ << 2) | n+, Dirichlet -1, Neumann -2.
@@ -124,6 +126,8 @@ struct festung_ctx {
     festung::HostTables tab;
     double *dTab = nullptr;  // FP64 tables, layout table_offsets
     float *fTab = nullptr;   // FP32 copy
+    float *bTab = nullptr;   // BF16-rounded values (FESTUNG_BF16TAB), FP32 storage
+    bool tab_bf16 = false;   // FP32 applies use the BF16-rounded tables (set during such solves)
     // state and data (N x K unless noted)
     double *dC = nullptr, *dD = nullptr, *dF = nullptr;
     double *dCprev = nullptr, *dCprev2 = nullptr;  // C^{n-1}, C^{n-2} for the extrapolated initial guess

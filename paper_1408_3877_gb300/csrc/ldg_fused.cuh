@@ -3,13 +3,19 @@
 // Triangles are stored in Morton order of their centroids, so TE consecutive
 // triangles form a compact patch ("tile").  One thread block handles one tile and its
 // halo (the interior neighbours outside the tile), one triangle ("slot") per thread:
-//   A1  traces of x and d_h on the three edges of every slot -> shared memory;
+//   A1  traces of x on the three edges of every slot -> shared memory;
 //   A2  flux unknowns Z^m = -M^{-1} B_m x (block rows 1-2 of eq. timeDepSystem) from
-//       the slot's own and its neighbours' x traces, and their traces -> shared memory;
+//       the slot's own and its neighbours' x traces, held in contravariant form
+//       zeta = det(B) B^{-1} Z, and the normal fluxes sigma = d_h zeta . nu^ on the
+//       three edges -> shared memory;
 //   B   for every tile triangle, the volume term -sum_m G^m Z^m and the edge terms
 //       R^m, R_D^m, S, S_D from its own and its neighbours' traces.
+// In contravariant form the volume and edge quadratures are those of the reference
+// triangle: the geometry enters once per slot, through the metric B^T B / det B.
 // The flux unknowns never leave the chip, and every trace is evaluated once per slot.
 #pragma once
+
+#include <vector>
 
 #include "dfloat.cuh"
 #include "dispatch.h"
@@ -43,9 +49,10 @@ __constant__ CTab<T, N, R2, R1> c_tab;
 
 // Copy the reference tables of the context's (N, R2, R1) into this translation unit's
 // constant bank, once per device.  The tables depend only on p and the quadrature, so
-// every context of the same shape writes identical values.
+// every context of the same shape writes identical values.  bf16: round every entry to
+// BF16 first (a unit that uses this holds only BF16-valued tables).
 template <typename T>
-cudaError_t upload_ctab(const festung_ctx *c) {
+cudaError_t upload_ctab(const festung_ctx *c, bool bf16 = false) {
     cudaError_t err = cudaSuccess;
     int dev = 0;
     if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
@@ -55,7 +62,14 @@ cudaError_t upload_ctab(const festung_ctx *c) {
         const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
         if (done & bit) return;
         CTab<T, N, R2, R1> h;
-        const HostTables &t = c->tab;
+        const HostTables &t0 = c->tab;
+        HostTables tb;
+        if (bf16) {
+            tb = t0;
+            for (std::vector<double> *v : {&tb.phiQ, &tb.gw1, &tb.gw2, &tb.H1, &tb.H2, &tb.phiE, &tb.wphiE})
+                for (double &e : *v) e = round_to_bf16(e);
+        }
+        const HostTables &t = bf16 ? tb : t0;
         for (int i = 0; i < R2 * N; ++i) {
             h.phiQ[i] = (T)t.phiQ[i];
             h.gw1[i] = (T)t.gw1[i];
@@ -89,7 +103,7 @@ __device__ __forceinline__ void ctrace(const T (&c)[N], T (&out)[R1]) {
     }
 }
 
-// Shared-memory traces of field f (0: x, 1: d_h, 2: z^1, 3: z^2) on edge n of slot s.
+// Shared-memory traces of field f (0: x, 1: sigma) on edge n of slot s.
 // When padding the R1 Gauss points to 16 bytes costs little, a trace is one padded
 // vector moved with 128-bit accesses; otherwise (R1 = 5 in FP32) the points are stored
 // one array per point, which keeps the shared memory of a block small enough for two
@@ -138,72 +152,63 @@ __device__ __forceinline__ void tr_load(const T *tr, int f, int n, int slot, int
     }
 }
 
-// Phase A1 for triangle e at shared-memory slot `slot`: loads x and d_h of e and stores
-// their traces on the three edges.
 // Double-float arithmetic is 10-20 instructions per multiply-add: fully unrolled, its
-// trace loops alone would not fit the instruction cache.  Its traces are therefore
-// computed with the point loop rolled and stored point by point.
+// point loops would not fit the instruction cache.  For that type the loops over
+// quadrature points stay rolled and traces are moved point by point.
 template <typename T>
 constexpr bool kCompactCode = std::is_same<T, dfloat>::value;
 
-// trace of c on own edge n into field f of the slot's shared-memory traces (compact code)
+// The basis is hierarchical: functions 0 | 1-2 | 3-5 | 6-9 | 10-14 have degrees 0..4.
+// d phi_i / dx^_m has degree deg(i) - 1, so it is orthogonal to every phi_j of degree
+// >= deg(i): H^_m[i][j] = int d_m phi_i phi_j vanishes unless j < nbelow(i)
+// (build_tables checks this and stores exact zeros there).
+__host__ __device__ constexpr int basis_degree(int i) { return i < 1 ? 0 : i < 3 ? 1 : i < 6 ? 2 : i < 10 ? 3 : 4; }
+__host__ __device__ constexpr int nbelow(int i) { return basis_degree(i) * (basis_degree(i) + 1) / 2; }
+
+// point r of the trace of field f on edge n of slot s in shared memory (either layout)
+template <typename T, int R1>
+__device__ __forceinline__ T &tr_at(T *tr, int f, int n, int slot, int NS, int r) {
+    using L = TraceLayout<T, R1>;
+    if constexpr (L::vec)
+        return tr[((size_t)(f * 3 + n) * NS + slot) * L::RP + r];
+    else
+        return tr[((size_t)(f * 3 + n) * R1 + r) * NS + slot];
+}
+
+// trace of c on own edge n into field f of the slot's shared-memory traces
 template <typename T, int N, int R2, int R1, int n>
-__device__ __forceinline__ void trace_store(const T (&c)[N], T *tr, int f, int NS, int slot) {
-    {
-        using L = TraceLayout<T, R1>;
+__device__ __forceinline__ void store_trace(const T (&c)[N], T *tr, int f, int NS, int slot) {
+    if constexpr (kCompactCode<T>) {
         const CTab<T, N, R2, R1> &t = c_tab<T, N, R2, R1>;
 #pragma unroll 1
         for (int r = 0; r < R1; ++r) {
             T v = T(0);
 #pragma unroll
             for (int j = 0; j < N; ++j) v += t.phiE[(n * R1 + r) * N + j] * c[j];
-            if constexpr (L::vec)
-                tr[((size_t)(f * 3 + n) * NS + slot) * L::RP + r] = v;
-            else
-                tr[((size_t)(f * 3 + n) * R1 + r) * NS + slot] = v;
+            tr_at<T, R1>(tr, f, n, slot, NS, r) = v;
         }
-    }
-}
-
-template <typename T, int N, int R2, int R1, int n>
-__device__ __forceinline__ void a1_edge(const T (&x)[N], const T (&d)[N], T *tr, int NS, int slot) {
-    if constexpr (kCompactCode<T>) {
-        trace_store<T, N, R2, R1, n>(x, tr, 0, NS, slot);
-        trace_store<T, N, R2, R1, n>(d, tr, 1, NS, slot);
     } else {
-        T xt[R1], dt[R1];
-        ctrace<T, N, R2, R1, n>(x, xt);
-        ctrace<T, N, R2, R1, n>(d, dt);
-        tr_store<T, R1>(tr, 0, n, slot, NS, xt);
-        tr_store<T, R1>(tr, 1, n, slot, NS, dt);
+        T v[R1];
+        ctrace<T, N, R2, R1, n>(c, v);
+        tr_store<T, R1>(tr, f, n, slot, NS, v);
     }
 }
 
+// Phase A1: traces of x on the three edges of a slot (field 0).
 template <typename T, int N, int R2, int R1>
-__device__ __forceinline__ void slot_a1(const T *__restrict__ X, const T *__restrict__ Dc, int Ki, int e, T *tr,
-                                        int NS, int slot, T (&d)[N]) {
-    T x[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-        x[j] = X[j * Ki + e];
-        d[j] = Dc[j * Ki + e];
-    }
-    a1_edge<T, N, R2, R1, 0>(x, d, tr, NS, slot);
-    a1_edge<T, N, R2, R1, 1>(x, d, tr, NS, slot);
-    a1_edge<T, N, R2, R1, 2>(x, d, tr, NS, slot);
+__device__ __forceinline__ void slot_xtraces(const T (&x)[N], T *tr, int NS, int slot) {
+    store_trace<T, N, R2, R1, 0>(x, tr, 0, NS, slot);
+    store_trace<T, N, R2, R1, 1>(x, tr, 0, NS, slot);
+    store_trace<T, N, R2, R1, 2>(x, tr, 0, NS, slot);
 }
 
-// Phase A2, edge n: the edge's contribution nu_en |E_en| int phi_i {c} to B_m x (central
-// flux, eq. globQ; interior value on Neumann edges, eq. globQm:N; nothing on Dirichlet
-// edges).  The neighbour's trace comes from its slot, or from global memory when the
-// neighbour of a halo triangle lies outside the tile's slots (nsl == -2).
+// Central value {x} of the edge at our Gauss point r: the mean of our trace and the
+// neighbour's, taken at its point R1 - 1 - r (the maps of eq. mapEE reverse the edge);
+// our own trace on a Neumann edge (eq. globQm:N).  The neighbour's trace comes from its
+// slot, or from global memory when the neighbour of a halo triangle has no slot (nsl = -2).
 template <typename T, int N, int R2, int R1, int n>
-__device__ __forceinline__ void a2_edge(const T *phiE_s, const T *__restrict__ X, int Ki, int code, int nsl,
-                                        const T *tr, int NS, int slot, T b11, T b12, T b21, T b22, T (&a1)[N],
-                                        T (&a2)[N]) {
-    if (code == NBR_DIRICHLET) return;  // c_D enters the right-hand side only
-    const CTab<T, N, R2, R1> &t = c_tab<T, N, R2, R1>;
-    T f[R1];
+__device__ __forceinline__ void edge_mean(const T *phiE_s, const T *__restrict__ X, int Ki, int code, int nsl,
+                                          const T *tr, int NS, int slot, T (&f)[R1]) {
     tr_load<T, R1>(tr, 0, n, slot, NS, f);
     if (code >= 0) {
         T cp[R1];
@@ -211,24 +216,34 @@ __device__ __forceinline__ void a2_edge(const T *phiE_s, const T *__restrict__ X
             T nb[R1];
             tr_load<T, R1>(tr, 0, code & 3, nsl, NS, nb);
 #pragma unroll
-            for (int r = 0; r < R1; ++r) cp[r] = nb[R1 - 1 - r];  // the maps of eq. mapEE reverse the edge
+            for (int r = 0; r < R1; ++r) cp[r] = nb[R1 - 1 - r];
         } else {
             trace_nbr<T, N, R1>(phiE_s, X, (int64_t)Ki, code >> 2, code & 3, cp);
         }
 #pragma unroll
         for (int r = 0; r < R1; ++r) f[r] = T(0.5) * (f[r] + cp[r]);
     }
-    T nx, ny;
-    edge_normal(n, b11, b12, b21, b22, nx, ny);
+}
+
+// e += sgn * sum_r wphi_E[n][r][i] f_r: the edge's part of the reference flux (P or Q).
+template <typename T, int N, int R2, int R1, int n>
+__device__ __forceinline__ void edge_test_add(const T (&f)[R1], T (&a)[N], T (&b)[N], int which) {
+    const CTab<T, N, R2, R1> &t = c_tab<T, N, R2, R1>;
     if constexpr (kCompactCode<T>) {
 #pragma unroll 1
         for (int r = 0; r < R1; ++r) {
-            const T fx = nx * f[r], fy = ny * f[r];
+            const T fr = f[r];
 #pragma unroll
             for (int i = 0; i < N; ++i) {
-                const T w = t.wphiE[(n * R1 + r) * N + i];
-                a1[i] += w * fx;
-                a2[i] += w * fy;
+                const T v = t.wphiE[(n * R1 + r) * N + i] * fr;
+                if (which == 0) {
+                    a[i] -= v;
+                    b[i] -= v;
+                } else if (which == 1) {
+                    a[i] += v;
+                } else {
+                    b[i] += v;
+                }
             }
         }
     } else {
@@ -237,52 +252,79 @@ __device__ __forceinline__ void a2_edge(const T *phiE_s, const T *__restrict__ X
             T v = T(0);
 #pragma unroll
             for (int r = 0; r < R1; ++r) v += t.wphiE[(n * R1 + r) * N + i] * f[r];
-            a1[i] += nx * v;
-            a2[i] += ny * v;
+            if (which == 0) {
+                a[i] -= v;
+                b[i] -= v;
+            } else if (which == 1) {
+                a[i] += v;
+            } else {
+                b[i] += v;
+            }
         }
     }
 }
 
+// sigma_n = d_h (nu^_n . zeta) at the Gauss points of edge n (field 1): the normal flux
+// d_h z . nu |E| of the edge in reference coordinates (nu^_0 = (1, 1), nu^_1 = (-1, 0),
+// nu^_2 = (0, -1)).
 template <typename T, int N, int R2, int R1, int n>
-__device__ __forceinline__ void slot_ztrace(const T (&z1)[N], const T (&z2)[N], T *tr, int NS, int slot) {
+__device__ __forceinline__ void store_sigma(const T (&d)[N], const T (&z1)[N], const T (&z2)[N], T *tr, int NS,
+                                            int slot) {
+    const CTab<T, N, R2, R1> &t = c_tab<T, N, R2, R1>;
+    T w[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) w[j] = n == 0 ? z1[j] + z2[j] : (n == 1 ? -z1[j] : -z2[j]);
     if constexpr (kCompactCode<T>) {
-        trace_store<T, N, R2, R1, n>(z1, tr, 2, NS, slot);
-        trace_store<T, N, R2, R1, n>(z2, tr, 3, NS, slot);
+#pragma unroll 1
+        for (int r = 0; r < R1; ++r) {
+            T dv = T(0), wv = T(0);
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                dv += t.phiE[(n * R1 + r) * N + j] * d[j];
+                wv += t.phiE[(n * R1 + r) * N + j] * w[j];
+            }
+            tr_at<T, R1>(tr, 1, n, slot, NS, r) = dv * wv;
+        }
     } else {
-        T t1[R1], t2[R1];
-        ctrace<T, N, R2, R1, n>(z1, t1);
-        ctrace<T, N, R2, R1, n>(z2, t2);
-        tr_store<T, R1>(tr, 2, n, slot, NS, t1);
-        tr_store<T, R1>(tr, 3, n, slot, NS, t2);
+        T dv[R1], wv[R1];
+        ctrace<T, N, R2, R1, n>(d, dv);
+        ctrace<T, N, R2, R1, n>(w, wv);
+#pragma unroll
+        for (int r = 0; r < R1; ++r) dv[r] *= wv[r];
+        tr_store<T, R1>(tr, 1, n, slot, NS, dv);
     }
 }
 
-// Phase A2 for triangle e at slot `slot`: Z^m = -M^{-1} B_m x, and the traces of z^1,
-// z^2.  nsl[n]: slot of the neighbour across edge n (see a2_edge).
+// Phase A2 for triangle e at slot `slot`: the flux unknowns in contravariant form,
+// zeta = det(B) B^{-1} Z (Z^m = -M^{-1} B_m x, block rows 1-2 of eq. timeDepSystem), and
+// the normal-flux traces sigma of its three edges.
+//
+// With u^_m = H^_m x (Sec. 3.6.2) and e_n = sum_r wphi_E[n][r] {x}(r) the edge terms
+// (eq. globQ, globQm:N; nothing on Dirichlet edges), the edge normals nu_n |E_n| of
+// (Sec. 3.1) and the metric G = B^T B turn Z into
+//   zeta^1 = (G22 P - G12 Q) / det B,  zeta^2 = (G11 Q - G12 P) / det B,
+//   P = u^_1 - e_0 + e_1,  Q = u^_2 - e_0 + e_2,
+// so that B enters through G and det B alone.  nsl[n]: slot of the neighbour across
+// edge n (see edge_mean).
 template <typename T, int N, int R2, int R1>
-__device__ __forceinline__ void slot_a2(const T *phiE_s, const T *__restrict__ X, const T *__restrict__ Bg,
-                                        const int32_t *__restrict__ nbr, int Ki, int e, const int (&nsl)[3],
-                                        T *tr, int NS, int slot, T (&z1)[N], T (&z2)[N]) {
+__device__ __forceinline__ void slot_zeta(const T *phiE_s, const T *__restrict__ X, const T *__restrict__ Bg,
+                                          const int32_t *__restrict__ nbr, int Ki, int e, const int (&nsl)[3],
+                                          const T (&d)[N], T *tr, int NS, int slot, T (&z1)[N], T (&z2)[N]) {
     const CTab<T, N, R2, R1> &t = c_tab<T, N, R2, R1>;
-    const T b11 = Bg[e], b12 = Bg[Ki + e], b21 = Bg[2 * Ki + e], b22 = Bg[3 * Ki + e];
-    // -H^m x with H^1 = B22 H^_1 - B21 H^_2, H^2 = -B12 H^_1 + B11 H^_2 (Sec. 3.6.2)
+    // P = H^_1 x, Q = H^_2 x (only the entries below the diagonal blocks of degree are nonzero)
     if constexpr (kCompactCode<T>) {
-        T h1[N], h2[N];
 #pragma unroll
-        for (int i = 0; i < N; ++i) h1[i] = h2[i] = T(0);
+        for (int i = 0; i < N; ++i) z1[i] = z2[i] = T(0);
 #pragma unroll 1
         for (int j = 0; j < N; ++j) {
             const T xj = X[j * Ki + e];
 #pragma unroll
             for (int i = 0; i < N; ++i) {
-                h1[i] += t.H1[i * N + j] * xj;
-                h2[i] += t.H2[i * N + j] * xj;
+                if (j < nbelow(i)) {
+                    z1[i] += t.H1[i * N + j] * xj;
+                    z2[i] += t.H2[i * N + j] * xj;
+                }
             }
-        }
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-            z1[i] = -(b22 * h1[i] - b21 * h2[i]);
-            z2[i] = -(b11 * h2[i] - b12 * h1[i]);
         }
     } else {
         T x[N];
@@ -292,68 +334,88 @@ __device__ __forceinline__ void slot_a2(const T *phiE_s, const T *__restrict__ X
         for (int i = 0; i < N; ++i) {
             T h1 = T(0), h2 = T(0);
 #pragma unroll
-            for (int j = 0; j < N; ++j) {
+            for (int j = 0; j < nbelow(i); ++j) {
                 h1 += t.H1[i * N + j] * x[j];
                 h2 += t.H2[i * N + j] * x[j];
             }
-            z1[i] = -(b22 * h1 - b21 * h2);
-            z2[i] = -(b11 * h2 - b12 * h1);
+            z1[i] = h1;
+            z2[i] = h2;
         }
     }
     const int c0 = nbr[e], c1 = nbr[Ki + e], c2 = nbr[2 * Ki + e];
-    a2_edge<T, N, R2, R1, 0>(phiE_s, X, Ki, c0, nsl[0], tr, NS, slot, b11, b12, b21, b22, z1, z2);
-    a2_edge<T, N, R2, R1, 1>(phiE_s, X, Ki, c1, nsl[1], tr, NS, slot, b11, b12, b21, b22, z1, z2);
-    a2_edge<T, N, R2, R1, 2>(phiE_s, X, Ki, c2, nsl[2], tr, NS, slot, b11, b12, b21, b22, z1, z2);
-    const T inv = T(-1) / (b11 * b22 - b12 * b21);  // Z = -M^{-1} (B_m x), M = 2|T_e| I
+    {
+        T f[R1];
+        if (c0 != NBR_DIRICHLET) {
+            edge_mean<T, N, R2, R1, 0>(phiE_s, X, Ki, c0, nsl[0], tr, NS, slot, f);
+            edge_test_add<T, N, R2, R1, 0>(f, z1, z2, 0);
+        }
+        if (c1 != NBR_DIRICHLET) {
+            edge_mean<T, N, R2, R1, 1>(phiE_s, X, Ki, c1, nsl[1], tr, NS, slot, f);
+            edge_test_add<T, N, R2, R1, 1>(f, z1, z2, 1);
+        }
+        if (c2 != NBR_DIRICHLET) {
+            edge_mean<T, N, R2, R1, 2>(phiE_s, X, Ki, c2, nsl[2], tr, NS, slot, f);
+            edge_test_add<T, N, R2, R1, 2>(f, z1, z2, 2);
+        }
+    }
+    const T b11 = Bg[e], b12 = Bg[Ki + e], b21 = Bg[2 * Ki + e], b22 = Bg[3 * Ki + e];
+    const T inv = T(1) / (b11 * b22 - b12 * b21);
+    const T g11 = (b11 * b11 + b21 * b21) * inv, g12 = (b11 * b12 + b21 * b22) * inv,
+            g22 = (b12 * b12 + b22 * b22) * inv;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        z1[i] *= inv;
-        z2[i] *= inv;
+        const T P = z1[i], Q = z2[i];
+        z1[i] = g22 * P - g12 * Q;
+        z2[i] = g11 * Q - g12 * P;
     }
-    slot_ztrace<T, N, R2, R1, 0>(z1, z2, tr, NS, slot);
-    slot_ztrace<T, N, R2, R1, 1>(z1, z2, tr, NS, slot);
-    slot_ztrace<T, N, R2, R1, 2>(z1, z2, tr, NS, slot);
+    store_sigma<T, N, R2, R1, 0>(d, z1, z2, tr, NS, slot);
+    store_sigma<T, N, R2, R1, 1>(d, z1, z2, tr, NS, slot);
+    store_sigma<T, N, R2, R1, 2>(d, z1, z2, tr, NS, slot);
 }
 
 // Phase B, edge n of tile triangle i: R^m, R_D^m (eq. globR, globR:D) and the penalty
-// S, S_D (eq. globS, globS:D) from the traces in shared memory.
+// S, S_D (eq. globS, globS:D) from the traces in shared memory.  On an interior edge
+// the neighbour's outward normal is the opposite of ours, so the central flux
+// 1/2 nu . (d^- z^- + d^+ z^+) |E| is (sigma^- - sigma^+) / 2.
 template <typename T, int N, int R2, int R1, int n>
-__device__ __forceinline__ void tile_edge(int code, int sl, const T *tr, int NS, int i, T b11, T b12, T b21, T b22,
-                                          T eta, T (&acc)[N]) {
+__device__ __forceinline__ void tile_edge(int code, int sl, const T *tr, int NS, int i, T eta, T (&acc)[N]) {
     if (code == NBR_NEUMANN) return;
     const CTab<T, N, R2, R1> &t = c_tab<T, N, R2, R1>;
-    T nx, ny;
-    edge_normal(n, b11, b12, b21, b22, nx, ny);
-    T g[R1], xm[R1], dm[R1], am[R1], bm[R1];
-    tr_load<T, R1>(tr, 0, n, i, NS, xm);
-    tr_load<T, R1>(tr, 1, n, i, NS, dm);
-    tr_load<T, R1>(tr, 2, n, i, NS, am);
-    tr_load<T, R1>(tr, 3, n, i, NS, bm);
-    if (code >= 0) {
-        const int n2 = code & 3;
-        T xp[R1], dp[R1], ap[R1], bp[R1];
-        tr_load<T, R1>(tr, 0, n2, sl, NS, xp);
-        tr_load<T, R1>(tr, 1, n2, sl, NS, dp);
-        tr_load<T, R1>(tr, 2, n2, sl, NS, ap);
-        tr_load<T, R1>(tr, 3, n2, sl, NS, bp);
-#pragma unroll
-        for (int r = 0; r < R1; ++r) {
-            const int rp = R1 - 1 - r;  // the neighbour's Gauss point at our point r (eq. mapEE)
-            g[r] = T(0.5) * (nx * (dm[r] * am[r] + dp[rp] * ap[rp]) + ny * (dm[r] * bm[r] + dp[rp] * bp[rp])) +
-                   eta * (xm[r] - xp[rp]);
-        }
-    } else {  // Dirichlet
-#pragma unroll
-        for (int r = 0; r < R1; ++r) g[r] = dm[r] * (nx * am[r] + ny * bm[r]) + eta * xm[r];
-    }
     if constexpr (kCompactCode<T>) {
 #pragma unroll 1
         for (int r = 0; r < R1; ++r) {
-            const T gr = g[r];
+            const T xm = tr_at<T, R1>(const_cast<T *>(tr), 0, n, i, NS, r);
+            const T sm = tr_at<T, R1>(const_cast<T *>(tr), 1, n, i, NS, r);
+            T g;
+            if (code >= 0) {
+                const int n2 = code & 3, rp = R1 - 1 - r;
+                const T xp = tr_at<T, R1>(const_cast<T *>(tr), 0, n2, sl, NS, rp);
+                const T sp = tr_at<T, R1>(const_cast<T *>(tr), 1, n2, sl, NS, rp);
+                g = T(0.5) * (sm - sp) + eta * (xm - xp);
+            } else {
+                g = sm + eta * xm;
+            }
 #pragma unroll
-            for (int j = 0; j < N; ++j) acc[j] += t.wphiE[(n * R1 + r) * N + j] * gr;
+            for (int j = 0; j < N; ++j) acc[j] += t.wphiE[(n * R1 + r) * N + j] * g;
         }
     } else {
+        T g[R1], xm[R1], sm[R1];
+        tr_load<T, R1>(tr, 0, n, i, NS, xm);
+        tr_load<T, R1>(tr, 1, n, i, NS, sm);
+        if (code >= 0) {
+            const int n2 = code & 3;
+            T xp[R1], sp[R1];
+            tr_load<T, R1>(tr, 0, n2, sl, NS, xp);
+            tr_load<T, R1>(tr, 1, n2, sl, NS, sp);
+#pragma unroll
+            for (int r = 0; r < R1; ++r) {
+                const int rp = R1 - 1 - r;  // the neighbour's Gauss point at our point r (eq. mapEE)
+                g[r] = T(0.5) * (sm[r] - sp[rp]) + eta * (xm[r] - xp[rp]);
+            }
+        } else {  // Dirichlet
+#pragma unroll
+            for (int r = 0; r < R1; ++r) g[r] = sm[r] + eta * xm[r];
+        }
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             T v = T(0);
@@ -377,10 +439,12 @@ struct FusedOcc {
     static constexpr int min_blocks = (sizeof(T) == 4 && N >= 10) ? 2 : 0;
 };
 
-// volume term -sum_m G^m Z^m at the triangle points (Sec. 3.6.3), tables in the constant bank
+// Volume term -sum_m G^m Z^m at the triangle points (Sec. 3.6.3).  In contravariant
+// form the integrand grad phi_i . d_h z is (grad^ phi_i . d_h zeta) / det B and the
+// quadrature weight carries det B, so no geometry enters: -sum_r d_h (w_r d_1 phi_i
+// zeta^1 + w_r d_2 phi_i zeta^2) at q_r.  Tables in the constant bank.
 template <typename T, int N, int R2, int R1>
-__device__ __forceinline__ void volume_const(const T (&d)[N], const T (&z1)[N], const T (&z2)[N], T b11, T b12,
-                                             T b21, T b22, T (&acc)[N]) {
+__device__ __forceinline__ void volume_const(const T (&d)[N], const T (&z1)[N], const T (&z2)[N], T (&acc)[N]) {
     const CTab<T, N, R2, R1> &t = c_tab<T, N, R2, R1>;
 #pragma unroll
     for (int r = 0; r < R2; ++r) {
@@ -392,10 +456,11 @@ __device__ __forceinline__ void volume_const(const T (&d)[N], const T (&z1)[N], 
             w1 += ph * z1[j];
             w2 += ph * z2[j];
         }
-        const T u = dv * (b22 * w1 - b12 * w2);
-        const T v = dv * (b11 * w2 - b21 * w1);
+        const T u = dv * w1;
+        const T v = dv * w2;
+        // d phi_0 / dx^ = 0: the constant function has no volume term
 #pragma unroll
-        for (int j = 0; j < N; ++j) acc[j] -= t.gw1[r * N + j] * u + t.gw2[r * N + j] * v;
+        for (int j = 1; j < N; ++j) acc[j] -= t.gw1[r * N + j] * u + t.gw2[r * N + j] * v;
     }
 }
 
@@ -404,8 +469,7 @@ __device__ __forceinline__ void volume_const(const T (&d)[N], const T (&z1)[N], 
 // high orders small
 template <typename T, int N, int R2, int NP>
 __device__ __forceinline__ void volume_smem(const T *phiQ_s, const T *gw1_s, const T *gw2_s, const T (&d)[N],
-                                            const T (&z1)[N], const T (&z2)[N], T b11, T b12, T b21, T b22,
-                                            T (&acc)[N]) {
+                                            const T (&z1)[N], const T (&z2)[N], T (&acc)[N]) {
 #pragma unroll 1
     for (int r = 0; r < R2; ++r) {
         alignas(16) T ph[NP];
@@ -424,17 +488,18 @@ __device__ __forceinline__ void volume_smem(const T *phiQ_s, const T *gw1_s, con
             w1 += ph[j] * z1[j];
             w2 += ph[j] * z2[j];
         }
-        const T u = dv * (b22 * w1 - b12 * w2);
-        const T v = dv * (b11 * w2 - b21 * w1);
+        const T u = dv * w1;
+        const T v = dv * w2;
 #pragma unroll
-        for (int j = 0; j < N; ++j) acc[j] -= g1[j] * u + g2[j] * v;
+        for (int j = 1; j < N; ++j) acc[j] -= g1[j] * u + g2[j] * v;
     }
 }
 
-// Dynamic shared memory of one block: four traced fields on three edges per slot.
+// Dynamic shared memory of one block: two traced fields (x and sigma) on three edges
+// per slot.
 template <typename T, int R1>
 constexpr size_t fused_smem(int nslot) {
-    return (size_t)4 * 3 * TraceLayout<T, R1>::RP * nslot * sizeof(T);
+    return (size_t)2 * 3 * TraceLayout<T, R1>::RP * nslot * sizeof(T);
 }
 
 // Let a kernel take the device's opt-in maximum of dynamic shared memory (once per
@@ -511,29 +576,44 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
             }
         }
     }
-    // A1: traces of x and d_h of every slot (tile triangles keep d_h in registers)
+    // A1: traces of x of every slot (tile triangles load d_h for the later phases)
     if (i < TE) {
-        if (i < cnt) slot_a1<T, N, R2, R1>(X, Dc, Ki, start + i, tr, NS, i, d);
+        if (i < cnt) {
+            const int k = start + i;
+            T x[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                x[j] = X[j * Ki + k];
+                d[j] = Dc[j * Ki + k];
+            }
+            slot_xtraces<T, N, R2, R1>(x, tr, NS, i);
+        }
     } else {
         for (int j = i - TE; j < nh; j += hstride) {
-            T hd[N];
-            slot_a1<T, N, R2, R1>(X, Dc, Ki, halo[h0 + j], tr, NS, TE + j, hd);
+            const int e = halo[h0 + j];
+            T x[N];
+#pragma unroll
+            for (int l = 0; l < N; ++l) x[l] = X[l * Ki + e];
+            slot_xtraces<T, N, R2, R1>(x, tr, NS, TE + j);
         }
     }
     __syncthreads();
-    // A2: flux unknowns and their traces
+    // A2: flux unknowns (contravariant form) and the normal-flux traces
     if (i < TE) {
         if (i < cnt) {
             const int k = start + i;
             const int nsl[3] = {slotg[k], slotg[Ki + k], slotg[2 * Ki + k]};
-            slot_a2<T, N, R2, R1>(phiE_s, X, Bg, nbr, Ki, k, nsl, tr, NS, i, z1, z2);
+            slot_zeta<T, N, R2, R1>(phiE_s, X, Bg, nbr, Ki, k, nsl, d, tr, NS, i, z1, z2);
         }
     } else {
         for (int j = i - TE; j < nh; j += hstride) {
+            const int e = halo[h0 + j];
             const int q = 3 * (h0 + j);
             const int nsl[3] = {halo_slot[q], halo_slot[q + 1], halo_slot[q + 2]};
-            T hz1[N], hz2[N];
-            slot_a2<T, N, R2, R1>(phiE_s, X, Bg, nbr, Ki, halo[h0 + j], nsl, tr, NS, TE + j, hz1, hz2);
+            T hd[N], hz1[N], hz2[N];
+#pragma unroll
+            for (int l = 0; l < N; ++l) hd[l] = Dc[l * Ki + e];
+            slot_zeta<T, N, R2, R1>(phiE_s, X, Bg, nbr, Ki, e, nsl, hd, tr, NS, TE + j, hz1, hz2);
         }
     }
     __syncthreads();
@@ -545,23 +625,22 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
     if (i < cnt) {
         // B: volume and edge terms of the tile triangles
         const int k = start + i;
-        const T b11 = Bg[k], b12 = Bg[Ki + k], b21 = Bg[2 * Ki + k], b22 = Bg[3 * Ki + k];
         T acc[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) acc[j] = T(0);
         if constexpr (kBigVolume)
-            volume_smem<T, N, R2, NP>(vol_s, vol_s + R2 * NP, vol_s + 2 * R2 * NP, d, z1, z2, b11, b12, b21, b22,
-                                      acc);
+            volume_smem<T, N, R2, NP>(vol_s, vol_s + R2 * NP, vol_s + 2 * R2 * NP, d, z1, z2, acc);
         else
-            volume_const<T, N, R2, R1>(d, z1, z2, b11, b12, b21, b22, acc);
+            volume_const<T, N, R2, R1>(d, z1, z2, acc);
         const int c0 = nbr[k], c1 = nbr[Ki + k], c2 = nbr[2 * Ki + k];
-        tile_edge<T, N, R2, R1, 0>(c0, c0 >= 0 ? slotg[k] : 0, tr, NS, i, b11, b12, b21, b22, eta, acc);
-        tile_edge<T, N, R2, R1, 1>(c1, c1 >= 0 ? slotg[Ki + k] : 0, tr, NS, i, b11, b12, b21, b22, eta, acc);
-        tile_edge<T, N, R2, R1, 2>(c2, c2 >= 0 ? slotg[2 * Ki + k] : 0, tr, NS, i, b11, b12, b21, b22, eta, acc);
-        const T det = b11 * b22 - b12 * b21;
+        tile_edge<T, N, R2, R1, 0>(c0, c0 >= 0 ? slotg[k] : 0, tr, NS, i, eta, acc);
+        tile_edge<T, N, R2, R1, 1>(c1, c1 >= 0 ? slotg[Ki + k] : 0, tr, NS, i, eta, acc);
+        tile_edge<T, N, R2, R1, 2>(c2, c2 >= 0 ? slotg[2 * Ki + k] : 0, tr, NS, i, eta, acc);
+        const T det = Bg[k] * Bg[3 * Ki + k] - Bg[Ki + k] * Bg[2 * Ki + k];
+        const T md = mass * det;
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            const T yj = mass * det * X[j * Ki + k] + tau * acc[j];
+            const T yj = md * X[j * Ki + k] + tau * acc[j];
             Y[j * Ki + k] = yj;
             if constexpr (EPI == FUSED_EPI_ALPHA) {
                 dots[0] += (A)e1[j * Ki + k] * (A)yj;

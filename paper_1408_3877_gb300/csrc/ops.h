@@ -55,12 +55,22 @@ int elem_grid(const festung_ctx *c);
 int fused_resident_blocks(const festung_ctx *c, int nslot);
 size_t fused_smem_bytes(const festung_ctx *c, int nslot, bool fp64);
 
+// The FP32 fused apply with the reference tables rounded to BF16 (FESTUNG_BF16TAB): plain
+// and with the BiCGStab epilogue, as launch_apply / launch_apply_bicg.  The FP32
+// launchers call these while the context's tab_bf16 is set.
+void launch_apply_bf16tab(const festung_ctx *c, const float *x, float *y, float tau, const int *skip,
+                          cudaStream_t st);
+void launch_apply_bicg_bf16tab(const festung_ctx *c, const float *x, float *y, float tau, int epi, const float *e1,
+                               const float *e2, double *part, KScal *sc, unsigned int *counter, const int *skip,
+                               cudaStream_t st, const BatchView &bv);
+
 // Reference tables of the context's (p, quadrature) into the constant bank of the
-// fused apply kernels (FP64 and FP32 copies).
+// fused apply kernels (FP64 and FP32 copies; BF16-rounded for launch_apply_bf16tab).
 cudaError_t upload_tables_f64(const festung_ctx *c);
 cudaError_t upload_tables_f32(const festung_ctx *c);
 cudaError_t upload_tables_f32_kr(const festung_ctx *c);
 cudaError_t upload_tables_df(const festung_ctx *c);
+cudaError_t upload_tables_bf16(const festung_ctx *c);
 
 // Block-Jacobi preconditioner: Pinv <- inverse of the N x N diagonal blocks of S (E1),
 // built in FP32 (scratch P, layout [(i N + j) K + k]) from the FP32 copies of geometry,

@@ -9,6 +9,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
+#include <cstring>
 #include <stdexcept>
 
 namespace festung {
@@ -296,6 +298,17 @@ void build_tables(int p, int qT, HostTables &T) {
             T.H1[i * N + j] = s1;
             T.H2[i * N + j] = s2;
         }
+    // d_m phi_i has degree deg(i) - 1 and the basis is orthonormal and ordered by degree,
+    // so H^[i][j] vanishes for every phi_j of degree >= deg(i); the kernels skip these
+    // entries, so they are checked here and stored as exact zeros
+    auto degree = [](int i) { return i < 1 ? 0 : i < 3 ? 1 : i < 6 ? 2 : i < 10 ? 3 : 4; };
+    for (int i = 0; i < N; ++i)
+        for (int j = degree(i) * (degree(i) + 1) / 2; j < N; ++j) {
+            if (std::abs(T.H1[i * N + j]) > 1e-12 || std::abs(T.H2[i * N + j]) > 1e-12)
+                throw std::runtime_error("H^ is not strictly lower block-triangular by degree");
+            T.H1[i * N + j] = 0.0;
+            T.H2[i * N + j] = 0.0;
+        }
     // edge traces: phi_j(gamma_n(s_r)), gamma_1(s) = (1-s, s), gamma_2 = (0, 1-s), gamma_3 = (s, 0)
     T.phiE.assign(3 * R1 * N, 0.0);
     T.wphiE.assign(3 * R1 * N, 0.0);
@@ -312,6 +325,19 @@ void build_tables(int p, int qT, HostTables &T) {
                 T.wphiE[(n * R1 + r) * N + j] = edg.w[r] * ph[j];
             }
         }
+}
+
+float round_to_bf16(double v) {
+    // keep the top 16 bits of the IEEE single, rounding the low 16 away (ties to even)
+    const float f = (float)v;
+    uint32_t u;
+    std::memcpy(&u, &f, sizeof(u));
+    if ((u & 0x7f800000u) == 0x7f800000u) return f;  // Inf or NaN: unchanged
+    const uint32_t lsb = (u >> 16) & 1u;
+    u = (u + 0x7fffu + lsb) & 0xffff0000u;
+    float r;
+    std::memcpy(&r, &u, sizeof(r));
+    return r;
 }
 
 }  // namespace festung

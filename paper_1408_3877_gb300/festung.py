@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(_HERE, "libfestung.so")
 
 OK, EINVAL, EMESH, ENOMEM, ECUDA, ENOCONV, ESTATE, EDATA = 0, -1, -2, -3, -4, -5, -6, -7
 HOST, DEVICE = 0, 1
-FP64, FP32, MIXED, DFLOAT = 0, 1, 2, 3
+FP64, FP32, MIXED, DFLOAT, BF16TAB, MIXED64 = 0, 1, 2, 3, 4, 5
 SOLVER_CG, SOLVER_BICGSTAB = 1, 2
 BATCH_UNION, BATCH_CONCURRENT = 0, 1
 BDR_INTERIOR, BDR_DIRICHLET, BDR_NEUMANN = 0, 1, 2
@@ -216,7 +216,8 @@ class Solver:
 
     def apply(self, x, y, dt, prec=FP64):
         """y = S x on device tensors of shape (N, K) in the internal triangle order: FP64 tensors for
-        prec FP64 or DFLOAT (double-float evaluation), FP32 tensors for FP32."""
+        prec FP64 or DFLOAT (double-float evaluation), FP32 tensors for FP32 or BF16TAB (tables
+        rounded to BF16)."""
         self._check(self.lib.festung_apply(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                                            prec, dt))
 

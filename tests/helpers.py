@@ -36,6 +36,18 @@ def rounding_bound(S_abs, x, eps):
     return eps * np.linalg.norm(S_abs @ np.abs(x))
 
 
+def factored_scale(L, D, tau, x):
+    """Rounding scale of y = S x evaluated in factors, as the kernels do (Z^m = -M^{-1}
+    B_m x first, then M x + tau (eta S_t x + sum_m A_m Z^m)): the same product with every
+    factor and x replaced by its absolute value.  It bounds the magnitude of every partial
+    sum of the evaluation, which |S| |x| (after the cancellations inside S) does not."""
+    ax = np.abs(np.asarray(x).ravel())
+    A = L.Am(D)
+    minv = abs(L.Minv)
+    flux = sum(abs(A[m]) @ (minv @ (abs(L.Bm[m]) @ ax)) for m in range(2))
+    return abs(L.M) @ ax + tau * (L.eta * (abs(L.St) @ ax) + flux)
+
+
 def to_gpu_layout(x, K, N, dtype, order):
     """Caller-order K x N coefficients -> device layout N x K in the library's internal order."""
     import torch
@@ -52,7 +64,8 @@ def from_gpu_layout(y, order):
 
 
 def patch_oracle_rows(cV, V0T, bdr, p, dfun, x, tau, ks, quad_order=None, eta=1.0):
-    """Rows k of S x (and of |S| |x|) computed by the oracle on the 2-ring patch of each k.
+    """Rows k of S x (and of its factored rounding scale, see factored_scale) computed by
+    the oracle on the 2-ring patch of each k.
 
     y_k depends on x and d in the 2-ring of k only (the flux unknowns of k and of its
     neighbours).  Edges that leave the patch get an arbitrary boundary type; they touch
@@ -96,7 +109,7 @@ def patch_oracle_rows(cV, V0T, bdr, p, dfun, x, tau, ks, quad_order=None, eta=1.
         S = L.operator(D, tau)
         xr = xk[ring].ravel()
         y = (S @ xr).reshape(len(ring), N)
-        sc = (abs(S) @ np.abs(xr)).reshape(len(ring), N)
+        sc = factored_scale(L, D, tau, xr).reshape(len(ring), N)
         out.append(y[loc[k]])
         scale.append(sc[loc[k]])
     return np.array(out), np.array(scale)

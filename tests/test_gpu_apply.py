@@ -1,7 +1,10 @@
 """Parity of the CUDA operator apply y = S x (E1) with the oracle's CSR product.
 
 FP64: |y_gpu - y_oracle| is bounded by a small multiple of the rounding scale
-eps64 |S| |x| (the two sides sum the same quadrature terms in different orders).
+eps64 |S| |x| in 2-norm, and element by element by a small multiple of eps64 times the
+factored scale |M| |x| + tau (eta |S_t| |x| + sum_m |A_m| |M^{-1}| |B_m| |x|) (the two
+sides sum the same quadrature terms in different orders and groupings; the kernels
+evaluate S in factors, the flux unknowns first).
 FP32: the same bound with eps32 (geometry, tables, D and x rounded to FP32).
 Double-float (FESTUNG_DFLOAT): the same bound with 2^-47 (value = hi + lo of two
 FP32 numbers; inputs split with 2^-48 relative error, sums and products with errors
@@ -10,8 +13,8 @@ of a few units of 2^-48 of the operand magnitudes).
 import numpy as np
 import pytest
 
-from helpers import (from_gpu_layout, gpu_solver, mesh, patch_oracle_rows, rounding_bound, samples, smooth_d,
-                     to_gpu_layout)
+from helpers import (factored_scale, from_gpu_layout, gpu_solver, mesh, patch_oracle_rows, rounding_bound, samples,
+                     smooth_d, to_gpu_layout)
 
 pytestmark = pytest.mark.gpu
 
@@ -48,7 +51,7 @@ def _case(n, p, mix, tau, quad_order=None, seed=1, jitter=0.2):
         torch.cuda.synchronize()
         out[prec] = from_gpu_layout(yg, order).ravel()
     s.close()
-    return S, x, y_or, out
+    return S, x, y_or, out, factored_scale(L, D, tau, x)
 
 
 @pytest.mark.parametrize("p", [0, 1, 2, 3, 4])
@@ -56,15 +59,15 @@ def _case(n, p, mix, tau, quad_order=None, seed=1, jitter=0.2):
 def test_apply_matches_oracle(p, mix):
     from paper_1408_3877_gb300 import festung as F
     # n = 13: K = 338 spans two 256-thread blocks with a ragged tail
-    S, x, y, out = _case(13, p, mix, tau=0.01)
+    S, x, y, out, scale = _case(13, p, mix, tau=0.01)
     bound = rounding_bound(abs(S), x, 1.0)
     e64 = np.linalg.norm(out[F.FP64] - y)
     e32 = np.linalg.norm(out[F.FP32] - y)
     assert e64 <= 64 * EPS64 * bound, (e64, bound)
     assert e32 <= 64 * EPS32 * bound, (e32, bound)
     # element by element
-    scale = np.abs(S) @ np.abs(x)
-    assert np.all(np.abs(out[F.FP64] - y) <= 256 * EPS64 * (scale + 1e-300))
+    assert np.all(np.abs(out[F.FP64] - y) <= 256 * EPS64 * (scale + 1e-300)), \
+        np.max(np.abs(out[F.FP64] - y) / (scale + 1e-300))
     assert np.all(np.abs(out[F.DFLOAT] - y) <= 256 * EPSDF * (scale + 1e-300)), \
         np.max(np.abs(out[F.DFLOAT] - y) / (scale + 1e-300))
 
@@ -72,7 +75,7 @@ def test_apply_matches_oracle(p, mix):
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
 def test_apply_quadrature_2p_plus_1(p):
     from paper_1408_3877_gb300 import festung as F
-    S, x, y, out = _case(6, p, "mixed", tau=0.05, quad_order=2 * p + 1)
+    S, x, y, out, _ = _case(6, p, "mixed", tau=0.05, quad_order=2 * p + 1)
     bound = rounding_bound(abs(S), x, 1.0)
     assert np.linalg.norm(out[F.FP64] - y) <= 64 * EPS64 * bound
 
@@ -181,3 +184,34 @@ def test_autotune_changes_only_the_tiling():
     torch.cuda.synchronize()
     assert float((y1 - y0).abs().max()) <= 1e-12 * float(y0.abs().max())
     s.close()
+
+
+@pytest.mark.parametrize("p", [1, 2, 4])
+def test_apply_bf16_tables_within_their_rounding(p):
+    """FESTUNG_BF16TAB: every reference table entry rounded to BF16 (relative error <= 2^-9),
+    FP32 data and sums.  Each term of the factored evaluation is a product of at most three
+    table entries, so the result stays within 4 * 2^-9 of the factored scale; and it must
+    differ from the FP32 operator (the tables really are the rounded ones)."""
+    import torch
+    from oracle.solve import LDG
+    from paper_1408_3877_gb300 import festung as F
+    cV, V0T, bdr = mesh(13, "mixed", seed=1)
+    L = LDG(cV, V0T, bdr, p)
+    s = gpu_solver(cV, V0T, bdr, p)
+    s.set_coeff(samples(s, smooth_d))
+    D = L.project(smooth_d)
+    tau = 0.01
+    y = L.operator(D, tau) @ (x := np.random.default_rng(3).standard_normal(L.K * L.N))
+    scale = factored_scale(L, D, tau, x)
+    order = s.element_order()
+    xg = to_gpu_layout(x, L.K, L.N, torch.float32, order)
+    out = {}
+    for prec in (F.FP32, F.BF16TAB):
+        yg = torch.empty_like(xg)
+        s.apply(xg, yg, tau, prec)
+        torch.cuda.synchronize()
+        out[prec] = from_gpu_layout(yg, order).ravel()
+    s.close()
+    err = np.abs(out[F.BF16TAB] - y)
+    assert np.all(err <= 4 * 2.0 ** -9 * scale + 64 * EPS32 * scale), np.max(err / scale)
+    assert np.max(np.abs(out[F.BF16TAB] - out[F.FP32]) / scale) > 1e-5

@@ -115,3 +115,32 @@ def test_multitile_stationary_matches_oracle():
     s.close()
     # without the mass term cond(S) grows like h^-2 (~1e4-1e5 here): error <= cond(S) tol
     assert err <= 1e-8, (err, info)
+
+
+@pytest.mark.parametrize("p", [1, 2, 4])
+def test_multitile_mixed64_step_matches_oracle(p):
+    """FESTUNG_MIXED64: FP32 inner sweeps with the refinement residual in FP64."""
+    from paper_1408_3877_gb300 import festung as F
+    man = W.Manufactured(W.d_config2)
+    C, info = _gpu_step(p, "mixed", man, TAU, F.MIXED64, 1e-12, inner_tol=1e-2)
+    Co = _oracle(p, "mixed", man, TAU)
+    err = np.linalg.norm(C - Co) / np.linalg.norm(Co)
+    assert err <= 1e-9, (err, info)
+    assert info["rel_residual"] <= 1e-12
+    assert info["outer"] >= 2 and info["fp64_iterations"] == 0, info
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_multitile_bf16_table_step_matches_oracle(p):
+    """FESTUNG_BF16TAB: inner sweeps on the operator with BF16-rounded tables; the FP64
+    refinement still reaches the tolerance on the exact operator, so the result matches
+    the oracle like the other modes (at the cost of more sweeps)."""
+    from paper_1408_3877_gb300 import festung as F
+    man = W.Manufactured(W.d_config2)
+    C, info = _gpu_step(p, "mixed", man, TAU, F.BF16TAB, 1e-12, inner_tol=1e-2)
+    Cm, info_m = _gpu_step(p, "mixed", man, TAU, F.MIXED, 1e-12, inner_tol=1e-2)
+    Co = _oracle(p, "mixed", man, TAU)
+    err = np.linalg.norm(C - Co) / np.linalg.norm(Co)
+    assert err <= 1e-9, (err, info)
+    assert info["rel_residual"] <= 1e-12
+    assert info["outer"] >= info_m["outer"], (info, info_m)  # BF16 tables need at least as many sweeps

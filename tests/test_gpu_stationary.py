@@ -48,14 +48,17 @@ def test_stationary_matches_oracle(p):
 
 
 def test_stationary_rates_on_gpu():
-    """Sec. 3.9 / Tab. 2: errors decrease with order p + 1 (FP64 Krylov, tol 1e-12: without
-    the mass term the stationary operator is too ill-conditioned for FP32 sweeps at p = 4)."""
+    """Sec. 3.9 / Tab. 2: errors decrease with order p + 1 (FP64 Krylov: without the mass
+    term the stationary operator is too ill-conditioned for FP32 sweeps at p = 4).  The
+    algebraic error is at most cond(S) times the tolerance; at p = 4 on 64 x 64 the
+    discretisation error is ~6e-10, so the solve goes to 1e-13 to keep the algebraic part
+    well below it."""
     from paper_1408_3877_gb300 import festung as F
     gold = {int(p): a for p, a in np.loadtxt(os.path.join(GOLDEN, "verification_rates.txt"))}
     for p in (1, 2, 3, 4):
         errs = []
         for n in (8, 16, 32, 64):
-            s, info, _ = _gpu_stationary(n, p, 1e-12, F.FP64)
+            s, info, _ = _gpu_stationary(n, p, 1e-13, F.FP64)
             xy, _ = s.quad_points()
             errs.append(s.l2_error(MAN.c(0, xy[..., 0], xy[..., 1])))
             s.close()
