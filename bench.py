@@ -806,8 +806,8 @@ def run_grf_step(args):
     `grf_steps` implicit steps is run with the plain FP64 solve and with FP32 inner sweeps on
     the FP32 operator and on the BF16-table operator (both refined on FP64 residuals; the
     double-float residual mode beside them), each to 1e-10; every final state is compared
-    with an FP64 trajectory solved to 1e-12 (the FP64 rounding floor of this operator
-    lies near 1e-13).  L2 is flushed before every step (the state
+    with an FP64 trajectory solved to 1e-11 (on this stiff operator, tau/h^2 = 105, the
+    FP64 residual stagnates near 1e-12).  L2 is flushed before every step (the state
     alone is 100 MB)."""
     import torch
     from paper_1408_3877_gb300 import festung as F
@@ -829,25 +829,32 @@ def run_grf_step(args):
 
     def trajectory(prec, tol_):
         s.set_state(C0)
-        secs, its, outer, fb = [], [], [], 0
+        secs, its, outer, fb, failed = [], [], [], 0, []
         clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
         clocks.start()
-        for _ in range(nsteps):
+        for k in range(nsteps):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            info = s.step(dt, tol=tol_, prec=prec, inner_tol=1e-2)
+            try:
+                info = s.step(dt, tol=tol_, prec=prec, inner_tol=1e-2, max_iter=args.grf_max_iter)
+            except F.FestungError as e:  # the state stays C^n; counted
+                failed.append("step %d: %s" % (k, e))
+                torch.cuda.synchronize()
+                continue
             b.record(stream)
             torch.cuda.synchronize()
             secs.append(a.elapsed_time(b) / 1e3)
             its.append(info["iterations"])
             outer.append(info["outer"])
             fb += info["fp64_iterations"]
-        return s.get_state(), {"s_per_step": float(np.mean(secs)), "iterations_per_step": float(np.mean(its)),
-                               "outer_per_step": float(np.mean(outer)), "fp64_fallback_iterations": fb,
+        return s.get_state(), {"s_per_step": float(np.mean(secs)) if secs else None,
+                               "iterations_per_step": float(np.mean(its)) if its else None,
+                               "outer_per_step": float(np.mean(outer)) if outer else None,
+                               "fp64_fallback_iterations": fb, "steps_not_converged": failed,
                                "clocks": clocks.stop()}
 
-    C_ref, ref = trajectory(F.FP64, 1e-12)
+    C_ref, ref = trajectory(F.FP64, 1e-11)
     out = {}
     for name, prec in (("fp64", F.FP64), ("fp32_fp64_residual", F.MIXED64),
                        ("bf16_tables_fp64_residual", F.BF16TAB), ("fp32_dfloat_residual", F.MIXED)):
@@ -855,13 +862,14 @@ def run_grf_step(args):
         r["err_vs_fp64_reference"] = float(np.linalg.norm(C - C_ref) / np.linalg.norm(C_ref))
         out[name] = r
     s.close()
-    best = min(out.values(), key=lambda r: r["s_per_step"])
+    best = min((r for r in out.values() if r["s_per_step"] and not r["steps_not_converged"]),
+               key=lambda r: r["s_per_step"], default={"s_per_step": None})
     return {"metric": "sec per implicit step at 1e-10 rel. residual, precision sweep", "value": best["s_per_step"],
             "unit": "s/step", "n_gpus": 1, "steps": nsteps, "higher_is_better": False,
             "dtype": "f64 / f32 / bf16-tables+f32, f64 refinement", "data": "synthetic (seeded field and state)",
             "config": {"workload": "grf1024_p2", "triangles": K, "p": c["p"], "dofs": K * N, "dt": dt, "tol": tol,
                        "l2": "flushed before every step"},
-            "modes": out, "fp64_reference_1e-12": ref,
+            "modes": out, "fp64_reference_1e-11": ref,
             "note": "value = the fastest mode; each mode runs the same %d steps from C^0" % nsteps}
 
 
@@ -883,6 +891,7 @@ def main():
     ap.add_argument("--weighted-loss", type=int, default=0,
                     help="learned: weight the loss by sqrt(diag S / 2|T|) (1) or not (0)")
     ap.add_argument("--grf-steps", type=int, default=50, help="grf1024_p2: implicit steps per mode")
+    ap.add_argument("--grf-max-iter", type=int, default=100000, help="grf1024_p2: Krylov iteration bound per step")
     ap.add_argument("--workload", default=None, choices=["batched512", "learned", "grf1024_p2"],
                     help="run another workload than the default step benchmark; prints one line")
     ap.add_argument("--nprob", type=int, default=None, help="batched512: number of problems (default 512)")

@@ -307,9 +307,9 @@ __device__ __forceinline__ void store_sigma(const T (&d)[N], const T (&z1)[N], c
 // so that B enters through G and det B alone.  nsl[n]: slot of the neighbour across
 // edge n (see edge_mean).
 template <typename T, int N, int R2, int R1>
-__device__ __forceinline__ void slot_zeta(const T *phiE_s, const T *__restrict__ X, const T *__restrict__ Bg,
-                                          const int32_t *__restrict__ nbr, int Ki, int e, const int (&nsl)[3],
-                                          const T (&d)[N], T *tr, int NS, int slot, T (&z1)[N], T (&z2)[N]) {
+__device__ __forceinline__ void slot_zeta(const T *phiE_s, const T *__restrict__ X, int Ki, int e, const T (&x)[N],
+                                          const T (&d)[N], const T (&bk)[4], const int (&code)[3],
+                                          const int (&nsl)[3], T *tr, int NS, int slot, T (&z1)[N], T (&z2)[N]) {
     const CTab<T, N, R2, R1> &t = c_tab<T, N, R2, R1>;
     // P = H^_1 x, Q = H^_2 x (only the entries below the diagonal blocks of degree are nonzero)
     if constexpr (kCompactCode<T>) {
@@ -327,9 +327,6 @@ __device__ __forceinline__ void slot_zeta(const T *phiE_s, const T *__restrict__
             }
         }
     } else {
-        T x[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) x[j] = X[j * Ki + e];
 #pragma unroll
         for (int i = 0; i < N; ++i) {
             T h1 = T(0), h2 = T(0);
@@ -342,7 +339,7 @@ __device__ __forceinline__ void slot_zeta(const T *phiE_s, const T *__restrict__
             z2[i] = h2;
         }
     }
-    const int c0 = nbr[e], c1 = nbr[Ki + e], c2 = nbr[2 * Ki + e];
+    const int c0 = code[0], c1 = code[1], c2 = code[2];
     {
         T f[R1];
         if (c0 != NBR_DIRICHLET) {
@@ -358,7 +355,7 @@ __device__ __forceinline__ void slot_zeta(const T *phiE_s, const T *__restrict__
             edge_test_add<T, N, R2, R1, 2>(f, z1, z2, 2);
         }
     }
-    const T b11 = Bg[e], b12 = Bg[Ki + e], b21 = Bg[2 * Ki + e], b22 = Bg[3 * Ki + e];
+    const T b11 = bk[0], b12 = bk[1], b21 = bk[2], b22 = bk[3];
     const T inv = T(1) / (b11 * b22 - b12 * b21);
     const T g11 = (b11 * b11 + b21 * b21) * inv, g12 = (b11 * b12 + b21 * b22) * inv,
             g22 = (b12 * b12 + b22 * b22) * inv;
@@ -433,10 +430,12 @@ constexpr int FUSED_MAX_TE = 256;
 
 // Minimum resident blocks per SM asked of the register allocator: two for the FP32
 // kernels of p >= 3, which would otherwise take 130-168 registers a thread and run
-// one block per SM (0 leaves the allocator's default).
+// one block per SM; four for p = 1, 2 (at most 51 registers: measured on 2,097,152
+// triangles at p = 2, 141 us with the allocator's 64-register choice and three blocks
+// per SM, 121 us with four); 0 leaves the allocator's default.
 template <typename T, int N>
 struct FusedOcc {
-    static constexpr int min_blocks = (sizeof(T) == 4 && N >= 10) ? 2 : 0;
+    static constexpr int min_blocks = (sizeof(T) == 4 && N >= 10) ? 2 : (sizeof(T) == 4 && N >= 3) ? 4 : 0;
 };
 
 // Volume term -sum_m G^m Z^m at the triangle points (Sec. 3.6.3).  In contravariant
@@ -576,25 +575,27 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
             }
         }
     }
+    T bk[4];
+    int code[3], nsl[3];
     // A1: traces of x of every slot (tile triangles load d_h for the later phases)
     if (i < TE) {
         if (i < cnt) {
             const int k = start + i;
-            T x[N];
+            T xa[N];
 #pragma unroll
             for (int j = 0; j < N; ++j) {
-                x[j] = X[j * Ki + k];
+                xa[j] = X[j * Ki + k];
                 d[j] = Dc[j * Ki + k];
             }
-            slot_xtraces<T, N, R2, R1>(x, tr, NS, i);
+            slot_xtraces<T, N, R2, R1>(xa, tr, NS, i);
         }
     } else {
         for (int j = i - TE; j < nh; j += hstride) {
-            const int e = halo[h0 + j];
-            T x[N];
+            const int eh = halo[h0 + j];
+            T xh[N];
 #pragma unroll
-            for (int l = 0; l < N; ++l) x[l] = X[l * Ki + e];
-            slot_xtraces<T, N, R2, R1>(x, tr, NS, TE + j);
+            for (int l = 0; l < N; ++l) xh[l] = X[l * Ki + eh];
+            slot_xtraces<T, N, R2, R1>(xh, tr, NS, TE + j);
         }
     }
     __syncthreads();
@@ -602,18 +603,34 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
     if (i < TE) {
         if (i < cnt) {
             const int k = start + i;
-            const int nsl[3] = {slotg[k], slotg[Ki + k], slotg[2 * Ki + k]};
-            slot_zeta<T, N, R2, R1>(phiE_s, X, Bg, nbr, Ki, k, nsl, d, tr, NS, i, z1, z2);
+            T xa[N], ba[4];
+            int ca[3];
+#pragma unroll
+            for (int j = 0; j < N; ++j) xa[j] = X[j * Ki + k];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) ba[q] = Bg[q * Ki + k];
+#pragma unroll
+            for (int n = 0; n < 3; ++n) ca[n] = nbr[n * Ki + k];
+            const int sa[3] = {slotg[k], slotg[Ki + k], slotg[2 * Ki + k]};
+            slot_zeta<T, N, R2, R1>(phiE_s, X, Ki, k, xa, d, ba, ca, sa, tr, NS, i, z1, z2);
         }
     } else {
         for (int j = i - TE; j < nh; j += hstride) {
-            const int e = halo[h0 + j];
+            const int eh = halo[h0 + j];
             const int q = 3 * (h0 + j);
-            const int nsl[3] = {halo_slot[q], halo_slot[q + 1], halo_slot[q + 2]};
-            T hd[N], hz1[N], hz2[N];
+            T xh[N], hd[N], hb[4], hz1[N], hz2[N];
+            int hc[3];
+            const int hs[3] = {halo_slot[q], halo_slot[q + 1], halo_slot[q + 2]};
 #pragma unroll
-            for (int l = 0; l < N; ++l) hd[l] = Dc[l * Ki + e];
-            slot_zeta<T, N, R2, R1>(phiE_s, X, Bg, nbr, Ki, e, nsl, hd, tr, NS, TE + j, hz1, hz2);
+            for (int l = 0; l < N; ++l) {
+                xh[l] = X[l * Ki + eh];
+                hd[l] = Dc[l * Ki + eh];
+            }
+#pragma unroll
+            for (int l = 0; l < 4; ++l) hb[l] = Bg[l * Ki + eh];
+#pragma unroll
+            for (int n = 0; n < 3; ++n) hc[n] = nbr[n * Ki + eh];
+            slot_zeta<T, N, R2, R1>(phiE_s, X, Ki, eh, xh, hd, hb, hc, hs, tr, NS, TE + j, hz1, hz2);
         }
     }
     __syncthreads();
@@ -632,12 +649,17 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
             volume_smem<T, N, R2, NP>(vol_s, vol_s + R2 * NP, vol_s + 2 * R2 * NP, d, z1, z2, acc);
         else
             volume_const<T, N, R2, R1>(d, z1, z2, acc);
-        const int c0 = nbr[k], c1 = nbr[Ki + k], c2 = nbr[2 * Ki + k];
-        tile_edge<T, N, R2, R1, 0>(c0, c0 >= 0 ? slotg[k] : 0, tr, NS, i, eta, acc);
-        tile_edge<T, N, R2, R1, 1>(c1, c1 >= 0 ? slotg[Ki + k] : 0, tr, NS, i, eta, acc);
-        tile_edge<T, N, R2, R1, 2>(c2, c2 >= 0 ? slotg[2 * Ki + k] : 0, tr, NS, i, eta, acc);
-        const T det = Bg[k] * Bg[3 * Ki + k] - Bg[Ki + k] * Bg[2 * Ki + k];
-        const T md = mass * det;
+        // loaded after the volume term, whose registers are then free
+#pragma unroll
+        for (int n = 0; n < 3; ++n) code[n] = nbr[n * Ki + k];
+#pragma unroll
+        for (int n = 0; n < 3; ++n) nsl[n] = code[n] >= 0 ? slotg[n * Ki + k] : 0;
+        tile_edge<T, N, R2, R1, 0>(code[0], code[0] >= 0 ? nsl[0] : 0, tr, NS, i, eta, acc);
+        tile_edge<T, N, R2, R1, 1>(code[1], code[1] >= 0 ? nsl[1] : 0, tr, NS, i, eta, acc);
+        tile_edge<T, N, R2, R1, 2>(code[2], code[2] >= 0 ? nsl[2] : 0, tr, NS, i, eta, acc);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) bk[q] = Bg[q * Ki + k];
+        const T md = mass * (bk[0] * bk[3] - bk[1] * bk[2]);
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             const T yj = md * X[j * Ki + k] + tau * acc[j];
