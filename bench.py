@@ -45,13 +45,24 @@ def peaks():
 
 
 def flops_per_element(N, R2, R1):
-    """Algorithmic FLOPs (2 x multiply-adds) of one apply per interior triangle in the
-    quadrature formulation the fused kernel executes:
-    2 N^2 (-H^m x) + 18 R1 N (traces of x and d_h on 3 edges, the neighbour's x trace
-    for the central flux, the flux test, traces of z^1 and z^2) + 5 R2 N (d_h, z^1, z^2
-    at the triangle points and the gradient test) + 3 R1 N (edge test).  Recomputation
-    for halo triangles is overhead and not counted."""
-    return 2 * (2 * N * N + 18 * R1 * N + 5 * R2 * N + 3 * R1 * N)
+    """Algorithmic FLOPs (2 per multiply-add, 1 per add or multiply) of one apply per
+    interior triangle in the contravariant quadrature form the fused kernel executes:
+      3 R1 N           traces of x on the three edges;
+      nnz(H^_1, H^_2)  u^_m = H^_m x (entries below the degree blocks only);
+      3 R1 N           edge tests of the central values {x};
+      8 N              P, Q and zeta = G P, Q / det B;
+      6 R1 N + 3 R1    traces of d_h and of nu^ . zeta, sigma = their product;
+      R2 (5 N + 2)     d_h, zeta^1, zeta^2 at the triangle points, the products, the
+                       gradient test (the constant function has none: 2 (N - 1));
+      3 R1 (N + 4)     the edge terms and their test;
+      2 N              y = M x + tau acc.
+    Multiply-adds count twice.  Recomputation for halo triangles is overhead and not
+    counted."""
+    deg = [0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4, 4][:N]
+    nnz_h = 2 * sum(d * (d + 1) // 2 for d in deg)
+    fma = 3 * R1 * N + nnz_h + 3 * R1 * N + 4 * N + 6 * R1 * N + R2 * (3 * N + 2 * (N - 1)) + 3 * R1 * N + 2 * N
+    single = 4 * N + 3 * R1 + 2 * R2 + 3 * R1 * 4
+    return 2 * fma + single
 
 
 def bytes_per_element(N, s, geom_s):

@@ -27,7 +27,7 @@ def nvcc():
 
 def flags(extra=()):
     return ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O3", "-I" + os.path.join(ROOT, "include"),
-            *ARCH, *extra]
+            "-I" + BUILD, *ARCH, *extra]
 
 
 def _compile(src, extra):
@@ -39,8 +39,25 @@ def _compile(src, extra):
     return obj, r.stderr
 
 
+def gen_tables():
+    """Compile and run gen_tables (host code: the library's own table builder) to write the
+    FP32 reference tables as device constants into _build/festung_tables_gen.h."""
+    exe = os.path.join(BUILD, "gen_tables")
+    cmd = [nvcc(), "-O2", "-std=c++17", "-I" + os.path.join(ROOT, "include"), "-x", "cu",
+           os.path.join(CSRC, "gen_tables.cpp"), "-x", "cu", os.path.join(CSRC, "tables.cpp"), "-o", exe]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("gen_tables build failed:\n%s\n%s" % (" ".join(cmd), r.stderr[-4000:]))
+    out = os.path.join(BUILD, "festung_tables_gen.h")
+    r = subprocess.run([exe, out], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("gen_tables failed:\n%s" % r.stderr[-4000:])
+    return out
+
+
 def build(verbose=False, extra=()):
     os.makedirs(BUILD, exist_ok=True)
+    gen_tables()
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         results = list(ex.map(lambda s: _compile(s, extra), SOURCES))
     objs = [o for o, _ in results]

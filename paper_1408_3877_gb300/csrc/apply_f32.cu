@@ -78,6 +78,5 @@ void launch_apply_twopass<float>(const festung_ctx *c, const float *x, float *y,
     });
 }
 
-cudaError_t upload_tables_f32(const festung_ctx *c) { return upload_ctab<float>(c); }
 
 }  // namespace festung

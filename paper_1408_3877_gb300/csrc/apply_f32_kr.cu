@@ -31,6 +31,5 @@ void launch_apply_bicg<float>(const festung_ctx *c, const float *x, float *y, fl
     });
 }
 
-cudaError_t upload_tables_f32_kr(const festung_ctx *c) { return upload_ctab<float>(c); }
 
 }  // namespace festung

@@ -1087,10 +1087,7 @@ int festung_setup(festung_ctx *c, int p, int quad_order, double eta) {
     FCK(cudaMalloc(&c->bTab, o.total * sizeof(float)));
     FCK(cudaMemcpy(c->bTab, hb.data(), o.total * sizeof(float), cudaMemcpyHostToDevice));
     FCK(upload_tables_f64(c));
-    FCK(upload_tables_f32(c));
-    FCK(upload_tables_f32_kr(c));
     FCK(upload_tables_df(c));
-    FCK(upload_tables_bf16(c));
     {
         // double-float copies of the tables and the geometry (residual applies)
         std::vector<dfloat> hx(o.total);

@@ -49,10 +49,9 @@ __constant__ CTab<T, N, R2, R1> c_tab;
 
 // Copy the reference tables of the context's (N, R2, R1) into this translation unit's
 // constant bank, once per device.  The tables depend only on p and the quadrature, so
-// every context of the same shape writes identical values.  bf16: round every entry to
-// BF16 first (a unit that uses this holds only BF16-valued tables).
+// every context of the same shape writes identical values.
 template <typename T>
-cudaError_t upload_ctab(const festung_ctx *c, bool bf16 = false) {
+cudaError_t upload_ctab(const festung_ctx *c) {
     cudaError_t err = cudaSuccess;
     int dev = 0;
     if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
@@ -62,14 +61,7 @@ cudaError_t upload_ctab(const festung_ctx *c, bool bf16 = false) {
         const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
         if (done & bit) return;
         CTab<T, N, R2, R1> h;
-        const HostTables &t0 = c->tab;
-        HostTables tb;
-        if (bf16) {
-            tb = t0;
-            for (std::vector<double> *v : {&tb.phiQ, &tb.gw1, &tb.gw2, &tb.H1, &tb.H2, &tb.phiE, &tb.wphiE})
-                for (double &e : *v) e = round_to_bf16(e);
-        }
-        const HostTables &t = bf16 ? tb : t0;
+        const HostTables &t = c->tab;
         for (int i = 0; i < R2 * N; ++i) {
             h.phiQ[i] = (T)t.phiQ[i];
             h.gw1[i] = (T)t.gw1[i];
@@ -90,10 +82,31 @@ cudaError_t upload_ctab(const festung_ctx *c, bool bf16 = false) {
 }
 }  // namespace
 
-// own-edge trace with a compile-time edge index (constant-bank table)
-template <typename T, int N, int R2, int R1, int n>
+// The FP32 tables as compile-time constants: GenTab<N, R2, R1, kind> is specialised in
+// festung_tables_gen.h, which the build writes from build_tables() (kind 0: FP32 values,
+// kind 1: rounded to BF16).  An initialised constant object lets the compiler fold every
+// access with a compile-time index into an immediate operand; FP64 and double-float
+// kernels read the constant-bank copy c_tab filled by upload_ctab.
+template <int N, int R2, int R1, int TK>
+struct GenTab;
+}  // namespace festung
+
+#include "festung_tables_gen.h"
+
+namespace festung {
+
+template <typename T, int N, int R2, int R1, int TK>
+__device__ __forceinline__ const CTab<T, N, R2, R1> &tab_ref() {
+    if constexpr (std::is_same<T, float>::value)
+        return GenTab<N, R2, R1, TK>::get();
+    else
+        return c_tab<T, N, R2, R1>;
+}
+
+// own-edge trace with a compile-time edge index
+template <typename T, int N, int R2, int R1, int TK, int n>
 __device__ __forceinline__ void ctrace(const T (&c)[N], T (&out)[R1]) {
-    const CTab<T, N, R2, R1> &t = c_tab<T, N, R2, R1>;
+    const CTab<T, N, R2, R1> &t = tab_ref<T, N, R2, R1, TK>();
 #pragma unroll
     for (int r = 0; r < R1; ++r) {
         T v = T(0);
@@ -176,10 +189,10 @@ __device__ __forceinline__ T &tr_at(T *tr, int f, int n, int slot, int NS, int r
 }
 
 // trace of c on own edge n into field f of the slot's shared-memory traces
-template <typename T, int N, int R2, int R1, int n>
+template <typename T, int N, int R2, int R1, int TK, int n>
 __device__ __forceinline__ void store_trace(const T (&c)[N], T *tr, int f, int NS, int slot) {
     if constexpr (kCompactCode<T>) {
-        const CTab<T, N, R2, R1> &t = c_tab<T, N, R2, R1>;
+        const CTab<T, N, R2, R1> &t = tab_ref<T, N, R2, R1, TK>();
 #pragma unroll 1
         for (int r = 0; r < R1; ++r) {
             T v = T(0);
@@ -189,24 +202,24 @@ __device__ __forceinline__ void store_trace(const T (&c)[N], T *tr, int f, int N
         }
     } else {
         T v[R1];
-        ctrace<T, N, R2, R1, n>(c, v);
+        ctrace<T, N, R2, R1, TK, n>(c, v);
         tr_store<T, R1>(tr, f, n, slot, NS, v);
     }
 }
 
 // Phase A1: traces of x on the three edges of a slot (field 0).
-template <typename T, int N, int R2, int R1>
+template <typename T, int N, int R2, int R1, int TK>
 __device__ __forceinline__ void slot_xtraces(const T (&x)[N], T *tr, int NS, int slot) {
-    store_trace<T, N, R2, R1, 0>(x, tr, 0, NS, slot);
-    store_trace<T, N, R2, R1, 1>(x, tr, 0, NS, slot);
-    store_trace<T, N, R2, R1, 2>(x, tr, 0, NS, slot);
+    store_trace<T, N, R2, R1, TK, 0>(x, tr, 0, NS, slot);
+    store_trace<T, N, R2, R1, TK, 1>(x, tr, 0, NS, slot);
+    store_trace<T, N, R2, R1, TK, 2>(x, tr, 0, NS, slot);
 }
 
 // Central value {x} of the edge at our Gauss point r: the mean of our trace and the
 // neighbour's, taken at its point R1 - 1 - r (the maps of eq. mapEE reverse the edge);
 // our own trace on a Neumann edge (eq. globQm:N).  The neighbour's trace comes from its
 // slot, or from global memory when the neighbour of a halo triangle has no slot (nsl = -2).
-template <typename T, int N, int R2, int R1, int n>
+template <typename T, int N, int R2, int R1, int TK, int n>
 __device__ __forceinline__ void edge_mean(const T *phiE_s, const T *__restrict__ X, int Ki, int code, int nsl,
                                           const T *tr, int NS, int slot, T (&f)[R1]) {
     tr_load<T, R1>(tr, 0, n, slot, NS, f);
@@ -226,9 +239,9 @@ __device__ __forceinline__ void edge_mean(const T *phiE_s, const T *__restrict__
 }
 
 // e += sgn * sum_r wphi_E[n][r][i] f_r: the edge's part of the reference flux (P or Q).
-template <typename T, int N, int R2, int R1, int n>
+template <typename T, int N, int R2, int R1, int TK, int n>
 __device__ __forceinline__ void edge_test_add(const T (&f)[R1], T (&a)[N], T (&b)[N], int which) {
-    const CTab<T, N, R2, R1> &t = c_tab<T, N, R2, R1>;
+    const CTab<T, N, R2, R1> &t = tab_ref<T, N, R2, R1, TK>();
     if constexpr (kCompactCode<T>) {
 #pragma unroll 1
         for (int r = 0; r < R1; ++r) {
@@ -267,10 +280,10 @@ __device__ __forceinline__ void edge_test_add(const T (&f)[R1], T (&a)[N], T (&b
 // sigma_n = d_h (nu^_n . zeta) at the Gauss points of edge n (field 1): the normal flux
 // d_h z . nu |E| of the edge in reference coordinates (nu^_0 = (1, 1), nu^_1 = (-1, 0),
 // nu^_2 = (0, -1)).
-template <typename T, int N, int R2, int R1, int n>
+template <typename T, int N, int R2, int R1, int TK, int n>
 __device__ __forceinline__ void store_sigma(const T (&d)[N], const T (&z1)[N], const T (&z2)[N], T *tr, int NS,
                                             int slot) {
-    const CTab<T, N, R2, R1> &t = c_tab<T, N, R2, R1>;
+    const CTab<T, N, R2, R1> &t = tab_ref<T, N, R2, R1, TK>();
     T w[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) w[j] = n == 0 ? z1[j] + z2[j] : (n == 1 ? -z1[j] : -z2[j]);
@@ -287,8 +300,8 @@ __device__ __forceinline__ void store_sigma(const T (&d)[N], const T (&z1)[N], c
         }
     } else {
         T dv[R1], wv[R1];
-        ctrace<T, N, R2, R1, n>(d, dv);
-        ctrace<T, N, R2, R1, n>(w, wv);
+        ctrace<T, N, R2, R1, TK, n>(d, dv);
+        ctrace<T, N, R2, R1, TK, n>(w, wv);
 #pragma unroll
         for (int r = 0; r < R1; ++r) dv[r] *= wv[r];
         tr_store<T, R1>(tr, 1, n, slot, NS, dv);
@@ -306,11 +319,11 @@ __device__ __forceinline__ void store_sigma(const T (&d)[N], const T (&z1)[N], c
 //   P = u^_1 - e_0 + e_1,  Q = u^_2 - e_0 + e_2,
 // so that B enters through G and det B alone.  nsl[n]: slot of the neighbour across
 // edge n (see edge_mean).
-template <typename T, int N, int R2, int R1>
+template <typename T, int N, int R2, int R1, int TK>
 __device__ __forceinline__ void slot_zeta(const T *phiE_s, const T *__restrict__ X, int Ki, int e, const T (&x)[N],
                                           const T (&d)[N], const T (&bk)[4], const int (&code)[3],
                                           const int (&nsl)[3], T *tr, int NS, int slot, T (&z1)[N], T (&z2)[N]) {
-    const CTab<T, N, R2, R1> &t = c_tab<T, N, R2, R1>;
+    const CTab<T, N, R2, R1> &t = tab_ref<T, N, R2, R1, TK>();
     // P = H^_1 x, Q = H^_2 x (only the entries below the diagonal blocks of degree are nonzero)
     if constexpr (kCompactCode<T>) {
 #pragma unroll
@@ -343,16 +356,16 @@ __device__ __forceinline__ void slot_zeta(const T *phiE_s, const T *__restrict__
     {
         T f[R1];
         if (c0 != NBR_DIRICHLET) {
-            edge_mean<T, N, R2, R1, 0>(phiE_s, X, Ki, c0, nsl[0], tr, NS, slot, f);
-            edge_test_add<T, N, R2, R1, 0>(f, z1, z2, 0);
+            edge_mean<T, N, R2, R1, TK, 0>(phiE_s, X, Ki, c0, nsl[0], tr, NS, slot, f);
+            edge_test_add<T, N, R2, R1, TK, 0>(f, z1, z2, 0);
         }
         if (c1 != NBR_DIRICHLET) {
-            edge_mean<T, N, R2, R1, 1>(phiE_s, X, Ki, c1, nsl[1], tr, NS, slot, f);
-            edge_test_add<T, N, R2, R1, 1>(f, z1, z2, 1);
+            edge_mean<T, N, R2, R1, TK, 1>(phiE_s, X, Ki, c1, nsl[1], tr, NS, slot, f);
+            edge_test_add<T, N, R2, R1, TK, 1>(f, z1, z2, 1);
         }
         if (c2 != NBR_DIRICHLET) {
-            edge_mean<T, N, R2, R1, 2>(phiE_s, X, Ki, c2, nsl[2], tr, NS, slot, f);
-            edge_test_add<T, N, R2, R1, 2>(f, z1, z2, 2);
+            edge_mean<T, N, R2, R1, TK, 2>(phiE_s, X, Ki, c2, nsl[2], tr, NS, slot, f);
+            edge_test_add<T, N, R2, R1, TK, 2>(f, z1, z2, 2);
         }
     }
     const T b11 = bk[0], b12 = bk[1], b21 = bk[2], b22 = bk[3];
@@ -365,19 +378,19 @@ __device__ __forceinline__ void slot_zeta(const T *phiE_s, const T *__restrict__
         z1[i] = g22 * P - g12 * Q;
         z2[i] = g11 * Q - g12 * P;
     }
-    store_sigma<T, N, R2, R1, 0>(d, z1, z2, tr, NS, slot);
-    store_sigma<T, N, R2, R1, 1>(d, z1, z2, tr, NS, slot);
-    store_sigma<T, N, R2, R1, 2>(d, z1, z2, tr, NS, slot);
+    store_sigma<T, N, R2, R1, TK, 0>(d, z1, z2, tr, NS, slot);
+    store_sigma<T, N, R2, R1, TK, 1>(d, z1, z2, tr, NS, slot);
+    store_sigma<T, N, R2, R1, TK, 2>(d, z1, z2, tr, NS, slot);
 }
 
 // Phase B, edge n of tile triangle i: R^m, R_D^m (eq. globR, globR:D) and the penalty
 // S, S_D (eq. globS, globS:D) from the traces in shared memory.  On an interior edge
 // the neighbour's outward normal is the opposite of ours, so the central flux
 // 1/2 nu . (d^- z^- + d^+ z^+) |E| is (sigma^- - sigma^+) / 2.
-template <typename T, int N, int R2, int R1, int n>
+template <typename T, int N, int R2, int R1, int TK, int n>
 __device__ __forceinline__ void tile_edge(int code, int sl, const T *tr, int NS, int i, T eta, T (&acc)[N]) {
     if (code == NBR_NEUMANN) return;
-    const CTab<T, N, R2, R1> &t = c_tab<T, N, R2, R1>;
+    const CTab<T, N, R2, R1> &t = tab_ref<T, N, R2, R1, TK>();
     if constexpr (kCompactCode<T>) {
 #pragma unroll 1
         for (int r = 0; r < R1; ++r) {
@@ -442,9 +455,9 @@ struct FusedOcc {
 // form the integrand grad phi_i . d_h z is (grad^ phi_i . d_h zeta) / det B and the
 // quadrature weight carries det B, so no geometry enters: -sum_r d_h (w_r d_1 phi_i
 // zeta^1 + w_r d_2 phi_i zeta^2) at q_r.  Tables in the constant bank.
-template <typename T, int N, int R2, int R1>
+template <typename T, int N, int R2, int R1, int TK>
 __device__ __forceinline__ void volume_const(const T (&d)[N], const T (&z1)[N], const T (&z2)[N], T (&acc)[N]) {
-    const CTab<T, N, R2, R1> &t = c_tab<T, N, R2, R1>;
+    const CTab<T, N, R2, R1> &t = tab_ref<T, N, R2, R1, TK>();
 #pragma unroll
     for (int r = 0; r < R2; ++r) {
         T dv = T(0), w1 = T(0), w2 = T(0);
@@ -518,7 +531,7 @@ bool allow_max_smem(Kern kernel) {
 // EPI: reductions fused into the end of the apply (FUSED_EPI_* in krylov.cuh; one
 // partial per block, the last block updates the scalars); e1, e2: r0 (ALPHA); s, r0
 // (OMEGA).
-template <typename T, int N, int R2, int R1, int EPI = FUSED_EPI_NONE>
+template <typename T, int N, int R2, int R1, int EPI = FUSED_EPI_NONE, int TK = 0>
 __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_apply_fused(
     const T *__restrict__ X, T *__restrict__ Y, const T *__restrict__ Dc, const T *__restrict__ Bg,
     const int32_t *__restrict__ nbr, const int16_t *__restrict__ slotg, const int32_t *__restrict__ halo_ptr,
@@ -587,7 +600,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
                 xa[j] = X[j * Ki + k];
                 d[j] = Dc[j * Ki + k];
             }
-            slot_xtraces<T, N, R2, R1>(xa, tr, NS, i);
+            slot_xtraces<T, N, R2, R1, TK>(xa, tr, NS, i);
         }
     } else {
         for (int j = i - TE; j < nh; j += hstride) {
@@ -595,7 +608,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
             T xh[N];
 #pragma unroll
             for (int l = 0; l < N; ++l) xh[l] = X[l * Ki + eh];
-            slot_xtraces<T, N, R2, R1>(xh, tr, NS, TE + j);
+            slot_xtraces<T, N, R2, R1, TK>(xh, tr, NS, TE + j);
         }
     }
     __syncthreads();
@@ -612,7 +625,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
 #pragma unroll
             for (int n = 0; n < 3; ++n) ca[n] = nbr[n * Ki + k];
             const int sa[3] = {slotg[k], slotg[Ki + k], slotg[2 * Ki + k]};
-            slot_zeta<T, N, R2, R1>(phiE_s, X, Ki, k, xa, d, ba, ca, sa, tr, NS, i, z1, z2);
+            slot_zeta<T, N, R2, R1, TK>(phiE_s, X, Ki, k, xa, d, ba, ca, sa, tr, NS, i, z1, z2);
         }
     } else {
         for (int j = i - TE; j < nh; j += hstride) {
@@ -630,7 +643,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
             for (int l = 0; l < 4; ++l) hb[l] = Bg[l * Ki + eh];
 #pragma unroll
             for (int n = 0; n < 3; ++n) hc[n] = nbr[n * Ki + eh];
-            slot_zeta<T, N, R2, R1>(phiE_s, X, Ki, eh, xh, hd, hb, hc, hs, tr, NS, TE + j, hz1, hz2);
+            slot_zeta<T, N, R2, R1, TK>(phiE_s, X, Ki, eh, xh, hd, hb, hc, hs, tr, NS, TE + j, hz1, hz2);
         }
     }
     __syncthreads();
@@ -648,15 +661,15 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
         if constexpr (kBigVolume)
             volume_smem<T, N, R2, NP>(vol_s, vol_s + R2 * NP, vol_s + 2 * R2 * NP, d, z1, z2, acc);
         else
-            volume_const<T, N, R2, R1>(d, z1, z2, acc);
+            volume_const<T, N, R2, R1, TK>(d, z1, z2, acc);
         // loaded after the volume term, whose registers are then free
 #pragma unroll
         for (int n = 0; n < 3; ++n) code[n] = nbr[n * Ki + k];
 #pragma unroll
         for (int n = 0; n < 3; ++n) nsl[n] = code[n] >= 0 ? slotg[n * Ki + k] : 0;
-        tile_edge<T, N, R2, R1, 0>(code[0], code[0] >= 0 ? nsl[0] : 0, tr, NS, i, eta, acc);
-        tile_edge<T, N, R2, R1, 1>(code[1], code[1] >= 0 ? nsl[1] : 0, tr, NS, i, eta, acc);
-        tile_edge<T, N, R2, R1, 2>(code[2], code[2] >= 0 ? nsl[2] : 0, tr, NS, i, eta, acc);
+        tile_edge<T, N, R2, R1, TK, 0>(code[0], code[0] >= 0 ? nsl[0] : 0, tr, NS, i, eta, acc);
+        tile_edge<T, N, R2, R1, TK, 1>(code[1], code[1] >= 0 ? nsl[1] : 0, tr, NS, i, eta, acc);
+        tile_edge<T, N, R2, R1, TK, 2>(code[2], code[2] >= 0 ? nsl[2] : 0, tr, NS, i, eta, acc);
 #pragma unroll
         for (int q = 0; q < 4; ++q) bk[q] = Bg[q * Ki + k];
         const T md = mass * (bk[0] * bk[3] - bk[1] * bk[2]);

@@ -64,13 +64,11 @@ void launch_apply_bicg_bf16tab(const festung_ctx *c, const float *x, float *y, f
                                const float *e2, double *part, KScal *sc, unsigned int *counter, const int *skip,
                                cudaStream_t st, const BatchView &bv);
 
-// Reference tables of the context's (p, quadrature) into the constant bank of the
-// fused apply kernels (FP64 and FP32 copies; BF16-rounded for launch_apply_bf16tab).
+// Reference tables of the context's (p, quadrature) into the constant bank of the FP64
+// and double-float fused apply kernels (the FP32 kernels take them as compile-time
+// constants, festung_tables_gen.h).
 cudaError_t upload_tables_f64(const festung_ctx *c);
-cudaError_t upload_tables_f32(const festung_ctx *c);
-cudaError_t upload_tables_f32_kr(const festung_ctx *c);
 cudaError_t upload_tables_df(const festung_ctx *c);
-cudaError_t upload_tables_bf16(const festung_ctx *c);
 
 // Block-Jacobi preconditioner: Pinv <- inverse of the N x N diagonal blocks of S (E1),
 // built in FP32 (scratch P, layout [(i N + j) K + k]) from the FP32 copies of geometry,
