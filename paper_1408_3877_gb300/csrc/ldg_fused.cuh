@@ -539,7 +539,11 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
     T eta, T mass, const T *__restrict__ tabg, const int *__restrict__ skip, const T *__restrict__ e1 = nullptr,
     const T *__restrict__ e2 = nullptr, double *part = nullptr, KScal *sc = nullptr,
     unsigned int *counter = nullptr, BatchView bv = BatchView()) {
-    constexpr bool kBigVolume = R2 * N > 150;
+    // FP32: the volume loop is unrolled with immediate table operands at every order (on
+    // 131,072 triangles at p = 4: 29.6 us, against 34.9 us with the tables read from
+    // shared memory in a rolled loop); FP64 and double-float keep the rolled loop at
+    // high order, whose unrolled code would not fit the instruction cache
+    constexpr bool kBigVolume = R2 * N > 150 && !std::is_same<T, float>::value;
     constexpr int NP = ((N * (int)sizeof(T) + 15) / 16) * 16 / (int)sizeof(T);
     constexpr int VOL = kBigVolume ? 3 * R2 * NP : 4;
     __shared__ __align__(16) T phiE_s[3 * R1 * N];
