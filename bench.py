@@ -381,6 +381,9 @@ def run_festung(args):
         for _ in range(3):
             solver.apply(x, y, tau, prec)
         evs = []
+        # hold the stream for ~20 ms so that every launch below is queued before the GPU
+        # reaches it: the events then time the kernels, not the host's launch latency
+        torch.cuda._sleep(40_000_000)
         for _ in range(reps):
             if flush_l2:
                 flush.zero_()
