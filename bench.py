@@ -530,7 +530,7 @@ def profile_apply(args):
     else:
         s.set_coeff(W.d_config2(0.5, xy[..., 0], xy[..., 1])[0])
     prec, dt = {"fp32": (F.FP32, torch.float32), "fp64": (F.FP64, torch.float64),
-                "dfloat": (F.DFLOAT, torch.float64)}[args.prec]
+                "dfloat": (F.DFLOAT, torch.float64), "bf16tab": (F.BF16TAB, torch.float32)}[args.prec]
     x = torch.randn(s.N, s.K, dtype=dt, device="cuda")
     y = torch.empty_like(x)
     for _ in range(2):
@@ -542,7 +542,8 @@ def profile_apply(args):
     b.record()
     torch.cuda.synchronize()
     t = a.elapsed_time(b) / 1e3 / args.reps
-    nb = bytes_per_element(s.N, 4 if args.prec == "fp32" else 8, 4 if args.prec == "fp32" else 8) * s.K
+    s32 = args.prec in ("fp32", "bf16tab")
+    nb = bytes_per_element(s.N, 4 if s32 else 8, 4 if s32 else 8) * s.K
     out = {"profile_apply": args.profile_apply, "prec": args.prec, "triangles": s.K, "N": s.N,
            "us_per_apply": t * 1e6, "alg_gbs": nb / t / 1e9,
            "tflops": flops_per_element(s.N, s.R2, s.R1) * s.K / t / 1e12,
@@ -897,7 +898,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--profile-apply", default=None, metavar="WORKLOAD",
                     help="only run the operator apply on WORKLOAD (for ncu captures); prints one line")
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "dfloat"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "dfloat", "bf16tab"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--train-seeds", type=int, default=24, help="learned: training trajectories")
     ap.add_argument("--eval-seeds", type=int, default=8, help="learned: held-out trajectories")

@@ -2,7 +2,8 @@
 // edge traces) are rounded to BF16: the operator of the BF16-table arm of the precision
 // sweep (FESTUNG_BF16TAB): the kernels of table kind 1, whose compile-time tables hold
 // BF16 values (8-bit significand) widened exactly to FP32 operands; x, D, the geometry
-// and every sum stay FP32.
+// and every sum stay FP32.  At p >= 3 their volume term runs on the tensor cores
+// (ldg_tc.cuh: BF16-valued tables times TF32-split operands, FP32 accumulation).
 #include "dispatch.h"
 #include "ldg_fused.cuh"
 #include "ops.h"
@@ -15,7 +16,7 @@ void launch_apply_bf16tab(const festung_ctx *c, const float *x, float *y, float 
     c->launches += 1;
     dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
         constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
-        const size_t smem = fused_smem<float, R1>(c->nslot);
+        const size_t smem = fused_smem<float, N, R1, 1>(c->nslot, c->TE);
         static const bool smem_ok = allow_max_smem(k_apply_fused<float, N, R2, R1, FUSED_EPI_NONE, 1>);
         (void)smem_ok;
         k_apply_fused<float, N, R2, R1, FUSED_EPI_NONE, 1><<<tiles, c->fthreads, smem, st>>>(
@@ -31,7 +32,7 @@ void launch_apply_bicg_bf16tab(const festung_ctx *c, const float *x, float *y, f
     c->launches += 1;
     dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
         constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
-        const size_t smem = fused_smem<float, R1>(c->nslot);
+        const size_t smem = fused_smem<float, N, R1, 1>(c->nslot, c->TE);
         static const bool smem_a = allow_max_smem(k_apply_fused<float, N, R2, R1, FUSED_EPI_ALPHA, 1>);
         static const bool smem_o = allow_max_smem(k_apply_fused<float, N, R2, R1, FUSED_EPI_OMEGA, 1>);
         (void)smem_a;

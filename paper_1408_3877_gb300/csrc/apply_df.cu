@@ -15,7 +15,7 @@ void launch_apply_df(const festung_ctx *c, const dfloat *x, dfloat *y, double ta
     c->launches += 1;
     dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
         constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
-        const size_t smem = fused_smem<dfloat, R1>(c->nslot);
+        const size_t smem = fused_smem<dfloat, N, R1>(c->nslot, c->TE);
         static const bool smem_ok = allow_max_smem(k_apply_fused<dfloat, N, R2, R1>);
         (void)smem_ok;
         k_apply_fused<dfloat, N, R2, R1><<<tiles, c->fthreads, smem, st>>>(

@@ -20,7 +20,7 @@ void launch_apply<float>(const festung_ctx *c, const float *x, float *y, float *
     c->launches += 1;
     dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
         constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
-        const size_t smem = fused_smem<float, R1>(c->nslot);
+        const size_t smem = fused_smem<float, N, R1>(c->nslot, c->TE);
         static const bool smem_ok = allow_max_smem(k_apply_fused<float, N, R2, R1>);
         (void)smem_ok;
         k_apply_fused<float, N, R2, R1><<<tiles, c->fthreads, smem, st>>>(x, y, c->fD, c->fB, c->dNbr, c->dSlot, c->dHaloPtr,
@@ -36,7 +36,7 @@ int fused_resident_blocks(const festung_ctx *c, int nslot) {
         static const bool smem_ok = allow_max_smem(k_apply_fused<float, N, R2, R1>);
         (void)smem_ok;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_apply_fused<float, N, R2, R1>, c->fthreads,
-                                                          fused_smem<float, R1>(nslot)) != cudaSuccess)
+                                                          fused_smem<float, N, R1>(nslot, c->TE)) != cudaSuccess)
             nb = 0;
     });
     return std::max(1, nb) * c->num_sms;
@@ -44,9 +44,9 @@ int fused_resident_blocks(const festung_ctx *c, int nslot) {
 
 size_t fused_smem_bytes(const festung_ctx *c, int nslot, bool fp64) {
     size_t b = 0;
-    dispatch(c->N, c->R2, c->R1, [&](auto, auto, auto r1_) {
-        constexpr int R1 = decltype(r1_)::value;
-        b = fp64 ? fused_smem<double, R1>(nslot) : fused_smem<float, R1>(nslot);
+    dispatch(c->N, c->R2, c->R1, [&](auto n_, auto, auto r1_) {
+        constexpr int N = decltype(n_)::value, R1 = decltype(r1_)::value;
+        b = fp64 ? fused_smem<double, N, R1>(nslot, c->TE) : fused_smem<float, N, R1>(nslot, c->TE);
     });
     return b;
 }

@@ -18,7 +18,7 @@ void launch_apply_bicg<float>(const festung_ctx *c, const float *x, float *y, fl
     c->launches += 1;
     dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
         constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
-        const size_t smem = fused_smem<float, R1>(c->nslot);
+        const size_t smem = fused_smem<float, N, R1>(c->nslot, c->TE);
         static const bool smem_a = allow_max_smem(k_apply_fused<float, N, R2, R1, FUSED_EPI_ALPHA>);
         static const bool smem_o = allow_max_smem(k_apply_fused<float, N, R2, R1, FUSED_EPI_OMEGA>);
         (void)smem_a;

@@ -14,7 +14,7 @@ void launch_apply<double>(const festung_ctx *c, const double *x, double *y, doub
     c->launches += 1;
     dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
         constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
-        const size_t smem = fused_smem<double, R1>(c->nslot);
+        const size_t smem = fused_smem<double, N, R1>(c->nslot, c->TE);
         static const bool smem_ok = allow_max_smem(k_apply_fused<double, N, R2, R1>);
         (void)smem_ok;
         k_apply_fused<double, N, R2, R1><<<tiles, c->fthreads, smem, st>>>(x, y, c->dD, c->dB, c->dNbr, c->dSlot, c->dHaloPtr,

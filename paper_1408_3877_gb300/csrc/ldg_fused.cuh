@@ -21,6 +21,7 @@
 #include "dispatch.h"
 #include "krylov_kernels.cuh"
 #include "ldg_kernels.cuh"
+#include "ldg_tc.cuh"
 
 namespace festung {
 
@@ -507,11 +508,26 @@ __device__ __forceinline__ void volume_smem(const T *phiQ_s, const T *gw1_s, con
     }
 }
 
+// The FP32 kernels of p >= 3 evaluate the volume term on the tensor cores (ldg_tc.cuh).
+// The BF16-table operator (table kind 1) of p >= 3 evaluates its volume term on the tensor
+// cores (ldg_tc.cuh).  The FP32 operator keeps it on the FP32 pipes: with immediate table
+// operands that measured faster than the mma.sync form (131,072 triangles, p = 4: 29.6 us
+// against 39.5 us; p = 3: 8.8 against 12.8 us).
+template <typename T, int N, int TK>
+constexpr bool kTensorVolume = std::is_same<T, float>::value && N >= 10 && TK == 1;
+
 // Dynamic shared memory of one block: two traced fields (x and sigma) on three edges
-// per slot.
+// per slot, then (kTensorVolume) each tile warp's staged operands, from the next 16-byte
+// boundary (they are read as 16-byte vectors; 2 x 3 x R1 x nslot values need not end on
+// one).
 template <typename T, int R1>
-constexpr size_t fused_smem(int nslot) {
-    return (size_t)2 * 3 * TraceLayout<T, R1>::RP * nslot * sizeof(T);
+__host__ __device__ constexpr size_t trace_bytes_aligned(int nslot) {
+    return (((size_t)2 * 3 * TraceLayout<T, R1>::RP * nslot * sizeof(T) + 15) / 16) * 16;
+}
+template <typename T, int N, int R1, int TK = 0>
+constexpr size_t fused_smem(int nslot, int te) {
+    return trace_bytes_aligned<T, R1>(nslot) +
+           (kTensorVolume<T, N, TK> ? (size_t)(te / 32) * TC_STAGE_FLOATS * sizeof(float) : 0);
 }
 
 // Let a kernel take the device's opt-in maximum of dynamic shared memory (once per
@@ -544,6 +560,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
     // shared memory in a rolled loop); FP64 and double-float keep the rolled loop at
     // high order, whose unrolled code would not fit the instruction cache
     constexpr bool kBigVolume = R2 * N > 150 && !std::is_same<T, float>::value;
+    constexpr bool kTC = kTensorVolume<T, N, TK>;
+    __shared__ __align__(16) float tc_s[kTC ? TC_TAB_FLOATS : 1];
     constexpr int NP = ((N * (int)sizeof(T) + 15) / 16) * 16 / (int)sizeof(T);
     constexpr int VOL = kBigVolume ? 3 * R2 * NP : 4;
     __shared__ __align__(16) T phiE_s[3 * R1 * N];
@@ -552,6 +570,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
     T *tr = reinterpret_cast<T *>(dyn_smem);
     if (skip && *skip) return;
     const int Ki = (int)K;  // K * N < 2^31 (checked at setup): 32-bit offsets
+    if constexpr (kTC) {
+        const CTab<T, N, R2, R1> &ct = tab_ref<T, N, R2, R1, TK>();
+        tc_fill_tables<N, R2>(tc_s, ct.phiQ, ct.gw1, ct.gw2);
+    }
     {
         const int o_phiE = 4 * R2 * N + 2 * N * N;  // table layout of table_offsets()
         for (int j = threadIdx.x; j < 3 * R1 * N; j += blockDim.x) phiE_s[j] = tabg[o_phiE + j];
@@ -631,6 +653,14 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
             const int sa[3] = {slotg[k], slotg[Ki + k], slotg[2 * Ki + k]};
             slot_zeta<T, N, R2, R1, TK>(phiE_s, X, Ki, k, xa, d, ba, ca, sa, tr, NS, i, z1, z2);
         }
+        if constexpr (kTC) {
+            // the volume operands go to the warp's stage now, so that their registers are
+            // free in phase B (whole warps: TE is a multiple of 32; lanes past the end of
+            // the last tile stage zeros)
+            float *stage = reinterpret_cast<float *>(dyn_smem + trace_bytes_aligned<T, R1>(NS)) +
+                           (size_t)(i >> 5) * TC_STAGE_FLOATS;
+            tc_stage<N>(i < cnt, d, z1, z2, stage);
+        }
     } else {
         for (int j = i - TE; j < nh; j += hstride) {
             const int eh = halo[h0 + j];
@@ -656,16 +686,26 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
     A dots[ND];
 #pragma unroll
     for (int q = 0; q < ND; ++q) dots[q] = A(0);
+    T acc[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) acc[j] = T(0);
+    if constexpr (kTC) {
+        // B, volume term on the tensor cores: whole warps of the tile
+        if (i < TE) {
+            float *stage = reinterpret_cast<float *>(dyn_smem + trace_bytes_aligned<T, R1>(NS)) +
+                           (size_t)(i >> 5) * TC_STAGE_FLOATS;
+            volume_tc<N, R2, TK == 1>(acc, stage, tc_s);
+        }
+    }
     if (i < cnt) {
         // B: volume and edge terms of the tile triangles
         const int k = start + i;
-        T acc[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) acc[j] = T(0);
-        if constexpr (kBigVolume)
+        if constexpr (kTC) {
+        } else if constexpr (kBigVolume) {
             volume_smem<T, N, R2, NP>(vol_s, vol_s + R2 * NP, vol_s + 2 * R2 * NP, d, z1, z2, acc);
-        else
+        } else {
             volume_const<T, N, R2, R1, TK>(d, z1, z2, acc);
+        }
         // loaded after the volume term, whose registers are then free
 #pragma unroll
         for (int n = 0; n < 3; ++n) code[n] = nbr[n * Ki + k];
