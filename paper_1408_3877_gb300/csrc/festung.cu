@@ -73,6 +73,8 @@ struct Workspace {
     double *part2 = nullptr;          // second partials buffer (CG: (r, r))
     double *res = nullptr, *h_res = nullptr;  // device / pinned host pair for residual norms
     dfloat *xdf = nullptr, *ydf = nullptr;    // N x K double-float operand and result of the residual apply
+    int *loopctl = nullptr;    // device: chunks run by the Krylov graph's loop, and their bound
+    int *h_loopctl = nullptr;  // pinned host mirror of loopctl[0]
     bool use_P = false;        // P is valid for the current step
     GraphCache g64, g32;
 };
@@ -465,6 +467,8 @@ int ensure_ws(festung_ctx *c) {
         FCK(cudaMalloc(&w.part2, sizeof(double) * 4 * w.nblk));
         FCK(cudaMallocHost(&w.h_res, sizeof(double) * 2));
         FCK(cudaMallocHost(&w.h_flags, sizeof(int) * 4));
+        FCK(cudaMalloc(&w.loopctl, sizeof(int) * 2));
+        FCK(cudaMallocHost(&w.h_loopctl, sizeof(int)));
     }
     return FESTUNG_OK;
 }
@@ -496,6 +500,8 @@ void free_ctx_device(festung_ctx *c) {
         if (c->ws->h_flags) cudaFreeHost(c->ws->h_flags);
         if (c->ws->xdf) cudaFree(c->ws->xdf);
         if (c->ws->ydf) cudaFree(c->ws->ydf);
+        if (c->ws->loopctl) cudaFree(c->ws->loopctl);
+        if (c->ws->h_loopctl) cudaFreeHost(c->ws->h_loopctl);
         delete c->ws;
         c->ws = nullptr;
     }
@@ -575,7 +581,21 @@ bool ready(festung_ctx *c) {
 // ---------------------------------------------------------------------------
 // Krylov drivers
 // ---------------------------------------------------------------------------
-constexpr int CHUNK = 16;  // iterations per captured graph
+constexpr int CHUNK = 16;  // iterations per pass of the captured loop body
+
+// The Krylov iterations of a solve run as one CUDA graph: a conditional while-node whose
+// body is CHUNK iterations followed by k_loop_cond, which continues the loop while the
+// iteration is not done and fewer than ctl[1] passes have run.  The bound ends the loop
+// whatever the iteration does.
+__global__ void k_loop_init(int *ctl, int max_chunks) {
+    ctl[0] = 0;
+    ctl[1] = max_chunks;
+}
+
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const KScal *sc, int *ctl) {
+    const int n = ++ctl[0];
+    cudaGraphSetConditional(h, (!sc->done && n < ctl[1]) ? 1u : 0u);
+}
 
 // preconditioned update kernels (templated on N)
 // s = r - alpha v, sh = P^{-1} s, (s, s)
@@ -706,26 +726,43 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
             c->launches += 2;
         }
         FCK(cudaGetLastError());
-        // capture (or reuse) a graph of CHUNK iterations
+        // build (or reuse) the graph: while (not done and under the bound) { CHUNK iterations }
         GraphCache &gc = graph_of<T>(c);
         if (!gc.exec || gc.solver != solver || gc.tau != tau || gc.use_P != (int)w.use_P || gc.mass != c->mass ||
             gc.tab_bf16 != (int)c->tab_bf16) {
             if (gc.exec) cudaGraphExecDestroy(gc.exec);
             gc.exec = nullptr;
-            cudaStream_t cs;
-            FCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
             cudaGraph_t graph;
+            FCK(cudaGraphCreate(&graph, 0));
+            cudaGraphConditionalHandle handle;
+            cudaGraphNodeParams cp = {};
+            cudaGraphNode_t node;
+            cudaStream_t cs = nullptr;
+            cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+            if (e == cudaSuccess) {
+                cp.type = cudaGraphNodeTypeConditional;
+                cp.conditional.handle = handle;
+                cp.conditional.type = cudaGraphCondTypeWhile;
+                cp.conditional.size = 1;
+                e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+            }
+            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
             const int64_t saved = c->launches;
-            FCK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-            record_iterations<T>(c, solver, (T)tau, cs);
-            FCK(cudaStreamEndCapture(cs, &graph));
+            if (e == cudaSuccess)
+                e = cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                record_iterations<T>(c, solver, (T)tau, cs);
+                k_loop_cond<<<1, 1, 0, cs>>>(handle, w.scal, w.loopctl);
+                cudaGraph_t body = nullptr;
+                e = cudaStreamEndCapture(cs, &body);
+            }
+            gc.nodes = c->launches - saved + 1;  // kernels per pass of the body
             c->launches = saved;
-            size_t nodes = 0;
-            FCK(cudaGraphGetNodes(graph, nullptr, &nodes));
-            gc.nodes = (int64_t)nodes;
-            FCK(cudaGraphInstantiate(&gc.exec, graph, 0));
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&gc.exec, graph, 0);
             cudaGraphDestroy(graph);
-            cudaStreamDestroy(cs);
+            if (cs) cudaStreamDestroy(cs);
+            FCK(e);
             gc.solver = solver;
             gc.tau = tau;
             gc.use_P = (int)w.use_P;
@@ -780,8 +817,12 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
                 *iters = total;
                 return FESTUNG_OK;
             }
+            const int max_chunks = std::max(1, (max_iter - total - h.iter + CHUNK - 1) / CHUNK);
+            k_loop_init<<<1, 1, 0, st>>>(w.loopctl, max_chunks); ++c->launches;
             FCK(cudaGraphLaunch(gc.exec, st));
-            c->launches += gc.nodes;
+            FCK(cudaMemcpyAsync(w.h_loopctl, w.loopctl, sizeof(int), cudaMemcpyDeviceToHost, st));
+            FCK(cudaStreamSynchronize(st));
+            c->launches += gc.nodes * (int64_t)*w.h_loopctl;
         }
         if (!brk && !drift) break;
         // breakdown or drift: restart from the current iterate
