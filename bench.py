@@ -634,12 +634,16 @@ def run_batched(args):
     # many as the host has threads)
     batch = F.Batch(solvers)
     l0 = batch.launch_count()
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
     value, its_mean, failed_batch, infos, load_mean = run_mode(args.warmup, args.steps)
+    clk = clocks.stop()
     launches = batch.launch_count() - l0
     # the other modes of the same batch
     others = {}
-    for name, mode, workers in (("union", F.BATCH_UNION, 0), ("concurrent_8_workers", F.BATCH_CONCURRENT, 8),
-                                ("concurrent_4_workers", F.BATCH_CONCURRENT, 4)):
+    for name, mode, workers in ((() if args.batch_quick else
+                                 (("union", F.BATCH_UNION, 0), ("concurrent_8_workers", F.BATCH_CONCURRENT, 8),
+                                  ("concurrent_4_workers", F.BATCH_CONCURRENT, 4)))):
         batch.set_mode(mode, workers)
         v, it, f, _, _ = run_mode(args.warmup, args.steps)
         others[name] = {"value": v, "unit": "s/step", "iterations_per_step_mean": it, "failed_solves": f,
@@ -648,7 +652,7 @@ def run_batched(args):
     # the same problems one after the other: single-problem mixed solve, then plain FP64
     # (the same state and time levels; the last step is timed)
     single = {}
-    for name, prec in (("mixed_per_problem", F.MIXED), ("fp64_per_problem", F.FP64)):
+    for name, prec in (("mixed_per_problem", F.MIXED),) + (() if args.batch_quick else (("fp64_per_problem", F.FP64),)):
         secs, failed = [], 0
         reset()
         for k in range(args.warmup + 1):
@@ -677,6 +681,7 @@ def run_batched(args):
                                                      if i["rel_residual"] <= tol), default=0.0)),
             "input_loading_s_per_step": load_mean, "host_preparation_s": prep,
             "gpu_launches_per_step": launches / (args.warmup + args.steps),
+            "clocks": clk,
             "other_modes": others,
             "same_problems_one_by_one": {k: {"value": v, "unit": "s/step", "speedup_of_batch": v / value,
                                              "failed_solves": f} for k, (v, f) in single.items()}}
@@ -910,6 +915,8 @@ def main():
     ap.add_argument("--workload", default=None, choices=["batched512", "learned", "grf1024_p2"],
                     help="run another workload than the default step benchmark; prints one line")
     ap.add_argument("--nprob", type=int, default=None, help="batched512: number of problems (default 512)")
+    ap.add_argument("--batch-quick", action="store_true",
+                    help="batched512: the default mode and the one-by-one mixed solve only")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
