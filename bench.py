@@ -250,6 +250,8 @@ def run_festung(args):
     man = W.Manufactured(W.d_config2)
     p, dt, tol = cfg["p"], cfg["dt"], cfg["tol"]
     s = F.Solver(cV, V0T, bdr).setup(p)
+    if args.coarse:
+        s.set_coarse(True)
     stream = torch.cuda.current_stream()
     s.set_stream(stream)
     K, N = s.K, s.N
@@ -454,10 +456,14 @@ def run_festung(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+dfloat+f64",
         "data": "synthetic (seeded manufactured solution on a seeded jittered mesh)",
         "config": {"workload": CFG_NAME, "triangles": K, "p": p, "dofs": K * N, "dt": dt, "tol": tol,
-                   "precision": "FP32 inner Krylov; refinement on double-float (48-bit) residuals; FP64 state and right-hand side", "l2": "flushed between steps",
+                   "precision": "FP32 inner Krylov (each sweep started from a p = 1 coarse correction when "
+                                "coarse_correction is true); refinement on double-float (48-bit) residuals; FP64 "
+                                "state and right-hand side", "l2": "flushed between steps",
+                   "coarse_correction": bool(args.coarse),
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "iterations_per_step": float(np.mean([i["iterations"] for i in infos])),
         "outer_per_step": float(np.mean([i["outer"] for i in infos])),
+        "coarse_iterations_per_step": float(np.mean([i["coarse_iterations"] for i in infos])),
         "rel_residual_max": float(max(i["rel_residual"] for i in infos)),
         "initial_rel_residual_median": float(np.median([i["initial_rel_residual"] for i in infos])),
         "err_vs_fp64": err_vs_fp64,
@@ -901,6 +907,7 @@ def main():
     ap.add_argument("--impl", default="festung", choices=["festung", "reference"])
     ap.add_argument("--skip-big", action="store_true", help="skip the 2M-triangle apply measurement")
     ap.add_argument("--skip-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--coarse", type=int, default=1, help="FP32 sweeps start from a p = 1 coarse correction (1) or not (0)")
     ap.add_argument("--profile-apply", default=None, metavar="WORKLOAD",
                     help="only run the operator apply on WORKLOAD (for ncu captures); prints one line")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "dfloat", "bf16tab"])

@@ -105,6 +105,7 @@ typedef struct festung_step_info {
     int    fp64_iterations; /* mixed modes: iterations of the FP64 solve that finished the step
                                after an FP32 sweep failed to lower the residual (else 0)            */
     double initial_rel_residual; /* ||b - S C0||_2 / ||b||_2 of the initial guess C0               */
+    int    coarse_iterations;    /* Krylov iterations of the coarse (p = 1) solves, festung_set_coarse */
 } festung_step_info;
 
 /* Build the grid lists of Tab. 1 (Sec. 3.1, routine generateGridData): edges,
@@ -355,6 +356,19 @@ int festung_set_stream(festung_ctx *ctx, void *stream);
 /* Message of the last failed call on ctx (or of the last failed festung_mesh_create
  * when ctx is NULL).  Valid until the next call on the context. */
 const char *festung_last_error(const festung_ctx *ctx);
+
+/* Coarse correction of the FP32 sweeps (p >= 2; FESTUNG_MIXED, _MIXED64 and _BF16TAB
+ * steps and the stationary solve).  The basis is hierarchical, so the coefficients of
+ * phi_1..phi_3 of every triangle span the P1 subspace.  With enable = 1 each sweep first
+ * solves the p = 1 problem on the same mesh (the method of Sec. 2 at p = 1, d_h replaced by
+ * its P1 part, the same tau and mass term) for the P1 part of the sweep's right-hand side,
+ * to a relative residual of 1e-2 (FP32 Krylov, block Jacobi), and starts the sweep from
+ * that correction instead of from zero.  The smooth error components, which block-Jacobi
+ * Krylov removes slowest, are handled by the small problem.  The result does not depend on
+ * it beyond the tolerance.  The p = 1 problem is built at the first step that needs it
+ * (device memory of a p = 1 context).  enable = 0 (the default) turns it off.  The paper has
+ * no counterpart: it solves directly. */
+int festung_set_coarse(festung_ctx *ctx, int enable);
 
 /* Free the context and all its device memory.  NULL is a no-op. */
 void festung_destroy(festung_ctx *ctx);

@@ -482,6 +482,10 @@ void reset_graphs(festung_ctx *c) {
 }
 
 void free_ctx_device(festung_ctx *c) {
+    if (c->coarse) {
+        festung_destroy(c->coarse);
+        c->coarse = nullptr;
+    }
     reset_graphs(c);
     if (c->ws) {
         free_vecs(c->ws->d);
@@ -1472,6 +1476,47 @@ int commit_solution(festung_ctx *c, double dt, bool stationary) {
     return FESTUNG_OK;
 }
 
+// The p = 1 problem of the coarse correction, for this step: built at first use from the
+// context's mesh (the same internal order, checked), its d_h the P1 part of ours (the first
+// three coefficients: the basis is hierarchical and orthonormal), the same mass term, its
+// block-Jacobi preconditioner for dt.
+int prepare_coarse(festung_ctx *c, double dt) {
+    cudaStream_t st = c->stream;
+    if (!c->coarse) {
+        festung_ctx *cc = nullptr;
+        int rc = festung_mesh_create(c->coordV.data(), c->numV, c->V0T.data(), c->K, c->bdr.data(), &cc);
+        if (rc == FESTUNG_OK) rc = festung_setup(cc, 1, 0, c->eta);
+        if (rc == FESTUNG_OK && cc->perm != c->perm) rc = FESTUNG_EMESH;
+        if (rc != FESTUNG_OK) {
+            c->err = std::string("coarse problem: ") + (cc ? cc->err : festung_last_error(nullptr));
+            festung_destroy(cc);
+            return rc;
+        }
+        c->coarse = cc;
+    }
+    festung_ctx *cc = c->coarse;
+    cc->stream = st;
+    cc->mass = c->mass;
+    cc->symmetric = c->symmetric;
+    int rc = ensure_ws(cc);
+    if (rc) return rc;
+    Workspace &w = *cc->ws;
+    if ((rc = alloc_vecs<float>(cc, w.f, true))) return rc;
+    const int64_t K3 = 3 * c->K;
+    k_commit_coeff<<<small_grid(K3, c), 256, 0, st>>>(K3, c->dD, cc->dD, cc->fD); ++c->launches;
+    cc->xD_valid = false;
+    if (!w.P) FCK(cudaMalloc(&w.P, (size_t)9 * cc->K * sizeof(float)));
+    if (!w.Pb) FCK(cudaMalloc(&w.Pb, (size_t)((9 + 7) / 8) * cc->K * 16));
+    FCK(cudaMemsetAsync(w.d_flags, 0, sizeof(int), st));
+    launch_blockjacobi(cc, w.P, w.Pb, dt, w.d_flags, st);
+    c->launches += 2;
+    FCK(cudaGetLastError());
+    FCK(cudaMemcpyAsync(w.h_flags, w.d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FCK(cudaStreamSynchronize(st));
+    w.use_P = (w.h_flags[0] == 0);
+    return FESTUNG_OK;
+}
+
 int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts *opts, festung_step_info *info) {
     struct MassGuard {
         festung_ctx *c;
@@ -1495,7 +1540,9 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
     cudaStream_t st = c->stream;
     Vecs<double> &V = w.d;
     double *W1 = w.scratch64;
-    int iters = 0, outer = 0, iters64 = 0;
+    int iters = 0, outer = 0, iters64 = 0, coarse_iters = 0;
+    const bool use_coarse = c->coarse_mode && c->p >= 2 && o.prec != FESTUNG_FP64;
+    if (use_coarse && (rc = prepare_coarse(c, dt))) return rc;
     double r2 = 0, b2 = 0;
     bool conv = false;
     double relres = 0.0, relres0 = -1.0;
@@ -1556,6 +1603,31 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
             prev_rn = rn;
             k_scale_to_f32<<<small_grid(KN, c), 256, 0, st>>>(KN, V.r, F.b, 1.0 / rn); ++c->launches;
             k_zero_f32<<<small_grid(KN, c), 256, 0, st>>>(KN, F.x); ++c->launches;
+            bool x_zero = true;
+            if (use_coarse) {
+                // coarse correction: the p = 1 problem for the P1 part of the right-hand side (the
+                // first 3 K entries of the N x K layout), its solution as the sweep's start
+                festung_ctx *cc = c->coarse;
+                Vecs<float> &CF = cc->ws->f;
+                const int64_t K3 = 3 * c->K;
+                FCK(cudaMemcpyAsync(CF.b, F.b, K3 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+                int cit = 0;
+                bool ccin = false;
+                double cr2, cb2;
+                const int csolver = cc->symmetric ? FESTUNG_SOLVER_CG : FESTUNG_SOLVER_BICGSTAB;
+                const int64_t l0c = cc->launches;
+                rc = krylov_solve<float>(cc, csolver, dt, 1e-2, 2000, true, &cit, &cr2, &cb2, &ccin);
+                c->launches += cc->launches - l0c;
+                if (rc) {
+                    c->err = "coarse solve: " + cc->err;
+                    return rc;
+                }
+                coarse_iters += cit;
+                if (cr2 < cb2) {  // a usable correction (finite and lowering the coarse residual)
+                    FCK(cudaMemcpyAsync(F.x, CF.x, K3 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+                    x_zero = false;
+                }
+            }
             int it = 0;
             bool cin = false;
             double ir2, ib2;
@@ -1563,7 +1635,7 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
             // after a failure the next sweep starts from a reweighted shadow residual
             const double target = std::min(0.5, std::max(o.inner_tol, 0.5 * o.tol / relres));
             c->tab_bf16 = o.prec == FESTUNG_BF16TAB;
-            rc = krylov_solve<float>(c, solver, dt, target, o.max_iter - iters, true, &it, &ir2, &ib2, &cin,
+            rc = krylov_solve<float>(c, solver, dt, target, o.max_iter - iters, x_zero, &it, &ir2, &ib2, &cin,
                                      failures > 0);
             c->tab_bf16 = false;
             if (rc) return rc;
@@ -1611,6 +1683,7 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
         info->symmetric = c->symmetric ? 1 : 0;
         info->fp64_iterations = iters64;
         info->initial_rel_residual = relres0;
+        info->coarse_iterations = coarse_iters;
     }
     if (!conv) {
         char msg[96];
@@ -1826,6 +1899,16 @@ int festung_set_stream(festung_ctx *c, void *stream) {
 const char *festung_last_error(const festung_ctx *c) {
     if (!c) return g_create_err.c_str();
     return c->err.c_str();
+}
+
+int festung_set_coarse(festung_ctx *c, int enable) {
+    if (!c) return FESTUNG_EINVAL;
+    if (enable != 0 && enable != 1) {
+        c->err = "enable must be 0 or 1";
+        return FESTUNG_EINVAL;
+    }
+    c->coarse_mode = enable;
+    return FESTUNG_OK;
 }
 
 void festung_destroy(festung_ctx *c) {

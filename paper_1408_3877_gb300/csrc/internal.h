@@ -135,6 +135,8 @@ struct festung_ctx {
     uint64_t state_gen = 0;                        // bumped whenever C changes (batches detect outside changes)
     double *dGuess = nullptr;                      // N x K correction of the next step's initial guess
     bool has_guess = false;                        // dGuess holds a guess for the next step
+    festung_ctx *coarse = nullptr;                 // the p = 1 problem on the same mesh (coarse correction)
+    int coarse_mode = 0;                           // 1: each FP32 sweep starts from a coarse correction
     double dt_prev = 0.0, dt_prev2 = 0.0;
     float *fD = nullptr;
     // double-float copies for the residual of the mixed-precision refinement

@@ -47,9 +47,11 @@ def _oracle(p, mix, man, t):
     return _ORACLE[key]
 
 
-def _gpu_step(p, mix, man, t, prec, tol, **kw):
+def _gpu_step(p, mix, man, t, prec, tol, coarse=False, **kw):
     cV, V0T, bdr = mesh(MESH_N, mix, seed=21)
     s = gpu_solver(cV, V0T, bdr, p)
+    if coarse:
+        s.set_coarse(True)
     assert s.K == 2 * MESH_N ** 2
     s.set_state(samples(s, lambda x, y: man.c(0.0, x, y)), is_samples=True)
     s.set_coeff(samples(s, lambda x, y: man.d(t, x, y)))
@@ -144,3 +146,18 @@ def test_multitile_bf16_table_step_matches_oracle(p):
     assert err <= 1e-9, (err, info)
     assert info["rel_residual"] <= 1e-12
     assert info["outer"] >= info_m["outer"], (info, info_m)  # BF16 tables need at least as many sweeps
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+@pytest.mark.parametrize("prec_name", ["MIXED", "MIXED64"])
+def test_multitile_coarse_corrected_step_matches_oracle(p, prec_name):
+    """festung_set_coarse: every FP32 sweep starts from the p = 1 coarse correction; the step
+    still matches the oracle within the mixed bound (the answer does not depend on it)."""
+    from paper_1408_3877_gb300 import festung as F
+    man = W.Manufactured(W.d_config2)
+    C, info = _gpu_step(p, "mixed", man, TAU, getattr(F, prec_name), 1e-12, coarse=True, inner_tol=1e-2)
+    Co = _oracle(p, "mixed", man, TAU)
+    err = np.linalg.norm(C - Co) / np.linalg.norm(Co)
+    assert err <= 1e-9, (err, info)
+    assert info["rel_residual"] <= 1e-12
+    assert info["coarse_iterations"] > 0 and info["fp64_iterations"] == 0, info
