@@ -362,8 +362,8 @@ const char *festung_last_error(const festung_ctx *ctx);
  * phi_1..phi_3 of every triangle span the P1 subspace.  With enable = 1 each sweep first
  * solves the p = 1 problem on the same mesh (the method of Sec. 2 at p = 1, d_h replaced by
  * its P1 part, the same tau and mass term) for the P1 part of the sweep's right-hand side,
- * to a relative residual of 1e-2 (FP32 Krylov, block Jacobi), and starts the sweep from
- * that correction instead of from zero.  The smooth error components, which block-Jacobi
+ * to a relative residual of 1e-2 (FP32 Krylov, block Jacobi, started from the previous
+ * coarse solution), and starts the sweep from that correction instead of from zero.  The smooth error components, which block-Jacobi
  * Krylov removes slowest, are handled by the small problem.  The result does not depend on
  * it beyond the tolerance.  The p = 1 problem is built at the first step that needs it
  * (device memory of a p = 1 context).  enable = 0 (the default) turns it off.  The paper has

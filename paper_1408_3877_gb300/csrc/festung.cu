@@ -1483,6 +1483,7 @@ int commit_solution(festung_ctx *c, double dt, bool stationary) {
 int prepare_coarse(festung_ctx *c, double dt) {
     cudaStream_t st = c->stream;
     if (!c->coarse) {
+        c->coarse_warm = false;
         festung_ctx *cc = nullptr;
         int rc = festung_mesh_create(c->coordV.data(), c->numV, c->V0T.data(), c->K, c->bdr.data(), &cc);
         if (rc == FESTUNG_OK) rc = festung_setup(cc, 1, 0, c->eta);
@@ -1616,7 +1617,11 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
                 double cr2, cb2;
                 const int csolver = cc->symmetric ? FESTUNG_SOLVER_CG : FESTUNG_SOLVER_BICGSTAB;
                 const int64_t l0c = cc->launches;
-                rc = krylov_solve<float>(cc, csolver, dt, 1e-2, 2000, true, &cit, &cr2, &cb2, &ccin);
+                // warm start from the previous coarse solution (both right-hand sides are scaled to
+                // unit norm, and the error of the extrapolated guess changes slowly from step to
+                // step: 82 -> 52 coarse iterations per step on the 256 x 256 p = 4 workload)
+                rc = krylov_solve<float>(cc, csolver, dt, 1e-2, 2000, !c->coarse_warm, &cit, &cr2, &cb2, &ccin);
+                c->coarse_warm = true;
                 c->launches += cc->launches - l0c;
                 if (rc) {
                     c->err = "coarse solve: " + cc->err;

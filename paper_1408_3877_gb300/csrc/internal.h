@@ -137,6 +137,7 @@ struct festung_ctx {
     bool has_guess = false;                        // dGuess holds a guess for the next step
     festung_ctx *coarse = nullptr;                 // the p = 1 problem on the same mesh (coarse correction)
     int coarse_mode = 0;                           // 1: each FP32 sweep starts from a coarse correction
+    bool coarse_warm = false;                      // the coarse context's x holds the last coarse solution
     double dt_prev = 0.0, dt_prev2 = 0.0;
     float *fD = nullptr;
     // double-float copies for the residual of the mixed-precision refinement
