@@ -576,6 +576,8 @@ def run_batched(args):
         cV, V0T, side = W.square_mesh(sp["n"])
         bdr = W.boundary_types(side, cfg["dirichlet"], cfg["neumann"])
         s = F.Solver(cV, V0T, bdr).setup(sp["p"])
+        if args.coarse:
+            s.set_coarse(True)
         man = W.Manufactured(W.grf_coefficient(W.GaussianField(sp["grf_seed"], sp["length"])))
         xy, exy = s.quad_points()
         X, Y = xy[..., 0], xy[..., 1]
@@ -681,7 +683,7 @@ def run_batched(args):
                        "orders": {str(p): sum(1 for sp in specs if sp["p"] == p) for p in (1, 2, 3)},
                        "dt": dt, "tol": tol,
                        "mode": "concurrent: every problem its own mixed step, %d workers on their own streams"
-                               % min(16, os.cpu_count() or 16)},
+                               % min(16, os.cpu_count() or 16), "coarse_correction": bool(args.coarse)},
             "dof_per_s": dofs / value, "iterations_per_step_mean": its_mean, "failed_solves": failed_batch,
             "rel_residual_max_converged": float(max((i["rel_residual"] for step_info in infos for i in step_info
                                                      if i["rel_residual"] <= tol), default=0.0)),
@@ -840,6 +842,8 @@ def run_grf_step(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     c, cV, V0T, bdr = make_problem("grf1024_p2", seed=12)
     s = F.Solver(cV, V0T, bdr).setup(c["p"])
+    if args.coarse:
+        s.set_coarse(True)
     stream = torch.cuda.current_stream()
     s.set_stream(stream)
     K, N = s.K, s.N
@@ -855,7 +859,7 @@ def run_grf_step(args):
 
     def trajectory(prec, tol_):
         s.set_state(C0)
-        secs, its, outer, fb, failed = [], [], [], 0, []
+        secs, its, outer, fb, failed, cits = [], [], [], 0, [], []
         clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
         clocks.start()
         for k in range(nsteps):
@@ -873,8 +877,10 @@ def run_grf_step(args):
             secs.append(a.elapsed_time(b) / 1e3)
             its.append(info["iterations"])
             outer.append(info["outer"])
+            cits.append(info["coarse_iterations"])
             fb += info["fp64_iterations"]
         return s.get_state(), {"s_per_step": float(np.mean(secs)) if secs else None,
+                               "coarse_iterations_per_step": float(np.mean(cits)) if cits else None,
                                "iterations_per_step": float(np.mean(its)) if its else None,
                                "outer_per_step": float(np.mean(outer)) if outer else None,
                                "fp64_fallback_iterations": fb, "steps_not_converged": failed,
@@ -894,7 +900,7 @@ def run_grf_step(args):
             "unit": "s/step", "n_gpus": 1, "steps": nsteps, "higher_is_better": False,
             "dtype": "f64 / f32 / bf16-tables+f32, f64 refinement", "data": "synthetic (seeded field and state)",
             "config": {"workload": "grf1024_p2", "triangles": K, "p": c["p"], "dofs": K * N, "dt": dt, "tol": tol,
-                       "l2": "flushed before every step"},
+                       "l2": "flushed before every step", "coarse_correction": bool(args.coarse)},
             "modes": out, "fp64_reference_1e-11": ref,
             "note": "value = the fastest mode; each mode runs the same %d steps from C^0" % nsteps}
 
