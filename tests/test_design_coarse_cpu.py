@@ -25,9 +25,9 @@ def _bicgstab_iterations(S, b, x0, M, tol):
     return count[0], np.linalg.norm(b - S @ x) / np.linalg.norm(b)
 
 
-def test_coarse_correction_cuts_iterations():
+def _last_step(n, p):
+    """Operator, right-hand side and quadratically extrapolated guess of the fifth step."""
     from oracle.solve import LDG
-    n, p = 24, 3
     tau = 16.4 / n ** 2
     cV, V0T, side = W.square_mesh(n, jitter=0.2, seed=11)
     bdr = W.boundary_types(side, (2, 4), (1, 3))
@@ -44,6 +44,13 @@ def test_coarse_correction_cuts_iterations():
         states.append(spla.spsolve(S.tocsc(), b))
     # the last step again, from the quadratic extrapolation through the three states before it
     x0 = 3 * states[-2] - 3 * states[-3] + states[-4]
+    return L, D, S, b, x0, cV, V0T, bdr, tau
+
+
+def test_coarse_correction_cuts_iterations():
+    n, p = 24, 3
+    L, D, S, b, x0, cV, V0T, bdr, tau = _last_step(n, p)
+    K, N = L.K, L.N
     blocks = sp.block_diag([sp.csr_matrix(np.linalg.inv(S[k * N:(k + 1) * N, k * N:(k + 1) * N].toarray()))
                             for k in range(K)]).tocsr()
     coarse = np.concatenate([np.arange(k * N, k * N + 3) for k in range(K)])   # modes of p <= 1
@@ -61,3 +68,46 @@ def test_coarse_correction_cuts_iterations():
     it_2l, rr_2l = _bicgstab_iterations(S, b, x0, two_level, 1e-10)
     assert rr_bj <= 2e-10 and rr_2l <= 2e-10
     assert 10 * it_2l <= it_bj, (it_bj, it_2l)
+
+
+def test_one_shot_rediscretised_coarse_correction():
+    """The form the library uses (festung_set_coarse): before a block-Jacobi sweep, solve the
+    p = 1 problem on the same mesh (d_h replaced by its P1 part, the same tau) for the P1
+    part of the residual, only to 1e-2, and start the sweep from that correction.  The error
+    it acts on is the smooth remainder that block-Jacobi BiCGStab leaves behind (here: what
+    is left after a 1e3-fold reduction from C^n, as the extrapolated guesses of the bench
+    workload leave); a sweep that reduces the residual 20-fold then needs several times
+    fewer iterations."""
+    from oracle.solve import LDG
+    n, p, tau = 40, 3, 1e-3
+    cV, V0T, side = W.square_mesh(n, jitter=0.2, seed=11)
+    bdr = W.boundary_types(side, (2, 4), (1, 3))
+    man = W.Manufactured(W.d_config2)
+    L = LDG(cV, V0T, bdr, p)
+    K, N = L.K, L.N
+    t1 = 0.5 + tau
+    D = L.project(lambda x, y: man.d(t1, x, y))
+    S = L.operator(D, tau).tocsr()
+    xs = L.project(lambda x, y: man.c(t1, x, y)).ravel()
+    b = S @ xs
+    blocks = sp.block_diag([sp.csr_matrix(np.linalg.inv(S[k * N:(k + 1) * N, k * N:(k + 1) * N].toarray()))
+                            for k in range(K)]).tocsr()
+    bj = spla.LinearOperator(S.shape, matvec=lambda v: blocks @ v)
+    xc = L.project(lambda x, y: man.c(0.5, x, y)).ravel()
+    r_c = np.linalg.norm(b - S @ xc) / np.linalg.norm(b)
+    x0, _ = spla.bicgstab(S, b, x0=xc, rtol=1e-3 * r_c, atol=0.0, M=bj, maxiter=5000)
+    L1 = LDG(cV, V0T, bdr, 1)
+    S1 = L1.operator(D[:, :3], tau).tocsr()
+    blocks1 = sp.block_diag([sp.csr_matrix(np.linalg.inv(S1[k * 3:(k + 1) * 3, k * 3:(k + 1) * 3].toarray()))
+                             for k in range(K)]).tocsr()
+    coarse = np.concatenate([np.arange(k * N, k * N + 3) for k in range(K)])
+    r = b - S @ x0
+    d1, _ = spla.bicgstab(S1, r[coarse], rtol=1e-2, atol=0.0,
+                          M=spla.LinearOperator(S1.shape, matvec=lambda v: blocks1 @ v), maxiter=2000)
+    x1 = x0.copy()
+    x1[coarse] += d1
+    target = 0.05 * np.linalg.norm(r) / np.linalg.norm(b)
+    it_0, rr_0 = _bicgstab_iterations(S, b, x0, lambda v: blocks @ v, target)
+    it_1, rr_1 = _bicgstab_iterations(S, b, x1, lambda v: blocks @ v, target)
+    assert rr_0 <= 1.01 * target and rr_1 <= 1.01 * target
+    assert 3 * it_1 <= it_0, (it_0, it_1)
