@@ -252,6 +252,7 @@ def run_festung(args):
     s = F.Solver(cV, V0T, bdr).setup(p)
     if args.coarse:
         s.set_coarse(True)
+    s.set_precond_reuse(args.precond_reuse)
     stream = torch.cuda.current_stream()
     s.set_stream(stream)
     K, N = s.K, s.N
@@ -459,11 +460,12 @@ def run_festung(args):
                    "precision": "FP32 inner Krylov (each sweep started from a p = 1 coarse correction when "
                                 "coarse_correction is true); refinement on double-float (48-bit) residuals; FP64 "
                                 "state and right-hand side", "l2": "flushed between steps",
-                   "coarse_correction": bool(args.coarse),
+                   "coarse_correction": bool(args.coarse), "precond_reuse": args.precond_reuse,
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "iterations_per_step": float(np.mean([i["iterations"] for i in infos])),
         "outer_per_step": float(np.mean([i["outer"] for i in infos])),
         "coarse_iterations_per_step": float(np.mean([i["coarse_iterations"] for i in infos])),
+        "precond_builds": int(sum(i["precond_built"] for i in infos)),
         "rel_residual_max": float(max(i["rel_residual"] for i in infos)),
         "initial_rel_residual_median": float(np.median([i["initial_rel_residual"] for i in infos])),
         "err_vs_fp64": err_vs_fp64,
@@ -556,6 +558,44 @@ def profile_apply(args):
            "checksum": float(y.double().abs().sum().item())}
     s.close()
     return out
+
+
+def profile_step(args):
+    """The timed step of the default benchmark alone (warm-up steps, then `steps` steps), for
+    launch lists under ncu; prints one line with the CUDA-event time per step."""
+    import torch
+    from paper_1408_3877_gb300 import festung as F
+    cfg, cV, V0T, bdr = make_problem(CFG_NAME, seed=11)
+    man = W.Manufactured(W.d_config2)
+    s = F.Solver(cV, V0T, bdr).setup(cfg["p"])
+    if args.coarse:
+        s.set_coarse(True)
+    s.set_precond_reuse(args.precond_reuse)
+    stream = torch.cuda.current_stream()
+    s.set_stream(stream)
+    xy, _ = s.quad_points()
+    s.set_state(man.c(0.0, xy[..., 0], xy[..., 1]), is_samples=True)
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    infos, ts = [], []
+    for i in range(args.warmup + args.steps):
+        d, f, cD, gN = step_inputs(s, cfg, man, (i + 1) * cfg["dt"], dev)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.set_coeff(d)
+        s.set_source(f)
+        s.set_bc(cD, gN)
+        info = s.step(cfg["dt"], tol=cfg["tol"], prec=F.MIXED, inner_tol=1e-2)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            infos.append(info)
+            ts.append(a.elapsed_time(b) / 1e3)
+    s.close()
+    return {"profile_step": CFG_NAME, "coarse": args.coarse, "precond_reuse": args.precond_reuse, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.mean(ts)),
+            "iterations": [i["iterations"] for i in infos], "coarse_iterations": [i["coarse_iterations"] for i in infos],
+            "outer": [i["outer"] for i in infos], "precond_built": [i["precond_built"] for i in infos]}
 
 
 def run_batched(args):
@@ -844,6 +884,7 @@ def run_grf_step(args):
     s = F.Solver(cV, V0T, bdr).setup(c["p"])
     if args.coarse:
         s.set_coarse(True)
+    s.set_precond_reuse(args.precond_reuse)
     stream = torch.cuda.current_stream()
     s.set_stream(stream)
     K, N = s.K, s.N
@@ -900,7 +941,8 @@ def run_grf_step(args):
             "unit": "s/step", "n_gpus": 1, "steps": nsteps, "higher_is_better": False,
             "dtype": "f64 / f32 / bf16-tables+f32, f64 refinement", "data": "synthetic (seeded field and state)",
             "config": {"workload": "grf1024_p2", "triangles": K, "p": c["p"], "dofs": K * N, "dt": dt, "tol": tol,
-                       "l2": "flushed before every step", "coarse_correction": bool(args.coarse)},
+                       "l2": "flushed before every step", "coarse_correction": bool(args.coarse),
+                       "precond_reuse": args.precond_reuse},
             "modes": out, "fp64_reference_1e-11": ref,
             "note": "value = the fastest mode; each mode runs the same %d steps from C^0" % nsteps}
 
@@ -914,8 +956,12 @@ def main():
     ap.add_argument("--skip-big", action="store_true", help="skip the 2M-triangle apply measurement")
     ap.add_argument("--skip-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--coarse", type=int, default=1, help="FP32 sweeps start from a p = 1 coarse correction (1) or not (0)")
+    ap.add_argument("--precond-reuse", type=int, default=8,
+                    help="one block-Jacobi build serves up to this many steps (1: every step builds)")
     ap.add_argument("--profile-apply", default=None, metavar="WORKLOAD",
                     help="only run the operator apply on WORKLOAD (for ncu captures); prints one line")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="only run the steps of the default workload (for ncu launch lists); prints one line")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "dfloat", "bf16tab"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--train-seeds", type=int, default=24, help="learned: training trajectories")
@@ -935,6 +981,8 @@ def main():
         args.warmup = 3
     if args.profile_apply:
         line = profile_apply(args)
+    elif args.profile_step:
+        line = profile_step(args)
     elif args.workload == "batched512":
         line = run_batched(args)
     elif args.workload == "learned":

@@ -106,6 +106,8 @@ typedef struct festung_step_info {
                                after an FP32 sweep failed to lower the residual (else 0)            */
     double initial_rel_residual; /* ||b - S C0||_2 / ||b||_2 of the initial guess C0               */
     int    coarse_iterations;    /* Krylov iterations of the coarse (p = 1) solves, festung_set_coarse */
+    int    precond_built;        /* 1 if this step built its block-Jacobi blocks, 0 if it reused
+                                    earlier ones (festung_set_precond_reuse)                        */
 } festung_step_info;
 
 /* Build the grid lists of Tab. 1 (Sec. 3.1, routine generateGridData): edges,
@@ -369,6 +371,19 @@ const char *festung_last_error(const festung_ctx *ctx);
  * (device memory of a p = 1 context).  enable = 0 (the default) turns it off.  The paper has
  * no counterpart: it solves directly. */
 int festung_set_coarse(festung_ctx *ctx, int enable);
+
+/* Reuse of the block-Jacobi preconditioner over time steps.  Every step solves with the
+ * inverse diagonal blocks of S; they depend on d_h, dt and the mass term and cost about as
+ * much to build as a few Krylov iterations.  With max_steps = m > 1 one build serves up
+ * to m consecutive steps (festung_step, the FP32 sweeps and the FP64 solves alike, and the
+ * coarse problem's blocks with them) while dt and the mass term stay the same: the blocks
+ * then belong to d_h of the step that built them (a lagged preconditioner).  A step whose
+ * Krylov iterations exceed 1.5 times those of the building step plus 4 ends the reuse
+ * (the next step builds).  The answer does not depend on it beyond the tolerance;
+ * festung_step_info.precond_built tells which steps built.  max_steps = 1 (the default):
+ * every step builds its own.  EINVAL if max_steps < 1.  The paper has no counterpart: it
+ * solves directly. */
+int festung_set_precond_reuse(festung_ctx *ctx, int max_steps);
 
 /* Free the context and all its device memory.  NULL is a no-op. */
 void festung_destroy(festung_ctx *ctx);

@@ -1397,21 +1397,33 @@ int prepare_solve(festung_ctx *c, double dt, bool stationary, bool mixed) {
     FCK(cudaGetLastError());
     // block-Jacobi preconditioner: inverse diagonal blocks of S for this D and dt, built on
     // a second stream while this one forms the guess and the first residual
-    // (finish_precond joins it)
-    if (!w.P) FCK(cudaMalloc(&w.P, (size_t)c->N * c->N * c->K * sizeof(float)));
-    if (!w.Pb) FCK(cudaMalloc(&w.Pb, (size_t)((c->N * c->N + 7) / 8) * c->K * 16));
-    if (!c->side) {
-        FCK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
-        FCK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
-        FCK(cudaEventCreateWithFlags(&c->ev_P, cudaEventDisableTiming));
+    // (finish_precond joins it).  With festung_set_precond_reuse the blocks of an earlier
+    // step serve while dt and the mass term are unchanged, the build is younger than the
+    // reuse bound and the Krylov iterations have not grown much since the build (a lagged
+    // preconditioner: S changes with D from step to step, the answer does not depend on P).
+    c->P_built = !c->P_valid || c->P_dt != dt || c->P_mass != c->mass || c->P_age >= c->precond_reuse;
+    if (c->P_built) {
+        if (!w.P) FCK(cudaMalloc(&w.P, (size_t)c->N * c->N * c->K * sizeof(float)));
+        if (!w.Pb) FCK(cudaMalloc(&w.Pb, (size_t)((c->N * c->N + 7) / 8) * c->K * 16));
+        if (!c->side) {
+            FCK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+            FCK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+            FCK(cudaEventCreateWithFlags(&c->ev_P, cudaEventDisableTiming));
+        }
+        FCK(cudaEventRecord(c->ev_in, st));
+        FCK(cudaStreamWaitEvent(c->side, c->ev_in, 0));
+        FCK(cudaMemsetAsync(w.d_flags, 0, sizeof(int), c->side));
+        launch_blockjacobi(c, w.P, w.Pb, dt, w.d_flags, c->side);
+        FCK(cudaGetLastError());
+        FCK(cudaEventRecord(c->ev_P, c->side));
+        c->P_pending = true;
+        c->P_valid = true;
+        c->P_dt = dt;
+        c->P_mass = c->mass;
+        c->P_age = 0;
+        c->P_iters0 = -1;
     }
-    FCK(cudaEventRecord(c->ev_in, st));
-    FCK(cudaStreamWaitEvent(c->side, c->ev_in, 0));
-    FCK(cudaMemsetAsync(w.d_flags, 0, sizeof(int), c->side));
-    launch_blockjacobi(c, w.P, w.Pb, dt, w.d_flags, c->side);
-    FCK(cudaGetLastError());
-    FCK(cudaEventRecord(c->ev_P, c->side));
-    c->P_pending = true;
+    ++c->P_age;
     // initial guess: C^n plus a correction given with festung_set_guess, else
     // extrapolation in time from the previous states when they exist, else C^n (the
     // result does not depend on it beyond the tolerance)
@@ -1506,6 +1518,10 @@ int prepare_coarse(festung_ctx *c, double dt) {
     const int64_t K3 = 3 * c->K;
     k_commit_coeff<<<small_grid(K3, c), 256, 0, st>>>(K3, c->dD, cc->dD, cc->fD); ++c->launches;
     cc->xD_valid = false;
+    // the coarse blocks are rebuilt with the fine ones (festung_set_precond_reuse)
+    if (w.P && !c->P_built && cc->P_dt == dt && cc->P_mass == c->mass) return FESTUNG_OK;
+    cc->P_dt = dt;
+    cc->P_mass = c->mass;
     if (!w.P) FCK(cudaMalloc(&w.P, (size_t)9 * cc->K * sizeof(float)));
     if (!w.Pb) FCK(cudaMalloc(&w.Pb, (size_t)((9 + 7) / 8) * cc->K * 16));
     FCK(cudaMemsetAsync(w.d_flags, 0, sizeof(int), st));
@@ -1689,6 +1705,14 @@ int solve_system(festung_ctx *c, double dt, double mass, const festung_step_opts
         info->fp64_iterations = iters64;
         info->initial_rel_residual = relres0;
         info->coarse_iterations = coarse_iters;
+        info->precond_built = c->P_built ? 1 : 0;
+    }
+    // a step that needed many more iterations than the one that built the blocks ends
+    // their reuse
+    if (c->P_built) {
+        c->P_iters0 = iters;
+    } else if (c->P_iters0 >= 0 && 2 * iters > 3 * c->P_iters0 + 8) {
+        c->P_valid = false;
     }
     if (!conv) {
         char msg[96];
@@ -1809,6 +1833,7 @@ int festung_warmstart_features(festung_ctx *c, double dt, float *X, float *Wt, d
         if (!w.P) FCK(cudaMalloc(&w.P, (size_t)c->N * c->N * c->K * sizeof(float)));
         if (!w.Pb) FCK(cudaMalloc(&w.Pb, (size_t)((c->N * c->N + 7) / 8) * c->K * 16));
         launch_blockjacobi(c, w.P, w.Pb, dt, w.d_flags, st);
+        c->P_valid = false;  // the step's own build replaces them
         k_ws_weights<<<small_grid(K, c), 256, 0, st>>>(K, c->N, w.P, c->dB, Wt);
         ++c->launches;
     }
@@ -1861,6 +1886,7 @@ int festung_precond_blocks(festung_ctx *c, double dt, double *blocks, double *in
     cudaStream_t st = c->stream;
     FCK(cudaMemsetAsync(w.d_flags, 0, sizeof(int), st));
     launch_blockjacobi(c, w.P, w.Pb, dt, w.d_flags, st);
+    c->P_valid = false;  // the next step builds its own
     FCK(cudaGetLastError());
     std::vector<float> hP(blocks ? (size_t)N * N * K : 0);
     std::vector<uint16_t> hB(inverse ? (size_t)NQ * K * 8 : 0);
@@ -1904,6 +1930,16 @@ int festung_set_stream(festung_ctx *c, void *stream) {
 const char *festung_last_error(const festung_ctx *c) {
     if (!c) return g_create_err.c_str();
     return c->err.c_str();
+}
+
+int festung_set_precond_reuse(festung_ctx *c, int max_steps) {
+    if (!c) return FESTUNG_EINVAL;
+    if (max_steps < 1) {
+        c->err = "max_steps must be >= 1";
+        return FESTUNG_EINVAL;
+    }
+    c->precond_reuse = max_steps;
+    return FESTUNG_OK;
 }
 
 int festung_set_coarse(festung_ctx *c, int enable) {
@@ -2535,6 +2571,8 @@ int solve_group(festung_batch *b, BatchGroup &g, double dt, const festung_step_o
         in.symmetric = c->symmetric ? 1 : 0;
         in.fp64_iterations = 0;
         in.initial_rel_residual = rel0[m];
+        in.coarse_iterations = 0;
+        in.precond_built = c->P_built ? 1 : 0;
     }
     // the members left over: their own step from C^n (still in the member context), with
     // the FP64 fallback of the single-problem path

@@ -156,6 +156,13 @@ struct festung_ctx {
     cudaStream_t side = nullptr;         // the preconditioner build overlaps the right-hand side and residual
     cudaEvent_t ev_in = nullptr, ev_P = nullptr;
     bool P_pending = false;              // the block-Jacobi build runs on `side` until ev_P
+    // reuse of the block-Jacobi blocks over steps (festung_set_precond_reuse)
+    int precond_reuse = 1;     // steps one build serves at most (1: every step builds its own)
+    bool P_valid = false;      // w.P / w.Pb hold blocks of S for P_dt and P_mass
+    double P_dt = 0.0, P_mass = -1.0;
+    int P_age = 0;             // steps served by the current blocks
+    int P_iters0 = -1;         // Krylov iterations of the step that built them
+    bool P_built = false;      // the current step built its blocks
     int num_sms = 0;
     mutable int64_t launches = 0;  // kernels launched on behalf of this context (graph nodes counted)
     std::string err;

@@ -27,6 +27,7 @@ EXPORTS = [
     "festung_element_order", "festung_precond_blocks", "festung_launch_count", "festung_set_stream",
     "festung_last_error", "festung_destroy",
     "festung_autotune", "festung_fma_peak", "festung_warmstart_features", "festung_set_guess", "festung_set_coarse",
+    "festung_set_precond_reuse",
     "festung_mlp_create", "festung_mlp_sizes", "festung_mlp_set_stream", "festung_mlp_forward", "festung_mlp_grad",
     "festung_mlp_adam", "festung_mlp_get", "festung_mlp_set", "festung_mlp_last_error", "festung_mlp_destroy",
     "festung_batch_create", "festung_batch_set_stream", "festung_batch_set_mode", "festung_batch_step",
@@ -43,7 +44,8 @@ class StepOpts(ctypes.Structure):
 class StepInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("outer", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("solver", ctypes.c_int), ("symmetric", ctypes.c_int), ("fp64_iterations", ctypes.c_int),
-                ("initial_rel_residual", ctypes.c_double), ("coarse_iterations", ctypes.c_int)]
+                ("initial_rel_residual", ctypes.c_double), ("coarse_iterations", ctypes.c_int),
+                ("precond_built", ctypes.c_int)]
 
 
 class FestungError(RuntimeError):
@@ -94,6 +96,7 @@ def load(path=None):
     lib.festung_warmstart_features.argtypes = [vp, dbl, vp, vp, ctypes.POINTER(dbl)]
     lib.festung_set_guess.argtypes = [vp, vp, cint]
     lib.festung_set_coarse.argtypes = [vp, cint]
+    lib.festung_set_precond_reuse.argtypes = [vp, cint]
     lib.festung_mlp_create.argtypes = [cint, cint, ctypes.c_uint64, ctypes.POINTER(vp)]
     lib.festung_mlp_sizes.argtypes = [vp, ctypes.POINTER(cint), ctypes.POINTER(cint), ctypes.POINTER(cint)]
     lib.festung_mlp_set_stream.argtypes = [vp, vp]
@@ -228,7 +231,8 @@ class Solver:
         self._check(self.lib.festung_step(self.h, dt, ctypes.byref(o), ctypes.byref(info)))
         return {"iterations": info.iterations, "outer": info.outer, "rel_residual": info.rel_residual,
                 "solver": info.solver, "symmetric": info.symmetric, "fp64_iterations": info.fp64_iterations,
-                "initial_rel_residual": info.initial_rel_residual, "coarse_iterations": info.coarse_iterations}
+                "initial_rel_residual": info.initial_rel_residual, "coarse_iterations": info.coarse_iterations,
+                "precond_built": info.precond_built}
 
     def element_order(self):
         """order[i] = caller's index of the triangle at position i of the device layout."""
@@ -257,7 +261,13 @@ class Solver:
         self._check(self.lib.festung_solve_stationary(self.h, ctypes.byref(o), ctypes.byref(info)))
         return {"iterations": info.iterations, "outer": info.outer, "rel_residual": info.rel_residual,
                 "solver": info.solver, "symmetric": info.symmetric, "fp64_iterations": info.fp64_iterations,
-                "initial_rel_residual": info.initial_rel_residual, "coarse_iterations": info.coarse_iterations}
+                "initial_rel_residual": info.initial_rel_residual, "coarse_iterations": info.coarse_iterations,
+                "precond_built": info.precond_built}
+
+    def set_precond_reuse(self, max_steps):
+        """One block-Jacobi build serves up to max_steps steps (festung_set_precond_reuse)."""
+        self._check(self.lib.festung_set_precond_reuse(self.h, int(max_steps)))
+        return self
 
     def set_coarse(self, enable=True):
         """Start every FP32 sweep from a coarse (p = 1) correction (festung_set_coarse)."""
@@ -300,7 +310,8 @@ class Solver:
 def _info_dict(info):
     return {"iterations": info.iterations, "outer": info.outer, "rel_residual": info.rel_residual,
             "solver": info.solver, "symmetric": info.symmetric, "fp64_iterations": info.fp64_iterations,
-            "initial_rel_residual": info.initial_rel_residual, "coarse_iterations": info.coarse_iterations}
+            "initial_rel_residual": info.initial_rel_residual, "coarse_iterations": info.coarse_iterations,
+                "precond_built": info.precond_built}
 
 
 class Batch:
