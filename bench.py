@@ -253,6 +253,7 @@ def run_festung(args):
     if args.coarse:
         s.set_coarse(True)
     s.set_precond_reuse(args.precond_reuse)
+    s.set_persistent(bool(args.persistent))
     stream = torch.cuda.current_stream()
     s.set_stream(stream)
     K, N = s.K, s.N
@@ -460,7 +461,7 @@ def run_festung(args):
                    "precision": "FP32 inner Krylov (each sweep started from a p = 1 coarse correction when "
                                 "coarse_correction is true); refinement on double-float (48-bit) residuals; FP64 "
                                 "state and right-hand side", "l2": "flushed between steps",
-                   "coarse_correction": bool(args.coarse), "precond_reuse": args.precond_reuse,
+                   "coarse_correction": bool(args.coarse), "precond_reuse": args.precond_reuse, "persistent": args.persistent,
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "iterations_per_step": float(np.mean([i["iterations"] for i in infos])),
         "outer_per_step": float(np.mean([i["outer"] for i in infos])),
@@ -571,6 +572,7 @@ def profile_step(args):
     if args.coarse:
         s.set_coarse(True)
     s.set_precond_reuse(args.precond_reuse)
+    s.set_persistent(bool(args.persistent))
     stream = torch.cuda.current_stream()
     s.set_stream(stream)
     xy, _ = s.quad_points()
@@ -592,7 +594,7 @@ def profile_step(args):
             infos.append(info)
             ts.append(a.elapsed_time(b) / 1e3)
     s.close()
-    return {"profile_step": CFG_NAME, "coarse": args.coarse, "precond_reuse": args.precond_reuse, "steps": args.steps, "warmup": args.warmup,
+    return {"profile_step": CFG_NAME, "coarse": args.coarse, "precond_reuse": args.precond_reuse, "persistent": args.persistent, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * float(np.mean(ts)),
             "iterations": [i["iterations"] for i in infos], "coarse_iterations": [i["coarse_iterations"] for i in infos],
             "outer": [i["outer"] for i in infos], "precond_built": [i["precond_built"] for i in infos]}
@@ -885,6 +887,7 @@ def run_grf_step(args):
     if args.coarse:
         s.set_coarse(True)
     s.set_precond_reuse(args.precond_reuse)
+    s.set_persistent(bool(args.persistent))
     stream = torch.cuda.current_stream()
     s.set_stream(stream)
     K, N = s.K, s.N
@@ -956,6 +959,8 @@ def main():
     ap.add_argument("--skip-big", action="store_true", help="skip the 2M-triangle apply measurement")
     ap.add_argument("--skip-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--coarse", type=int, default=1, help="FP32 sweeps start from a p = 1 coarse correction (1) or not (0)")
+    ap.add_argument("--persistent", type=int, default=1,
+                    help="FP32 BiCGStab at p <= 1 (the coarse solves) as one persistent kernel (1) or a graph (0)")
     ap.add_argument("--precond-reuse", type=int, default=8,
                     help="one block-Jacobi build serves up to this many steps (1: every step builds)")
     ap.add_argument("--profile-apply", default=None, metavar="WORKLOAD",

@@ -372,6 +372,17 @@ const char *festung_last_error(const festung_ctx *ctx);
  * no counterpart: it solves directly. */
 int festung_set_coarse(festung_ctx *ctx, int enable);
 
+/* How the BiCGStab iterations of the FP32 solves run at p <= 1 (the inner sweeps of a
+ * p <= 1 context, and the coarse problem of festung_set_coarse).  enable = 1 (the
+ * default): one persistent cooperative kernel per solve, whose blocks each keep their
+ * tiles of the mesh and meet at grid-wide barriers between the four phases of an
+ * iteration; its reductions are summed in double-float arithmetic by every block in the
+ * same order.  enable = 0: the CUDA graph of four kernels per iteration (the form used at
+ * p >= 2).  Both iterate the same method; their sums are rounded differently.  A device
+ * that cannot hold the persistent grid falls back to the graph.  EINVAL unless enable is
+ * 0 or 1. */
+int festung_set_persistent(festung_ctx *ctx, int enable);
+
 /* Reuse of the block-Jacobi preconditioner over time steps.  Every step solves with the
  * inverse diagonal blocks of S; they depend on d_h, dt and the mass term and cost about as
  * much to build as a few Krylov iterations.  With max_steps = m > 1 one build serves up

@@ -75,6 +75,12 @@ struct Workspace {
     dfloat *xdf = nullptr, *ydf = nullptr;    // N x K double-float operand and result of the residual apply
     int *loopctl = nullptr;    // device: chunks run by the Krylov graph's loop, and their bound
     int *h_loopctl = nullptr;  // pinned host mirror of loopctl[0]
+    // persistent BiCGStab kernel (bicg_persist.cu): partials, grid-barrier counters, flag
+    float *ppart = nullptr;
+    void *pscal = nullptr;  // 256 bytes: the persistent kernel's scalars
+    int pcap = 0;
+    unsigned int *pbar = nullptr;
+    int *perr = nullptr, *h_perr = nullptr;
     bool use_P = false;        // P is valid for the current step
     GraphCache g64, g32;
 };
@@ -469,6 +475,14 @@ int ensure_ws(festung_ctx *c) {
         FCK(cudaMallocHost(&w.h_flags, sizeof(int) * 4));
         FCK(cudaMalloc(&w.loopctl, sizeof(int) * 2));
         FCK(cudaMallocHost(&w.h_loopctl, sizeof(int)));
+        if (bicg_persistent_supported(c)) {
+            w.pcap = (int)std::min<int64_t>(tiles, 1 << 20);
+            FCK(cudaMalloc(&w.ppart, sizeof(float) * 6 * (size_t)w.pcap));
+            FCK(cudaMalloc(&w.pscal, 256));
+            FCK(cudaMalloc(&w.pbar, sizeof(unsigned int) * 2));
+            FCK(cudaMalloc(&w.perr, sizeof(int)));
+            FCK(cudaMallocHost(&w.h_perr, sizeof(int)));
+        }
     }
     return FESTUNG_OK;
 }
@@ -506,6 +520,11 @@ void free_ctx_device(festung_ctx *c) {
         if (c->ws->ydf) cudaFree(c->ws->ydf);
         if (c->ws->loopctl) cudaFree(c->ws->loopctl);
         if (c->ws->h_loopctl) cudaFreeHost(c->ws->h_loopctl);
+        if (c->ws->ppart) cudaFree(c->ws->ppart);
+        if (c->ws->pscal) cudaFree(c->ws->pscal);
+        if (c->ws->pbar) cudaFree(c->ws->pbar);
+        if (c->ws->perr) cudaFree(c->ws->perr);
+        if (c->ws->h_perr) cudaFreeHost(c->ws->h_perr);
         delete c->ws;
         c->ws = nullptr;
     }
@@ -730,10 +749,15 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
             c->launches += 2;
         }
         FCK(cudaGetLastError());
-        // build (or reuse) the graph: while (not done and under the bound) { CHUNK iterations }
+        // FP32 BiCGStab at p <= 1: the iterations as one persistent kernel (bicg_persist.cu)
+        bool persistent = std::is_same<T, float>::value && solver == FESTUNG_SOLVER_BICGSTAB && c->persistent &&
+                          w.ppart && bicg_persistent_supported(c);
+        // else build (or reuse) the graph: while (not done and under the bound) { CHUNK iterations }
         GraphCache &gc = graph_of<T>(c);
-        if (!gc.exec || gc.solver != solver || gc.tau != tau || gc.use_P != (int)w.use_P || gc.mass != c->mass ||
-            gc.tab_bf16 != (int)c->tab_bf16) {
+        auto build_graph = [&]() -> int {
+            if (gc.exec && gc.solver == solver && gc.tau == tau && gc.use_P == (int)w.use_P && gc.mass == c->mass &&
+                gc.tab_bf16 == (int)c->tab_bf16)
+                return FESTUNG_OK;
             if (gc.exec) cudaGraphExecDestroy(gc.exec);
             gc.exec = nullptr;
             cudaGraph_t graph;
@@ -772,7 +796,10 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
             gc.use_P = (int)w.use_P;
             gc.mass = c->mass;
             gc.tab_bf16 = (int)c->tab_bf16;
-        }
+            return FESTUNG_OK;
+        };
+        int rc = persistent ? FESTUNG_OK : build_graph();
+        if (rc) return rc;
         bool brk = false, drift = false;
         while (true) {
             FCK(cudaMemcpyAsync(w.h_scal, w.scal, sizeof(KScal), cudaMemcpyDeviceToHost, st));
@@ -820,6 +847,31 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
                 *b2 = h.b2;
                 *iters = total;
                 return FESTUNG_OK;
+            }
+            if (persistent) {
+                if constexpr (std::is_same<T, float>::value) {
+                    // Z1, Z2 (not used by the fused applies) serve as the second p and v buffers
+                    const BicgVecs32 bv{V.x, V.r, V.p, V.v, V.ph, V.s, V.sh, V.t, V.Z1, V.Z2, V.r0, V.inv};
+                    const cudaError_t e = launch_bicg_persistent(c, bv, w.use_P ? w.Pb : nullptr, (float)tau, w.scal,
+                                                                 w.pscal, w.ppart, w.pcap, w.pbar, w.perr, max_iter - total, st);
+                    if (e == cudaErrorNotSupported || e == cudaErrorCooperativeLaunchTooLarge) {
+                        // the device cannot hold the grid: this context keeps to the graph
+                        (void)cudaGetLastError();
+                        persistent = false;
+                        c->persistent = false;
+                        if ((rc = build_graph())) return rc;
+                        continue;
+                    }
+                    FCK(e);
+                    ++c->launches;
+                    FCK(cudaMemcpyAsync(w.h_perr, w.perr, sizeof(int), cudaMemcpyDeviceToHost, st));
+                    FCK(cudaStreamSynchronize(st));
+                    if (*w.h_perr) {
+                        c->err = "persistent BiCGStab kernel: a grid barrier wait gave up";
+                        return FESTUNG_ECUDA;
+                    }
+                }
+                continue;
             }
             const int max_chunks = std::max(1, (max_iter - total - h.iter + CHUNK - 1) / CHUNK);
             k_loop_init<<<1, 1, 0, st>>>(w.loopctl, max_chunks); ++c->launches;
@@ -1509,6 +1561,7 @@ int prepare_coarse(festung_ctx *c, double dt) {
     }
     festung_ctx *cc = c->coarse;
     cc->stream = st;
+    cc->persistent = c->persistent;
     cc->mass = c->mass;
     cc->symmetric = c->symmetric;
     int rc = ensure_ws(cc);
@@ -1930,6 +1983,17 @@ int festung_set_stream(festung_ctx *c, void *stream) {
 const char *festung_last_error(const festung_ctx *c) {
     if (!c) return g_create_err.c_str();
     return c->err.c_str();
+}
+
+int festung_set_persistent(festung_ctx *c, int enable) {
+    if (!c) return FESTUNG_EINVAL;
+    if (enable != 0 && enable != 1) {
+        c->err = "enable must be 0 or 1";
+        return FESTUNG_EINVAL;
+    }
+    c->persistent = enable != 0;
+    if (c->coarse) c->coarse->persistent = c->persistent;
+    return FESTUNG_OK;
 }
 
 int festung_set_precond_reuse(festung_ctx *c, int max_steps) {

@@ -216,12 +216,52 @@ __device__ __forceinline__ void slot_xtraces(const T (&x)[N], T *tr, int NS, int
     store_trace<T, N, R2, R1, TK, 2>(x, tr, 0, NS, slot);
 }
 
+// Where the apply takes the x values of triangles: LoadX reads the N x K vector X (CG:
+// through L2, see ldv).  A source has first(e, slot, x), called once per slot in phase
+// A1 (slot: the triangle's slot in this block's tile and halo), get(e, slot, x) for a
+// slot's later reads and for a neighbour outside tile and halo (slot -1), and comp(e, j)
+// for one coefficient (the rolled loops of the double-float kernels).
+template <typename T, int N, bool CG>
+struct LoadX {
+    const T *X;
+    int Ki;
+    __device__ __forceinline__ void first(int e, int, T (&x)[N]) const { get(e, -1, x); }
+    __device__ __forceinline__ void get(int e, int, T (&x)[N]) const {
+#pragma unroll
+        for (int j = 0; j < N; ++j) x[j] = ldv<CG>(X + j * Ki + e);
+    }
+    __device__ __forceinline__ T comp(int e, int j) const { return ldv<CG>(X + j * Ki + e); }
+};
+
+// trace_nbr with the neighbour's x from a source
+template <typename T, int N, int R1, typename XS>
+__device__ __forceinline__ void trace_nbr_src(const T *phiE, const XS &xs, int k2, int n2, T (&out)[R1]) {
+#pragma unroll
+    for (int r = 0; r < R1; ++r) out[r] = T(0);
+    if constexpr (kCompactCode<T>) {
+#pragma unroll 1
+        for (int j = 0; j < N; ++j) {
+            const T v = xs.comp(k2, j);
+#pragma unroll
+            for (int r = 0; r < R1; ++r) out[r] += phiE[(n2 * R1 + (R1 - 1 - r)) * N + j] * v;
+        }
+    } else {
+        T v[N];
+        xs.get(k2, -1, v);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+#pragma unroll
+            for (int r = 0; r < R1; ++r) out[r] += phiE[(n2 * R1 + (R1 - 1 - r)) * N + j] * v[j];
+        }
+    }
+}
+
 // Central value {x} of the edge at our Gauss point r: the mean of our trace and the
 // neighbour's, taken at its point R1 - 1 - r (the maps of eq. mapEE reverse the edge);
 // our own trace on a Neumann edge (eq. globQm:N).  The neighbour's trace comes from its
 // slot, or from global memory when the neighbour of a halo triangle has no slot (nsl = -2).
-template <typename T, int N, int R2, int R1, int TK, int n>
-__device__ __forceinline__ void edge_mean(const T *phiE_s, const T *__restrict__ X, int Ki, int code, int nsl,
+template <typename T, int N, int R2, int R1, int TK, int n, typename XS>
+__device__ __forceinline__ void edge_mean(const T *phiE_s, const XS &xs, int code, int nsl,
                                           const T *tr, int NS, int slot, T (&f)[R1]) {
     tr_load<T, R1>(tr, 0, n, slot, NS, f);
     if (code >= 0) {
@@ -232,7 +272,7 @@ __device__ __forceinline__ void edge_mean(const T *phiE_s, const T *__restrict__
 #pragma unroll
             for (int r = 0; r < R1; ++r) cp[r] = nb[R1 - 1 - r];
         } else {
-            trace_nbr<T, N, R1>(phiE_s, X, (int64_t)Ki, code >> 2, code & 3, cp);
+            trace_nbr_src<T, N, R1>(phiE_s, xs, code >> 2, code & 3, cp);
         }
 #pragma unroll
         for (int r = 0; r < R1; ++r) f[r] = T(0.5) * (f[r] + cp[r]);
@@ -320,8 +360,8 @@ __device__ __forceinline__ void store_sigma(const T (&d)[N], const T (&z1)[N], c
 //   P = u^_1 - e_0 + e_1,  Q = u^_2 - e_0 + e_2,
 // so that B enters through G and det B alone.  nsl[n]: slot of the neighbour across
 // edge n (see edge_mean).
-template <typename T, int N, int R2, int R1, int TK>
-__device__ __forceinline__ void slot_zeta(const T *phiE_s, const T *__restrict__ X, int Ki, int e, const T (&x)[N],
+template <typename T, int N, int R2, int R1, int TK, typename XS>
+__device__ __forceinline__ void slot_zeta(const T *phiE_s, const XS &xs, int e, const T (&x)[N],
                                           const T (&d)[N], const T (&bk)[4], const int (&code)[3],
                                           const int (&nsl)[3], T *tr, int NS, int slot, T (&z1)[N], T (&z2)[N]) {
     const CTab<T, N, R2, R1> &t = tab_ref<T, N, R2, R1, TK>();
@@ -331,7 +371,7 @@ __device__ __forceinline__ void slot_zeta(const T *phiE_s, const T *__restrict__
         for (int i = 0; i < N; ++i) z1[i] = z2[i] = T(0);
 #pragma unroll 1
         for (int j = 0; j < N; ++j) {
-            const T xj = X[j * Ki + e];
+            const T xj = xs.comp(e, j);
 #pragma unroll
             for (int i = 0; i < N; ++i) {
                 if (j < nbelow(i)) {
@@ -357,15 +397,15 @@ __device__ __forceinline__ void slot_zeta(const T *phiE_s, const T *__restrict__
     {
         T f[R1];
         if (c0 != NBR_DIRICHLET) {
-            edge_mean<T, N, R2, R1, TK, 0>(phiE_s, X, Ki, c0, nsl[0], tr, NS, slot, f);
+            edge_mean<T, N, R2, R1, TK, 0>(phiE_s, xs, c0, nsl[0], tr, NS, slot, f);
             edge_test_add<T, N, R2, R1, TK, 0>(f, z1, z2, 0);
         }
         if (c1 != NBR_DIRICHLET) {
-            edge_mean<T, N, R2, R1, TK, 1>(phiE_s, X, Ki, c1, nsl[1], tr, NS, slot, f);
+            edge_mean<T, N, R2, R1, TK, 1>(phiE_s, xs, c1, nsl[1], tr, NS, slot, f);
             edge_test_add<T, N, R2, R1, TK, 1>(f, z1, z2, 1);
         }
         if (c2 != NBR_DIRICHLET) {
-            edge_mean<T, N, R2, R1, TK, 2>(phiE_s, X, Ki, c2, nsl[2], tr, NS, slot, f);
+            edge_mean<T, N, R2, R1, TK, 2>(phiE_s, xs, c2, nsl[2], tr, NS, slot, f);
             edge_test_add<T, N, R2, R1, TK, 2>(f, z1, z2, 2);
         }
     }
@@ -544,17 +584,21 @@ bool allow_max_smem(Kern kernel) {
                                 optin - (int)fa.sharedSizeBytes) == cudaSuccess;
 }
 
-// EPI: reductions fused into the end of the apply (FUSED_EPI_* in krylov.cuh; one
-// partial per block, the last block updates the scalars); e1, e2: r0 (ALPHA); s, r0
-// (OMEGA).
-template <typename T, int N, int R2, int R1, int EPI = FUSED_EPI_NONE, int TK = 0>
-__global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_apply_fused(
-    const T *__restrict__ X, T *__restrict__ Y, const T *__restrict__ Dc, const T *__restrict__ Bg,
+// One tile of y = S x: phases A1, A2 and B by the block's threads (a tile of TE triangles,
+// the threads past TE for its halo), x from the source xs (LoadX: a vector).
+// EPI != FUSED_EPI_NONE adds the tile's part of the epilogue's dot products to dots: e1,
+// e2 are r0 (ALPHA); s, r0 (OMEGA).  CG: e1 and e2 are read through L2 (ld.global.cg),
+// for a persistent kernel whose other blocks write them between its phases; a block
+// that runs several tiles in a row must call this between two block barriers.  Returns
+// the number of the tile's triangles it applied (0 for a batch tile whose problems are
+// all done).
+template <typename T, int N, int R2, int R1, int EPI, int TK, bool CG, typename XS>
+__device__ __forceinline__ int fused_tile(
+    int tile, const XS &xs, T *__restrict__ Y, const T *__restrict__ Dc, const T *__restrict__ Bg,
     const int32_t *__restrict__ nbr, const int16_t *__restrict__ slotg, const int32_t *__restrict__ halo_ptr,
-    const int32_t *__restrict__ halo, const int16_t *__restrict__ halo_slot, int64_t K, int TE, int NS, T tau,
-    T eta, T mass, const T *__restrict__ tabg, const int *__restrict__ skip, const T *__restrict__ e1 = nullptr,
-    const T *__restrict__ e2 = nullptr, double *part = nullptr, KScal *sc = nullptr,
-    unsigned int *counter = nullptr, BatchView bv = BatchView()) {
+    const int32_t *__restrict__ halo, const int16_t *__restrict__ halo_slot, int Ki, int TE, int NS, T tau, T eta,
+    T mass, const T *__restrict__ tabg, const T *__restrict__ e1, const T *__restrict__ e2, const KScal *sc,
+    const BatchView &bv, Acc<T> (&dots)[EPI == FUSED_EPI_OMEGA ? 4 : 1]) {
     // FP32: the volume loop is unrolled with immediate table operands at every order (on
     // 131,072 triangles at p = 4: 29.6 us, against 34.9 us with the tables read from
     // shared memory in a rolled loop); FP64 and double-float keep the rolled loop at
@@ -568,8 +612,6 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
     __shared__ __align__(16) T vol_s[VOL];
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     T *tr = reinterpret_cast<T *>(dyn_smem);
-    if (skip && *skip) return;
-    const int Ki = (int)K;  // K * N < 2^31 (checked at setup): 32-bit offsets
     if constexpr (kTC) {
         const CTab<T, N, R2, R1> &ct = tab_ref<T, N, R2, R1, TK>();
         tc_fill_tables<N, R2>(tc_s, ct.phiQ, ct.gw1, ct.gw2);
@@ -587,10 +629,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
             }
         }
     }
-    const int start = blockIdx.x * TE;
+    const int start = tile * TE;
     int cnt = (Ki - start) < TE ? (Ki - start) : TE;
-    const int h0 = halo_ptr[blockIdx.x];
-    int nh = halo_ptr[blockIdx.x + 1] - h0;
+    const int h0 = halo_ptr[tile];
+    int nh = halo_ptr[tile + 1] - h0;
     if constexpr (EPI != FUSED_EPI_NONE) {
         if (bv.eprob && cnt > 0) {
             // a batch: a tile whose problems have all finished their iterations does no
@@ -603,7 +645,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
     const int i = threadIdx.x;
     const int hstride = blockDim.x - TE;
     T z1[N], z2[N], d[N];
-    if constexpr (EPI != FUSED_EPI_NONE) {
+    if constexpr (EPI != FUSED_EPI_NONE && !CG) {
         // the epilogue's vectors: start their loads into L1 now, so that their latency
         // hides behind phases A and B
         if (i < cnt) {
@@ -622,18 +664,15 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
             const int k = start + i;
             T xa[N];
 #pragma unroll
-            for (int j = 0; j < N; ++j) {
-                xa[j] = X[j * Ki + k];
-                d[j] = Dc[j * Ki + k];
-            }
+            for (int j = 0; j < N; ++j) d[j] = Dc[j * Ki + k];
+            xs.first(k, i, xa);
             slot_xtraces<T, N, R2, R1, TK>(xa, tr, NS, i);
         }
     } else {
         for (int j = i - TE; j < nh; j += hstride) {
             const int eh = halo[h0 + j];
             T xh[N];
-#pragma unroll
-            for (int l = 0; l < N; ++l) xh[l] = X[l * Ki + eh];
+            xs.first(eh, TE + j, xh);
             slot_xtraces<T, N, R2, R1, TK>(xh, tr, NS, TE + j);
         }
     }
@@ -644,14 +683,13 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
             const int k = start + i;
             T xa[N], ba[4];
             int ca[3];
-#pragma unroll
-            for (int j = 0; j < N; ++j) xa[j] = X[j * Ki + k];
+            xs.get(k, i, xa);
 #pragma unroll
             for (int q = 0; q < 4; ++q) ba[q] = Bg[q * Ki + k];
 #pragma unroll
             for (int n = 0; n < 3; ++n) ca[n] = nbr[n * Ki + k];
             const int sa[3] = {slotg[k], slotg[Ki + k], slotg[2 * Ki + k]};
-            slot_zeta<T, N, R2, R1, TK>(phiE_s, X, Ki, k, xa, d, ba, ca, sa, tr, NS, i, z1, z2);
+            slot_zeta<T, N, R2, R1, TK>(phiE_s, xs, k, xa, d, ba, ca, sa, tr, NS, i, z1, z2);
         }
         if constexpr (kTC) {
             // the volume operands go to the warp's stage now, so that their registers are
@@ -668,24 +706,18 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
             T xh[N], hd[N], hb[4], hz1[N], hz2[N];
             int hc[3];
             const int hs[3] = {halo_slot[q], halo_slot[q + 1], halo_slot[q + 2]};
+            xs.get(eh, TE + j, xh);
 #pragma unroll
-            for (int l = 0; l < N; ++l) {
-                xh[l] = X[l * Ki + eh];
-                hd[l] = Dc[l * Ki + eh];
-            }
+            for (int l = 0; l < N; ++l) hd[l] = Dc[l * Ki + eh];
 #pragma unroll
             for (int l = 0; l < 4; ++l) hb[l] = Bg[l * Ki + eh];
 #pragma unroll
             for (int n = 0; n < 3; ++n) hc[n] = nbr[n * Ki + eh];
-            slot_zeta<T, N, R2, R1, TK>(phiE_s, X, Ki, eh, xh, hd, hb, hc, hs, tr, NS, TE + j, hz1, hz2);
+            slot_zeta<T, N, R2, R1, TK>(phiE_s, xs, eh, xh, hd, hb, hc, hs, tr, NS, TE + j, hz1, hz2);
         }
     }
     __syncthreads();
     using A = Acc<T>;
-    constexpr int ND = EPI == FUSED_EPI_OMEGA ? 4 : 1;
-    A dots[ND];
-#pragma unroll
-    for (int q = 0; q < ND; ++q) dots[q] = A(0);
     T acc[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) acc[j] = T(0);
@@ -717,14 +749,16 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
 #pragma unroll
         for (int q = 0; q < 4; ++q) bk[q] = Bg[q * Ki + k];
         const T md = mass * (bk[0] * bk[3] - bk[1] * bk[2]);
+        T xo[N];
+        xs.get(k, i, xo);
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            const T yj = md * X[j * Ki + k] + tau * acc[j];
+            const T yj = md * xo[j] + tau * acc[j];
             Y[j * Ki + k] = yj;
             if constexpr (EPI == FUSED_EPI_ALPHA) {
-                dots[0] += (A)e1[j * Ki + k] * (A)yj;
+                dots[0] += (A)ldv<CG>(e1 + j * Ki + k) * (A)yj;
             } else if constexpr (EPI == FUSED_EPI_OMEGA) {
-                const A sj = (A)e1[j * Ki + k], rj = (A)e2[j * Ki + k];
+                const A sj = (A)ldv<CG>(e1 + j * Ki + k), rj = (A)ldv<CG>(e2 + j * Ki + k);
                 dots[0] += (A)yj * sj;
                 dots[1] += (A)yj * (A)yj;
                 dots[2] += rj * sj;
@@ -732,9 +766,35 @@ __global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_a
             }
         }
     }
+    return cnt;
+}
+
+// y = S x, one tile per block.  EPI: reductions fused into the end of the apply
+// (FUSED_EPI_* in krylov.cuh; one partial per block, the last block updates the
+// scalars); e1, e2: r0 (ALPHA); s, r0 (OMEGA).
+template <typename T, int N, int R2, int R1, int EPI = FUSED_EPI_NONE, int TK = 0>
+__global__ void __launch_bounds__(FUSED_THREADS, FusedOcc<T, N>::min_blocks) k_apply_fused(
+    const T *__restrict__ X, T *__restrict__ Y, const T *__restrict__ Dc, const T *__restrict__ Bg,
+    const int32_t *__restrict__ nbr, const int16_t *__restrict__ slotg, const int32_t *__restrict__ halo_ptr,
+    const int32_t *__restrict__ halo, const int16_t *__restrict__ halo_slot, int64_t K, int TE, int NS, T tau,
+    T eta, T mass, const T *__restrict__ tabg, const int *__restrict__ skip, const T *__restrict__ e1 = nullptr,
+    const T *__restrict__ e2 = nullptr, double *part = nullptr, KScal *sc = nullptr,
+    unsigned int *counter = nullptr, BatchView bv = BatchView()) {
+    if (skip && *skip) return;
+    using A = Acc<T>;
+    constexpr int ND = EPI == FUSED_EPI_OMEGA ? 4 : 1;
+    A dots[ND];
+#pragma unroll
+    for (int q = 0; q < ND; ++q) dots[q] = A(0);
+    // K * N < 2^31 (checked at setup): 32-bit offsets
+    const LoadX<T, N, false> xs{X, (int)K};
+    const int cnt = fused_tile<T, N, R2, R1, EPI, TK, false>(blockIdx.x, xs, Y, Dc, Bg, nbr, slotg, halo_ptr, halo, halo_slot,
+                                             (int)K, TE, NS, tau, eta, mass, tabg, e1, e2, sc, bv, dots);
     if constexpr (EPI != FUSED_EPI_NONE) {
         if (bv.eprob) {
             // a batch: sums per problem, scalars of every running problem in the last block
+            const int start = blockIdx.x * TE;
+            const int i = threadIdx.x;
             double dd[ND];
 #pragma unroll
             for (int q = 0; q < ND; ++q) dd[q] = (double)dots[q];

@@ -94,14 +94,24 @@ __device__ __forceinline__ void trace_own(const T *phiE, int n, const T (&c)[N],
 // Trace of the neighbour's field (global, N x K) on its edge n2, at the points that
 // coincide with our Gauss points: every edge-to-edge map reverses the orientation
 // (eq. mapEE), so our point r is the neighbour's point R1 - 1 - r.
-template <typename T, int N, int R1>
+// CG: load through L2 only (ld.global.cg), for vectors that other blocks of a persistent
+// kernel write between phases; otherwise the ordinary (possibly read-only cached) load.
+template <bool CG, typename T>
+__device__ __forceinline__ T ldv(const T *p) {
+    if constexpr (CG)
+        return __ldcg(p);
+    else
+        return *p;
+}
+
+template <typename T, int N, int R1, bool CG = false>
 __device__ __forceinline__ void trace_nbr(const T *phiE, const T *__restrict__ V, int64_t K, int64_t k2,
                                           int n2, T (&out)[R1]) {
 #pragma unroll
     for (int r = 0; r < R1; ++r) out[r] = T(0);
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-        const T v = V[j * K + k2];
+        const T v = ldv<CG>(V + j * K + k2);
 #pragma unroll
         for (int r = 0; r < R1; ++r) out[r] += phiE[(n2 * R1 + (R1 - 1 - r)) * N + j] * v;
     }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "dfloat.cuh"
 #include "krylov.cuh"
 
 namespace festung {
@@ -77,5 +78,28 @@ cudaError_t upload_tables_df(const festung_ctx *c);
 // is singular.
 void launch_blockjacobi(const festung_ctx *c, float *P, __nv_bfloat16 *Pinv, double tau, int *flags,
                         cudaStream_t st);
+
+// The vectors of an FP32 BiCGStab solve (N x K each; inv: 1 / (2|T_k|), length K); p2,
+// v2: second buffers of p and v for the persistent kernel, which alternates them.
+struct BicgVecs32 {
+    float *x, *r, *p, *v, *ph, *s, *sh, *t, *p2, *v2;
+    const float *r0, *inv;
+};
+
+// True if launch_bicg_persistent serves this context (p <= 1, FP32 tables).
+bool bicg_persistent_supported(const festung_ctx *c);
+
+// The BiCGStab iterations of an FP32 solve as one persistent cooperative kernel
+// (bicg_persist.cu): from the state in *sc (k_fin_init and the vectors r, r0, p, v set
+// up as for the graph of iterations) until the iteration is done or sc->iter reaches
+// max_iter; *sc is then left as that graph leaves it (an update owed to x when pending
+// or sconv is set); p and v are left in either buffer.  ps: 256 bytes of device memory
+// for the scalars while the kernel runs.  part: partials, 6 floats per
+// block of at most part_blocks blocks; bar: 2 counters and err: a flag (both zeroed
+// here) of the grid barrier; err ends up non-zero if a barrier wait gave up.  cudaErrorNotSupported: the context's
+// order or the device cannot run it (the caller uses the graph instead).
+cudaError_t launch_bicg_persistent(const festung_ctx *c, const BicgVecs32 &v, const __nv_bfloat16 *P, float tau,
+                                   KScal *sc, void *ps, float *part, int part_blocks, unsigned int *bar, int *err,
+                                   int max_iter, cudaStream_t st);
 
 }  // namespace festung

@@ -27,7 +27,7 @@ EXPORTS = [
     "festung_element_order", "festung_precond_blocks", "festung_launch_count", "festung_set_stream",
     "festung_last_error", "festung_destroy",
     "festung_autotune", "festung_fma_peak", "festung_warmstart_features", "festung_set_guess", "festung_set_coarse",
-    "festung_set_precond_reuse",
+    "festung_set_precond_reuse", "festung_set_persistent",
     "festung_mlp_create", "festung_mlp_sizes", "festung_mlp_set_stream", "festung_mlp_forward", "festung_mlp_grad",
     "festung_mlp_adam", "festung_mlp_get", "festung_mlp_set", "festung_mlp_last_error", "festung_mlp_destroy",
     "festung_batch_create", "festung_batch_set_stream", "festung_batch_set_mode", "festung_batch_step",
@@ -97,6 +97,7 @@ def load(path=None):
     lib.festung_set_guess.argtypes = [vp, vp, cint]
     lib.festung_set_coarse.argtypes = [vp, cint]
     lib.festung_set_precond_reuse.argtypes = [vp, cint]
+    lib.festung_set_persistent.argtypes = [vp, cint]
     lib.festung_mlp_create.argtypes = [cint, cint, ctypes.c_uint64, ctypes.POINTER(vp)]
     lib.festung_mlp_sizes.argtypes = [vp, ctypes.POINTER(cint), ctypes.POINTER(cint), ctypes.POINTER(cint)]
     lib.festung_mlp_set_stream.argtypes = [vp, vp]
@@ -263,6 +264,12 @@ class Solver:
                 "solver": info.solver, "symmetric": info.symmetric, "fp64_iterations": info.fp64_iterations,
                 "initial_rel_residual": info.initial_rel_residual, "coarse_iterations": info.coarse_iterations,
                 "precond_built": info.precond_built}
+
+    def set_persistent(self, enable=True):
+        """FP32 BiCGStab at p <= 1 as one persistent kernel (1) or the graph of four kernels
+        per iteration (0) (festung_set_persistent)."""
+        self._check(self.lib.festung_set_persistent(self.h, 1 if enable else 0))
+        return self
 
     def set_precond_reuse(self, max_steps):
         """One block-Jacobi build serves up to max_steps steps (festung_set_precond_reuse)."""

@@ -161,3 +161,40 @@ def test_multitile_coarse_corrected_step_matches_oracle(p, prec_name):
     assert err <= 1e-9, (err, info)
     assert info["rel_residual"] <= 1e-12
     assert info["coarse_iterations"] > 0 and info["fp64_iterations"] == 0, info
+
+
+@pytest.mark.parametrize("p", [0, 1])
+def test_multitile_persistent_and_graph_iterations_match_oracle(p):
+    """festung_set_persistent: at p <= 1 the FP32 BiCGStab iterations run as one persistent
+    kernel (default) or as the graph of four kernels per iteration; on the 8-tile mesh both
+    reach the oracle's step within the mixed bound, with about the same iteration count
+    (their sums round differently)."""
+    from paper_1408_3877_gb300 import festung as F
+    man = W.Manufactured(W.d_config2)
+    Co = _oracle(p, "mixed", man, TAU)
+    out = {}
+    for persistent in (True, False):
+        cV, V0T, bdr = mesh(MESH_N, "mixed", seed=21)
+        s = gpu_solver(cV, V0T, bdr, p)
+        s.set_persistent(persistent)
+        s.set_state(samples(s, lambda x, y: man.c(0.0, x, y)), is_samples=True)
+        s.set_coeff(samples(s, lambda x, y: man.d(TAU, x, y)))
+        s.set_source(samples(s, lambda x, y: man.f(TAU, x, y)))
+        s.set_bc(edge_samples(s, lambda x, y: man.c(TAU, x, y)), edge_samples(s, lambda x, y: man.gN(TAU, x, y)))
+        info = s.step(TAU, tol=1e-12, prec=F.MIXED, inner_tol=1e-2)
+        C = s.get_state()
+        s.close()
+        err = np.linalg.norm(C - Co) / np.linalg.norm(Co)
+        assert err <= 1e-9, (persistent, err, info)
+        assert info["rel_residual"] <= 1e-12 and info["fp64_iterations"] == 0, (persistent, info)
+        out[persistent] = info["iterations"]
+    assert abs(out[True] - out[False]) <= max(2, out[False] // 5), out
+
+
+def test_persistent_switch_is_checked():
+    from paper_1408_3877_gb300 import festung as F
+    cV, V0T, bdr = mesh(8, "mixed", seed=3)
+    s = gpu_solver(cV, V0T, bdr, 1)
+    with pytest.raises(F.FestungError):
+        s._check(s.lib.festung_set_persistent(s.h, 2))
+    s.close()
