@@ -304,7 +304,9 @@ __device__ bool barrier_reduce(const PersistArgs &a, int slot, PScal &ps, Fin fi
     __syncthreads();
     unsigned int g = 0;
     if (threadIdx.x == 0) {
-        g = ld_acquire_gpu(a.bar + 1);
+        // the current generation: this block saw it advance at its last barrier, and it
+        // cannot advance again before this block arrives (a relaxed read suffices)
+        g = *(volatile unsigned int *)(a.bar + 1);
         last_s = atom_add_acq_rel_gpu(a.bar, 1u) == gridDim.x - 1;
     }
     __syncthreads();
@@ -314,13 +316,24 @@ __device__ bool barrier_reduce(const PersistArgs &a, int slot, PScal &ps, Fin fi
 #pragma unroll
         for (int q = 0; q < ND; ++q) sm[q] = cp[q] = 0.0f;
         const int G = gridDim.x;
-        for (int b = threadIdx.x; b < G; b += blockDim.x) {
+        // Neumaier's compensated summation over blocks b = tid, tid + blockDim, ...; the
+        // loads of two rounds are issued together
+        for (int b0 = threadIdx.x; b0 < G; b0 += 2 * blockDim.x) {
+            float v[2][ND];
 #pragma unroll
-            for (int q = 0; q < ND; ++q) {
-                // Neumaier's compensated summation
-                const float v = __ldcg(a.part + (slot + q) * G + b), t = sm[q] + v;
-                cp[q] += fabsf(sm[q]) >= fabsf(v) ? (sm[q] - t) + v : (v - t) + sm[q];
-                sm[q] = t;
+            for (int h = 0; h < 2; ++h) {
+                const int b = b0 + h * blockDim.x;
+#pragma unroll
+                for (int q = 0; q < ND; ++q) v[h][q] = b < G ? __ldcg(a.part + (slot + q) * G + b) : 0.0f;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                for (int q = 0; q < ND; ++q) {
+                    const float t = sm[q] + v[h][q];
+                    cp[q] += fabsf(sm[q]) >= fabsf(v[h][q]) ? (sm[q] - t) + v[h][q] : (v[h][q] - t) + sm[q];
+                    sm[q] = t;
+                }
             }
         }
 #pragma unroll
