@@ -115,28 +115,41 @@ template <> Vecs<float> &vecs<float>(festung_ctx *c) { return c->ws->f; }
 // ---------------------------------------------------------------------------
 // projection of samples (K x R2, row-major) onto the basis (Sec. 3.4)
 // ---------------------------------------------------------------------------
-__global__ void k_project(const double *__restrict__ samp, double *__restrict__ out, float *__restrict__ out32,
-                          const double *__restrict__ wphiQ, int64_t K, int N, int R2, int check_positive,
-                          const int32_t *__restrict__ perm, int *__restrict__ flags) {
-    extern __shared__ double sw[];
-    for (int i = threadIdx.x; i < R2 * N; i += blockDim.x) sw[i] = wphiQ[i];
+// The sums run in double-float arithmetic (dfloat.cuh, about 48 bits) on the FP32 pipe:
+// this device's FP64 pipe would take about 100 us for the 375 multiply-adds per triangle
+// of p = 4 on 131,072 triangles.  The checks of the samples look at their bits (bit0
+// non-finite, bit1 not > 0, bit2 not all equal bit for bit).
+template <int N, int R2>
+__global__ void __launch_bounds__(256) k_project(const double *__restrict__ samp, double *__restrict__ out,
+                                                 float *__restrict__ out32, const double *__restrict__ wphiQ,
+                                                 int64_t K, int check_positive, const int32_t *__restrict__ perm,
+                                                 int *__restrict__ flags) {
+    __shared__ dfloat sw[R2 * N];
+    for (int i = threadIdx.x; i < R2 * N; i += blockDim.x) sw[i] = dfloat(wphiQ[i]);
     __syncthreads();
+    constexpr long long kExp = 0x7ff0000000000000ll, kMag = 0x7fffffffffffffffll;
     int fl = 0;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x) {
-        double acc[NMAX];
-        for (int j = 0; j < N; ++j) acc[j] = 0.0;
-        const int64_t u = perm[k];  // samples arrive in the caller's triangle order
-        const double first = samp[u * R2];
+        dfloat acc[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc[j] = dfloat(0.0f, 0.0f);
+        const double *sp = samp + (int64_t)perm[k] * R2;  // samples arrive in the caller's triangle order
+        const long long first = __double_as_longlong(sp[0]);
+#pragma unroll 5
         for (int r = 0; r < R2; ++r) {
-            const double v = samp[u * R2 + r];
-            if (!isfinite(v)) fl |= 1;
-            if (check_positive && !(v > 0.0)) fl |= 2;
-            if (v != first) fl |= 4;
-            for (int j = 0; j < N; ++j) acc[j] += sw[r * N + j] * v;
+            const double v = sp[r];
+            const long long bits = __double_as_longlong(v), mag = bits & kMag;
+            if (mag >= kExp) fl |= 1;                                  // Inf or NaN
+            if (check_positive && (bits <= 0 || mag > kExp)) fl |= 2;  // <= +0, negative or NaN
+            if (bits != first) fl |= 4;
+            const dfloat dv(v);
+#pragma unroll
+            for (int j = 0; j < N; ++j) acc[j] += sw[r * N + j] * dv;
         }
+#pragma unroll
         for (int j = 0; j < N; ++j) {
-            out[j * K + k] = acc[j];
-            if (out32) out32[j * K + k] = (float)acc[j];
+            out[j * K + k] = (double)acc[j];
+            if (out32) out32[j * K + k] = acc[j].hi;
         }
     }
     if (fl) atomicOr(flags, fl);
@@ -583,8 +596,12 @@ int project_samples(festung_ctx *c, const double *samples, int loc, double *out,
     }
     FCK(cudaMemsetAsync(c->ws->d_flags, 0, sizeof(int), c->stream));
     const TableOffsets o = table_offsets(c->N, c->R2, c->R1);
-    k_project<<<elem_grid(c), 256, sizeof(double) * c->R2 * c->N, c->stream>>>(
-        src, out, out32, c->dTab + o.wphiQ, c->K, c->N, c->R2, check_pos, c->dPerm, c->ws->d_flags); ++c->launches;
+    dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto) {
+        constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value;
+        k_project<N, R2><<<elem_grid(c), 256, 0, c->stream>>>(src, out, out32, c->dTab + o.wphiQ, c->K, check_pos,
+                                                             c->dPerm, c->ws->d_flags);
+    });
+    ++c->launches;
     FCK(cudaGetLastError());
     FCK(cudaMemcpyAsync(c->ws->h_flags, c->ws->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     FCK(cudaStreamSynchronize(c->stream));
