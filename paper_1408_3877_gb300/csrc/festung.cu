@@ -768,7 +768,7 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
         FCK(cudaGetLastError());
         // FP32 BiCGStab at p <= 1: the iterations as one persistent kernel (bicg_persist.cu)
         bool persistent = std::is_same<T, float>::value && solver == FESTUNG_SOLVER_BICGSTAB && c->persistent &&
-                          w.ppart && bicg_persistent_supported(c);
+                          !c->persist_refused && w.ppart && bicg_persistent_supported(c);
         // else build (or reuse) the graph: while (not done and under the bound) { CHUNK iterations }
         GraphCache &gc = graph_of<T>(c);
         auto build_graph = [&]() -> int {
@@ -875,7 +875,7 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
                         // the device cannot hold the grid: this context keeps to the graph
                         (void)cudaGetLastError();
                         persistent = false;
-                        c->persistent = false;
+                        c->persist_refused = true;
                         if ((rc = build_graph())) return rc;
                         continue;
                     }
@@ -2750,7 +2750,12 @@ int batch_step_concurrent(festung_batch *b, double dt, const festung_step_opts &
             }
             const int64_t l0 = c->launches;
             c->stream = ws;
+            // several workers at once: no persistent (cooperative) solver kernels, whose
+            // grids would share the device with other workers' grids; the graph form
+            const bool persistent = c->persistent;
+            if (nw > 1) c->persistent = false;
             rcs[q] = solve_system(c, dt, 1.0, &o, &in);
+            c->persistent = persistent;
             if (rcs[q]) {
                 cudaStreamSynchronize(ws);  // a failed step may leave work in flight
                 errs[q] = c->err;
