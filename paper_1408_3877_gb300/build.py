@@ -14,7 +14,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libfestung.so")
-SOURCES = ["tables.cpp", "mesh.cpp", "festung.cu", "apply_f64.cu", "apply_f32.cu", "apply_f32_kr.cu", "apply_df.cu", "apply_bf16.cu", "bicg_persist.cu", "noalloc.cu", "mlp.cu", "peak.cu"]
+SOURCES = ["tables.cpp", "mesh.cpp", "festung.cu", "batch.cu", "apply_f64.cu", "apply_f32.cu", "apply_f32_kr.cu", "apply_df.cu", "apply_bf16.cu", "bicg_persist.cu", "warmstart.cu", "noalloc.cu", "mlp.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
