@@ -1,11 +1,13 @@
 // Double-float arithmetic: a value is the unevaluated sum hi + lo of two floats with
-// |lo| <= ulp(hi) / 2, about 48 significant bits from FP32 instructions.
+// |lo| <= ulp(hi) / 2 (about one ulp for a product, see operator*), about 48 significant
+// bits from FP32 instructions.
 //
 // The error-free transformations are the classical ones: the sum of two floats and
 // its exact rounding error (Knuth's two-sum, 6 operations; Dekker's fast two-sum, 3,
 // when |a| >= |b|) and the product with its exact error from one fused multiply-add.
 // Sums and products of double-floats follow Dekker (1971): combine the high parts
-// exactly, add the low-order terms, renormalise.  Each result carries an absolute
+// exactly, add the low-order terms, renormalise (sums; a product is renormalised by the
+// sum it feeds).  Each result carries an absolute
 // error of a few units of 2^-48 times the magnitudes of the operands, which is the
 // bound a residual b - S x needs (errors relative to |S| |x|, not to |S x|).
 //
@@ -47,12 +49,17 @@ __device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
 __device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
 __device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
 
+// The product is left unnormalised: p + e is the value the renormalisation (an exact
+// transformation) would give, with |e| at most about one ulp of p instead of half of one.
+// Every sum renormalises (operator+), and a product of such a pair drops only the term
+// a.lo b.lo either way, so results keep about 47 bits at three fewer instructions per
+// multiply-add.
 __device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
     const float p = __fmul_rn(a.hi, b.hi);
     float e = __fmaf_rn(a.hi, b.hi, -p);  // exact error of the product of the high parts
     e = __fmaf_rn(a.hi, b.lo, e);
     e = __fmaf_rn(a.lo, b.hi, e);
-    return df_fast_two_sum(p, e);
+    return dfloat(p, e);
 }
 
 // Division only where the kernels divide once per triangle: through FP64.

@@ -743,9 +743,51 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
         int rc = persistent ? FESTUNG_OK : build_graph();
         if (rc) return rc;
         bool brk = false, drift = false;
-        while (true) {
+        // enqueue the iterations (the persistent kernel, or the graph's loop) and behind them
+        // the copies of the scalars and of the kernel's flag or the loop's pass count, read
+        // after one wait; a solve that is already done returns at once in either form
+        int launched = 0;  // 1: persistent kernel, 2: graph
+        auto enqueue = [&](int iter_now) -> int {
+            launched = 0;
+            if (persistent) {
+                if constexpr (std::is_same<T, float>::value) {
+                    // Z1, Z2 (not used by the fused applies) serve as the second p and v buffers
+                    const BicgVecs32 bv{V.x, V.r, V.p, V.v, V.ph, V.s, V.sh, V.t, V.Z1, V.Z2, V.r0, V.inv};
+                    const cudaError_t e = launch_bicg_persistent(c, bv, w.use_P ? w.Pb : nullptr, (float)tau, w.scal,
+                                                                 w.pscal, w.ppart, w.pcap, w.pbar, w.perr,
+                                                                 max_iter - total, st);
+                    if (e == cudaErrorNotSupported || e == cudaErrorCooperativeLaunchTooLarge) {
+                        // the device cannot hold the grid: this context keeps to the graph
+                        (void)cudaGetLastError();
+                        persistent = false;
+                        c->persist_refused = true;
+                        if ((rc = build_graph())) return rc;
+                    } else {
+                        FCK(e);
+                        ++c->launches;
+                        FCK(cudaMemcpyAsync(w.h_perr, w.perr, sizeof(int), cudaMemcpyDeviceToHost, st));
+                        launched = 1;
+                    }
+                }
+            }
+            if (!launched) {
+                const int max_chunks = std::max(1, (max_iter - total - iter_now + CHUNK - 1) / CHUNK);
+                k_loop_init<<<1, 1, 0, st>>>(w.loopctl, max_chunks); ++c->launches;
+                FCK(cudaGraphLaunch(gc.exec, st));
+                FCK(cudaMemcpyAsync(w.h_loopctl, w.loopctl, sizeof(int), cudaMemcpyDeviceToHost, st));
+                launched = 2;
+            }
             FCK(cudaMemcpyAsync(w.h_scal, w.scal, sizeof(KScal), cudaMemcpyDeviceToHost, st));
+            return FESTUNG_OK;
+        };
+        if ((rc = enqueue(0))) return rc;
+        while (true) {
             FCK(cudaStreamSynchronize(st));
+            if (launched == 1 && *w.h_perr) {
+                c->err = "persistent BiCGStab kernel: a grid barrier wait gave up";
+                return FESTUNG_ECUDA;
+            }
+            if (launched == 2) c->launches += gc.nodes * (int64_t)*w.h_loopctl;
             const KScal h = *w.h_scal;
             if (relres0 && restart == 0) *relres0 = h.b2 > 0 ? std::sqrt(h.r2_0 / h.b2) : std::sqrt(h.r2_0);
             if (h.done) {
@@ -790,37 +832,7 @@ int krylov_solve(festung_ctx *c, int solver, double tau, double tol, int max_ite
                 *iters = total;
                 return FESTUNG_OK;
             }
-            if (persistent) {
-                if constexpr (std::is_same<T, float>::value) {
-                    // Z1, Z2 (not used by the fused applies) serve as the second p and v buffers
-                    const BicgVecs32 bv{V.x, V.r, V.p, V.v, V.ph, V.s, V.sh, V.t, V.Z1, V.Z2, V.r0, V.inv};
-                    const cudaError_t e = launch_bicg_persistent(c, bv, w.use_P ? w.Pb : nullptr, (float)tau, w.scal,
-                                                                 w.pscal, w.ppart, w.pcap, w.pbar, w.perr, max_iter - total, st);
-                    if (e == cudaErrorNotSupported || e == cudaErrorCooperativeLaunchTooLarge) {
-                        // the device cannot hold the grid: this context keeps to the graph
-                        (void)cudaGetLastError();
-                        persistent = false;
-                        c->persist_refused = true;
-                        if ((rc = build_graph())) return rc;
-                        continue;
-                    }
-                    FCK(e);
-                    ++c->launches;
-                    FCK(cudaMemcpyAsync(w.h_perr, w.perr, sizeof(int), cudaMemcpyDeviceToHost, st));
-                    FCK(cudaStreamSynchronize(st));
-                    if (*w.h_perr) {
-                        c->err = "persistent BiCGStab kernel: a grid barrier wait gave up";
-                        return FESTUNG_ECUDA;
-                    }
-                }
-                continue;
-            }
-            const int max_chunks = std::max(1, (max_iter - total - h.iter + CHUNK - 1) / CHUNK);
-            k_loop_init<<<1, 1, 0, st>>>(w.loopctl, max_chunks); ++c->launches;
-            FCK(cudaGraphLaunch(gc.exec, st));
-            FCK(cudaMemcpyAsync(w.h_loopctl, w.loopctl, sizeof(int), cudaMemcpyDeviceToHost, st));
-            FCK(cudaStreamSynchronize(st));
-            c->launches += gc.nodes * (int64_t)*w.h_loopctl;
+            if ((rc = enqueue(h.iter))) return rc;
         }
         if (!brk && !drift) break;
         // breakdown or drift: restart from the current iterate
