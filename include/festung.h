@@ -383,6 +383,13 @@ int festung_set_coarse(festung_ctx *ctx, int enable);
  * 0 or 1. */
 int festung_set_persistent(festung_ctx *ctx, int enable);
 
+/* Testing hook for the failure path of the persistent kernel: with enable = 1 every grid
+ * barrier of the context's persistent solves waits for one block more than the grid has,
+ * so that each wait runs out (after about a second) and the solve fails with
+ * FESTUNG_ECUDA ("a grid barrier wait gave up"); the context stays usable, and enable = 0
+ * restores normal solves.  EINVAL unless enable is 0 or 1. */
+int festung_test_barrier_timeout(festung_ctx *ctx, int enable);
+
 /* Reuse of the block-Jacobi preconditioner over time steps.  Every step solves with the
  * inverse diagonal blocks of S; they depend on d_h, dt and the mass term and cost about as
  * much to build as a few Krylov iterations.  With max_steps = m > 1 one build serves up

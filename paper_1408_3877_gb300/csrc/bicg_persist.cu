@@ -29,10 +29,18 @@ namespace festung {
 
 namespace {
 
-// Polls of a waiting block before a barrier is given up (with a 64 ns sleep between
-// polls: a fraction of a second).  Only a grid that is not resident as a whole could
-// reach it, which the cooperative launch rules out.
-constexpr unsigned int kSpinLimit = 1u << 22;
+// A waiting block gives up a barrier after a second (device global timer), or after
+// 2^24 polls whatever the timer says.  Only a grid that is not resident as a whole could
+// reach it, which the cooperative launch rules out (festung_test_barrier_timeout makes
+// the waits run out on purpose, for the test of this path).
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+constexpr unsigned int kSpinLimit = 1u << 24;
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
 
 struct PersistArgs {
     BicgVecs32 v;
@@ -50,6 +58,7 @@ struct PersistArgs {
     unsigned int *bar;  // [0] arrivals, [1] generation
     int *err;
     int max_iter;
+    int bar_extra;  // testing only: blocks a barrier waits for beyond the grid
 };
 
 // The scalars of the iteration while the kernel runs, in FP32 and double-float (the
@@ -307,7 +316,7 @@ __device__ bool barrier_reduce(const PersistArgs &a, int slot, PScal &ps, Fin fi
         // the current generation: this block saw it advance at its last barrier, and it
         // cannot advance again before this block arrives (a relaxed read suffices)
         g = *(volatile unsigned int *)(a.bar + 1);
-        last_s = atom_add_acq_rel_gpu(a.bar, 1u) == gridDim.x - 1;
+        last_s = atom_add_acq_rel_gpu(a.bar, 1u) == gridDim.x - 1 + (unsigned int)a.bar_extra;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
@@ -361,12 +370,16 @@ __device__ bool barrier_reduce(const PersistArgs &a, int slot, PScal &ps, Fin fi
         }
     } else if (threadIdx.x == 0) {
         unsigned int n = 0;
+        const unsigned long long t0 = globaltimer_ns();
         while (ld_acquire_gpu(a.bar + 1) == g) {
-            if (++n > kSpinLimit) {
-                atomicExch(a.err, 1);
-                break;
+            if (*(volatile int *)a.err) break;  // another block gave up
+            if (++n > 256) {
+                __nanosleep(32);
+                if ((n & 63) == 0 && (globaltimer_ns() - t0 > kWaitLimitNs || n > kSpinLimit)) {
+                    atomicExch(a.err, 1);
+                    break;
+                }
             }
-            if (n > 256) __nanosleep(32);
         }
     }
     if (threadIdx.x == 0) abort_s = *(volatile int *)a.err;
@@ -483,7 +496,7 @@ bool bicg_persistent_supported(const festung_ctx *c) {
 
 cudaError_t launch_bicg_persistent(const festung_ctx *c, const BicgVecs32 &v, const __nv_bfloat16 *P, float tau,
                                    KScal *sc, void *ps, float *part, int part_blocks, unsigned int *bar, int *err,
-                                   int max_iter, cudaStream_t st) {
+                                   int max_iter, int bar_extra, cudaStream_t st) {
     if (!bicg_persistent_supported(c)) return cudaErrorNotSupported;
     cudaError_t e = cudaErrorNotSupported;
     dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
@@ -527,6 +540,7 @@ cudaError_t launch_bicg_persistent(const festung_ctx *c, const BicgVecs32 &v, co
             a.bar = bar;
             a.err = err;
             a.max_iter = max_iter;
+            a.bar_extra = bar_extra;
             if ((e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), st)) != cudaSuccess) return;
             if ((e = cudaMemsetAsync(err, 0, sizeof(int), st)) != cudaSuccess) return;
             void *args[] = {&a};

@@ -165,6 +165,7 @@ struct festung_ctx {
     bool P_built = false;      // the current step built its blocks
     bool persistent = true;    // FP32 BiCGStab at p <= 1 as one persistent kernel (festung_set_persistent)
     bool persist_refused = false;  // the device refused the persistent grid once: the graph form
+    int test_barrier_extra = 0;    // festung_test_barrier_timeout: barriers wait for this many more blocks
     int num_sms = 0;
     mutable int64_t launches = 0;  // kernels launched on behalf of this context (graph nodes counted)
     std::string err;

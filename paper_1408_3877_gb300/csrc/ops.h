@@ -96,10 +96,12 @@ bool bicg_persistent_supported(const festung_ctx *c);
 // or sconv is set); p and v are left in either buffer.  ps: 256 bytes of device memory
 // for the scalars while the kernel runs.  part: partials, 6 floats per
 // block of at most part_blocks blocks; bar: 2 counters and err: a flag (both zeroed
-// here) of the grid barrier; err ends up non-zero if a barrier wait gave up.  cudaErrorNotSupported: the context's
+// here) of the grid barrier; err ends up non-zero if a barrier wait gave up.  bar_extra
+// > 0 (testing only) makes every barrier wait for that many blocks more than the grid has,
+// so that the waits run out.  cudaErrorNotSupported: the context's
 // order or the device cannot run it (the caller uses the graph instead).
 cudaError_t launch_bicg_persistent(const festung_ctx *c, const BicgVecs32 &v, const __nv_bfloat16 *P, float tau,
                                    KScal *sc, void *ps, float *part, int part_blocks, unsigned int *bar, int *err,
-                                   int max_iter, cudaStream_t st);
+                                   int max_iter, int bar_extra, cudaStream_t st);
 
 }  // namespace festung

@@ -86,7 +86,7 @@ inline const float *geomB<float>(const festung_ctx *c) { return c->fB; }
         }                                                                          \
     } while (0)
 
-constexpr int CHUNK = 16;  // Krylov iterations per pass of a solve's captured loop body
+constexpr int CHUNK = 8;  // Krylov iterations per pass of a solve's captured loop body
 
 // message of the last failed festung_mesh_create / festung_batch_create of this thread
 std::string &create_error();

@@ -27,7 +27,7 @@ EXPORTS = [
     "festung_element_order", "festung_precond_blocks", "festung_launch_count", "festung_set_stream",
     "festung_last_error", "festung_destroy",
     "festung_autotune", "festung_fma_peak", "festung_warmstart_features", "festung_set_guess", "festung_set_coarse",
-    "festung_set_precond_reuse", "festung_set_persistent",
+    "festung_set_precond_reuse", "festung_set_persistent", "festung_test_barrier_timeout",
     "festung_mlp_create", "festung_mlp_sizes", "festung_mlp_set_stream", "festung_mlp_forward", "festung_mlp_grad",
     "festung_mlp_adam", "festung_mlp_get", "festung_mlp_set", "festung_mlp_last_error", "festung_mlp_destroy",
     "festung_batch_create", "festung_batch_set_stream", "festung_batch_set_mode", "festung_batch_step",
@@ -98,6 +98,7 @@ def load(path=None):
     lib.festung_set_coarse.argtypes = [vp, cint]
     lib.festung_set_precond_reuse.argtypes = [vp, cint]
     lib.festung_set_persistent.argtypes = [vp, cint]
+    lib.festung_test_barrier_timeout.argtypes = [vp, cint]
     lib.festung_mlp_create.argtypes = [cint, cint, ctypes.c_uint64, ctypes.POINTER(vp)]
     lib.festung_mlp_sizes.argtypes = [vp, ctypes.POINTER(cint), ctypes.POINTER(cint), ctypes.POINTER(cint)]
     lib.festung_mlp_set_stream.argtypes = [vp, vp]

@@ -198,3 +198,33 @@ def test_persistent_switch_is_checked():
     with pytest.raises(F.FestungError):
         s._check(s.lib.festung_set_persistent(s.h, 2))
     s.close()
+
+
+def test_persistent_barrier_wait_runs_out_and_is_reported():
+    """The bounded waits of the persistent p <= 1 solver: with festung_test_barrier_timeout
+    every grid barrier waits for one block more than the grid has, each wait gives up after
+    about a second, and the step fails with FESTUNG_ECUDA, leaving the state as it was; the
+    context then steps normally and still matches the oracle."""
+    import time
+    from paper_1408_3877_gb300 import festung as F
+    man = W.Manufactured(W.d_config2)
+    cV, V0T, bdr = mesh(MESH_N, "mixed", seed=21)
+    s = gpu_solver(cV, V0T, bdr, 1)
+    s.set_state(samples(s, lambda x, y: man.c(0.0, x, y)), is_samples=True)
+    s.set_coeff(samples(s, lambda x, y: man.d(TAU, x, y)))
+    s.set_source(samples(s, lambda x, y: man.f(TAU, x, y)))
+    s.set_bc(edge_samples(s, lambda x, y: man.c(TAU, x, y)), edge_samples(s, lambda x, y: man.gN(TAU, x, y)))
+    C0 = s.get_state()
+    s._check(s.lib.festung_test_barrier_timeout(s.h, 1))
+    t0 = time.perf_counter()
+    with pytest.raises(F.FestungError, match="barrier"):
+        s.step(TAU, tol=1e-12, prec=F.MIXED, inner_tol=1e-2)
+    assert time.perf_counter() - t0 < 30
+    assert np.array_equal(s.get_state(), C0)
+    s._check(s.lib.festung_test_barrier_timeout(s.h, 0))
+    info = s.step(TAU, tol=1e-12, prec=F.MIXED, inner_tol=1e-2)
+    C = s.get_state()
+    s.close()
+    Co = _oracle(1, "mixed", man, TAU)
+    err = np.linalg.norm(C - Co) / np.linalg.norm(Co)
+    assert err <= 1e-9, (err, info)
