@@ -917,6 +917,15 @@ cudaError_t upload_mesh(festung_ctx *c, const MeshOrder &mo) {
               {c->dLift, mo.lift.data(), K * sizeof(uint8_t)}};
     for (const auto &u : up)
         if (u.bytes && (e = cudaMemcpy(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    std::vector<int32_t> lifted;
+    for (int64_t k = 0; k < K; ++k)
+        if (mo.lift[k] & 2) lifted.push_back((int32_t)k);
+    c->nLift = (int64_t)lifted.size();
+    if ((e = cudaMalloc(&c->dLiftList, std::max<size_t>(1, lifted.size()) * sizeof(int32_t))) != cudaSuccess) return e;
+    if (!lifted.empty() &&
+        (e = cudaMemcpy(c->dLiftList, lifted.data(), lifted.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+        return e;
     return retile(c, 256);
 }
 
@@ -1974,7 +1983,8 @@ void festung_destroy(festung_ctx *c) {
         cudaEventDestroy(c->ev_P);
     }
     free_ctx_device(c);
-    void *mesh_ptrs[] = {c->dB, c->fB, c->dNbr, c->dPerm, c->dSlot, c->dHaloPtr, c->dHalo, c->dHaloSlot, c->dLift};
+    void *mesh_ptrs[] = {c->dB, c->fB, c->dNbr, c->dPerm, c->dSlot, c->dHaloPtr, c->dHalo, c->dHaloSlot, c->dLift,
+                         c->dLiftList};
     for (void *q : mesh_ptrs)
         if (q) cudaFree(q);
     delete c;

@@ -114,6 +114,8 @@ struct festung_ctx {
     int16_t *dSlot = nullptr;   // 3 x K
     int16_t *dHaloSlot = nullptr;  // 3 per halo entry
     uint8_t *dLift = nullptr;      // K, see MeshOrder::lift
+    int32_t *dLiftList = nullptr;  // the triangles whose right-hand side the Dirichlet lift reaches
+    int64_t nLift = 0;
     bool has_dirichlet = false, has_neumann = false;
     // device mesh
     double *dB = nullptr;

@@ -184,6 +184,12 @@ __global__ void __launch_bounds__(256) k_flux(const T *__restrict__ X, T *__rest
 // ---------------------------------------------------------------------------
 // Pass 2.  MODE_APPLY:  y = mass M x + tau (eta (S + S_D) x + sum_m A_m Z^m)     (E1)
 //          MODE_RHS:    y = mass M x + tau (M F + eta K_D - K_N + sum_m A_m Z^m) (E2)
+// MODE_RHS runs in two launches.  Z = M^{-1} J_D (the Dirichlet lift) vanishes except on
+// the triangles next to a Dirichlet edge, so the terms with Z only matter on the few
+// triangles the lift reaches: the first launch (list = null) writes every triangle's y
+// without them, the second adds tau sum_m A_m Z^m and eta K_D on the listed triangles only
+// (list: their indices, nlist of them), one triangle per thread, so that their FP64
+// quadrature loops run in full warps instead of in one lane of a warp each.
 // (mass = 1 for a time step; mass = 0, tau = 1 for the stationary problem of Sec. 3.9)
 // with A_m = -G^m + R^m + R_D^m (G^m Sec. 3.6.3, R^m eq. globR, R_D^m eq. globR:D,
 // S eq. globS, S_D eq. globS:D, K_D eq. globK:D, K_N Sec. 3.6.12).  Volume terms use
@@ -199,14 +205,17 @@ __global__ void __launch_bounds__(256) k_apply(const T *__restrict__ X, const T 
                                                const int32_t *__restrict__ nbr, int64_t K, T tau, T eta, T mass,
                                                const T *__restrict__ tabg, const T *__restrict__ F,
                                                const T *__restrict__ cD, const T *__restrict__ gN,
-                                               const int32_t *__restrict__ perm, const uint8_t *__restrict__ lift,
-                                               const int *__restrict__ skip) {
+                                               const int32_t *__restrict__ perm, const int32_t *__restrict__ list,
+                                               int64_t nlist, const int *__restrict__ skip) {
     __shared__ SmemTab<T, N, R2, R1> s;
     if (skip && *skip) return;
     load_tables(s, tabg);
     __syncthreads();
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
-         k += (int64_t)gridDim.x * blockDim.x) {
+    const bool lift_pass = MODE == MODE_RHS && list != nullptr;
+    const int64_t n_it = lift_pass ? nlist : K;
+    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < n_it;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = lift_pass ? (int64_t)list[it] : it;
         T x[N], z1[N], z2[N], d[N], acc[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) {
@@ -217,9 +226,8 @@ __global__ void __launch_bounds__(256) k_apply(const T *__restrict__ X, const T 
             acc[j] = T(0);
         }
         const T b11 = Bg[k], b12 = Bg[K + k], b21 = Bg[2 * K + k], b22 = Bg[3 * K + k];
-        // right-hand side: Z = M^{-1} J_D vanishes on this triangle and its neighbours
-        // unless the Dirichlet lift reaches it; then only the Neumann data remain
-        const bool aterms = (MODE == MODE_APPLY) || (lift[k] & 2);
+        // right-hand side: the terms with Z in the lift pass only (see above)
+        const bool aterms = (MODE == MODE_APPLY) || lift_pass;
         // volume term -sum_m G^m Z^m
 #pragma unroll 1
         for (int r = 0; r < (aterms ? R2 : 0); ++r) {
@@ -240,7 +248,7 @@ __global__ void __launch_bounds__(256) k_apply(const T *__restrict__ X, const T 
 #pragma unroll 1
         for (int n = 0; n < 3; ++n) {
             const int code = nbr[n * K + k];
-            if (MODE == MODE_APPLY && code == NBR_NEUMANN) continue;
+            if ((MODE == MODE_APPLY || lift_pass) && code == NBR_NEUMANN) continue;
             if (!aterms && code != NBR_NEUMANN) continue;
             T nx, ny;
             edge_normal(n, b11, b12, b21, b22, nx, ny);
@@ -298,6 +306,10 @@ __global__ void __launch_bounds__(256) k_apply(const T *__restrict__ X, const T 
         const T det = b11 * b22 - b12 * b21;  // M = 2|T_k| I (Sec. 3.6.1)
 #pragma unroll
         for (int i = 0; i < N; ++i) {
+            if (lift_pass) {
+                Y[i * K + k] += tau * acc[i];
+                continue;
+            }
             if (MODE == MODE_RHS && F) acc[i] += det * F[i * K + k];
             Y[i * K + k] = mass * det * x[i] + tau * acc[i];
         }
