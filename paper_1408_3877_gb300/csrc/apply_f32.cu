@@ -74,7 +74,7 @@ void launch_apply_twopass<float>(const festung_ctx *c, const float *x, float *y,
         k_flux<float, N, R2, R1><<<grid, 256, 0, st>>>(x, Z1, Z2, c->fB, c->dNbr, c->K, c->fTab, skip);
         k_apply<float, N, R2, R1, MODE_APPLY><<<grid, 256, 0, st>>>(x, Z1, Z2, c->fD, y, c->fB, c->dNbr, c->K, tau,
                                                                   (float)c->eta, (float)c->mass, c->fTab, nullptr, nullptr, nullptr,
-                                                                  nullptr, nullptr, 0, skip);
+                                                                  nullptr, skip);
     });
 }
 

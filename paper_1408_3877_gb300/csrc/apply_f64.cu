@@ -26,7 +26,8 @@ void launch_apply<double>(const festung_ctx *c, const double *x, double *y, doub
 
 void launch_rhs(const festung_ctx *c, double *W1, double *W2, double *b, double tau, cudaStream_t st) {
     const int grid = elem_grid(c);
-    const int grid_lift = (int)std::max<int64_t>(1, std::min<int64_t>((c->nLift + 255) / 256, (int64_t)c->num_sms * 8));
+    const int grid_lift = (int)std::max<int64_t>(
+        1, std::min<int64_t>((c->nLift + LIFT_WARPS - 1) / LIFT_WARPS, (int64_t)c->num_sms * 16));
     c->launches += c->nLift > 0 ? 3 : 2;
     dispatch(c->N, c->R2, c->R1, [&](auto n_, auto r2_, auto r1_) {
         constexpr int N = decltype(n_)::value, R2 = decltype(r2_)::value, R1 = decltype(r1_)::value;
@@ -35,11 +36,11 @@ void launch_rhs(const festung_ctx *c, double *W1, double *W2, double *b, double 
         // every triangle without the lift's terms, then those terms on the triangles it reaches
         k_apply<double, N, R2, R1, MODE_RHS><<<grid, 256, 0, st>>>(c->dC, W1, W2, c->dD, b, c->dB, c->dNbr, c->K,
                                                                    tau, c->eta, c->mass, c->dTab, c->dF, c->dCD, c->dGN,
-                                                                   c->dPerm, nullptr, 0, nullptr);
+                                                                   c->dPerm, nullptr);
         if (c->nLift > 0)
-            k_apply<double, N, R2, R1, MODE_RHS><<<grid_lift, 256, 0, st>>>(
-                c->dC, W1, W2, c->dD, b, c->dB, c->dNbr, c->K, tau, c->eta, c->mass, c->dTab, c->dF, c->dCD, c->dGN,
-                c->dPerm, c->dLiftList, c->nLift, nullptr);
+            k_rhs_lift<N, R2, R1><<<grid_lift, 32 * LIFT_WARPS, 0, st>>>(W1, W2, c->dD, b, c->dB, c->dNbr, c->K, tau,
+                                                                        c->eta, c->dTab, c->dCD, c->dPerm,
+                                                                        c->dLiftList, c->nLift);
     });
 }
 
@@ -72,7 +73,7 @@ void launch_apply_twopass<double>(const festung_ctx *c, const double *x, double 
         k_flux<double, N, R2, R1><<<grid, 256, 0, st>>>(x, Z1, Z2, c->dB, c->dNbr, c->K, c->dTab, skip);
         k_apply<double, N, R2, R1, MODE_APPLY><<<grid, 256, 0, st>>>(x, Z1, Z2, c->dD, y, c->dB, c->dNbr, c->K, tau,
                                                                   (double)c->eta, (double)c->mass, c->dTab, nullptr, nullptr, nullptr,
-                                                                  nullptr, nullptr, 0, skip);
+                                                                  nullptr, skip);
     });
 }
 

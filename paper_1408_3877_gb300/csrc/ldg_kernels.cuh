@@ -184,12 +184,9 @@ __global__ void __launch_bounds__(256) k_flux(const T *__restrict__ X, T *__rest
 // ---------------------------------------------------------------------------
 // Pass 2.  MODE_APPLY:  y = mass M x + tau (eta (S + S_D) x + sum_m A_m Z^m)     (E1)
 //          MODE_RHS:    y = mass M x + tau (M F + eta K_D - K_N + sum_m A_m Z^m) (E2)
-// MODE_RHS runs in two launches.  Z = M^{-1} J_D (the Dirichlet lift) vanishes except on
-// the triangles next to a Dirichlet edge, so the terms with Z only matter on the few
-// triangles the lift reaches: the first launch (list = null) writes every triangle's y
-// without them, the second adds tau sum_m A_m Z^m and eta K_D on the listed triangles only
-// (list: their indices, nlist of them), one triangle per thread, so that their FP64
-// quadrature loops run in full warps instead of in one lane of a warp each.
+// MODE_RHS leaves out the terms with Z and eta K_D: Z = M^{-1} J_D (the Dirichlet lift)
+// vanishes except on the triangles next to a Dirichlet edge, so those terms only matter on
+// the few triangles the lift reaches, and k_rhs_lift adds them there.
 // (mass = 1 for a time step; mass = 0, tau = 1 for the stationary problem of Sec. 3.9)
 // with A_m = -G^m + R^m + R_D^m (G^m Sec. 3.6.3, R^m eq. globR, R_D^m eq. globR:D,
 // S eq. globS, S_D eq. globS:D, K_D eq. globK:D, K_N Sec. 3.6.12).  Volume terms use
@@ -205,17 +202,13 @@ __global__ void __launch_bounds__(256) k_apply(const T *__restrict__ X, const T 
                                                const int32_t *__restrict__ nbr, int64_t K, T tau, T eta, T mass,
                                                const T *__restrict__ tabg, const T *__restrict__ F,
                                                const T *__restrict__ cD, const T *__restrict__ gN,
-                                               const int32_t *__restrict__ perm, const int32_t *__restrict__ list,
-                                               int64_t nlist, const int *__restrict__ skip) {
+                                               const int32_t *__restrict__ perm, const int *__restrict__ skip) {
     __shared__ SmemTab<T, N, R2, R1> s;
     if (skip && *skip) return;
     load_tables(s, tabg);
     __syncthreads();
-    const bool lift_pass = MODE == MODE_RHS && list != nullptr;
-    const int64_t n_it = lift_pass ? nlist : K;
-    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < n_it;
-         it += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = lift_pass ? (int64_t)list[it] : it;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x) {
         T x[N], z1[N], z2[N], d[N], acc[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) {
@@ -226,8 +219,8 @@ __global__ void __launch_bounds__(256) k_apply(const T *__restrict__ X, const T 
             acc[j] = T(0);
         }
         const T b11 = Bg[k], b12 = Bg[K + k], b21 = Bg[2 * K + k], b22 = Bg[3 * K + k];
-        // right-hand side: the terms with Z in the lift pass only (see above)
-        const bool aterms = (MODE == MODE_APPLY) || lift_pass;
+        // right-hand side: the terms with Z come from k_rhs_lift (see above)
+        const bool aterms = MODE == MODE_APPLY;
         // volume term -sum_m G^m Z^m
 #pragma unroll 1
         for (int r = 0; r < (aterms ? R2 : 0); ++r) {
@@ -248,7 +241,7 @@ __global__ void __launch_bounds__(256) k_apply(const T *__restrict__ X, const T 
 #pragma unroll 1
         for (int n = 0; n < 3; ++n) {
             const int code = nbr[n * K + k];
-            if ((MODE == MODE_APPLY || lift_pass) && code == NBR_NEUMANN) continue;
+            if (MODE == MODE_APPLY && code == NBR_NEUMANN) continue;
             if (!aterms && code != NBR_NEUMANN) continue;
             T nx, ny;
             edge_normal(n, b11, b12, b21, b22, nx, ny);
@@ -306,13 +299,111 @@ __global__ void __launch_bounds__(256) k_apply(const T *__restrict__ X, const T 
         const T det = b11 * b22 - b12 * b21;  // M = 2|T_k| I (Sec. 3.6.1)
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            if (lift_pass) {
-                Y[i * K + k] += tau * acc[i];
-                continue;
-            }
             if (MODE == MODE_RHS && F) acc[i] += det * F[i * K + k];
             Y[i * K + k] = mass * det * x[i] + tau * acc[i];
         }
+    }
+}
+
+// The terms of the right-hand side that involve the Dirichlet lift Z = M^{-1} J_D^m:
+// y += tau (sum_m A_m Z^m + eta K_D) on the triangles in `list` (the ones the lift
+// reaches), after k_apply<MODE_RHS> wrote y without them.  One warp per triangle: its
+// lanes take the R2 points of the volume term, then the R1 points of each edge, then the
+// N test functions, so that the FP64 quadrature of a triangle runs 32 lanes wide (this
+// device's FP64 pipe is narrow; a thread per triangle left the few listed triangles on a
+// few SMs for 0.29 ms at p = 4).
+constexpr int LIFT_WARPS = 4;  // triangles per block
+
+template <int N, int R2, int R1>
+__global__ void __launch_bounds__(32 * LIFT_WARPS)
+    k_rhs_lift(const double *__restrict__ Z1, const double *__restrict__ Z2, const double *__restrict__ Dc,
+               double *__restrict__ Y, const double *__restrict__ Bg, const int32_t *__restrict__ nbr, int64_t K,
+               double tau, double eta, const double *__restrict__ tabg, const double *__restrict__ cD,
+               const int32_t *__restrict__ perm, const int32_t *__restrict__ list, int64_t nlist) {
+    static_assert(R2 <= 32 && N <= 32 && R1 <= 32, "one lane per point and per test function");
+    __shared__ SmemTab<double, N, R2, R1> s;
+    __shared__ double own[LIFT_WARPS][3][N], nb[LIFT_WARPS][3][N];  // d, z1, z2 of the triangle / a neighbour
+    __shared__ double pt[LIFT_WARPS][2][32];                         // values at the points
+    load_tables(s, tabg);
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t it = (int64_t)blockIdx.x * LIFT_WARPS + w; it < nlist; it += (int64_t)gridDim.x * LIFT_WARPS) {
+        const int64_t k = list[it];
+        if (lane < N) {
+            own[w][0][lane] = Dc[lane * K + k];
+            own[w][1][lane] = Z1[lane * K + k];
+            own[w][2][lane] = Z2[lane * K + k];
+        }
+        const double b11 = Bg[k], b12 = Bg[K + k], b21 = Bg[2 * K + k], b22 = Bg[3 * K + k];
+        __syncwarp();
+        // volume term -sum_m G^m Z^m: d_h, Z^1, Z^2 at point r = lane
+        if (lane < R2) {
+            double dv = 0.0, w1 = 0.0, w2 = 0.0;
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                const double ph = s.phiQ[lane * N + j];
+                dv += ph * own[w][0][j];
+                w1 += ph * own[w][1][j];
+                w2 += ph * own[w][2][j];
+            }
+            pt[w][0][lane] = dv * (b22 * w1 - b12 * w2);
+            pt[w][1][lane] = dv * (b11 * w2 - b21 * w1);
+        }
+        __syncwarp();
+        double acc = 0.0;  // lane i < N: test function i
+        if (lane < N) {
+#pragma unroll 5
+            for (int r = 0; r < R2; ++r) acc -= s.gw1[r * N + lane] * pt[w][0][r] + s.gw2[r * N + lane] * pt[w][1][r];
+        }
+        __syncwarp();
+        // edge terms R^m, R_D^m with Z, and eta K_D: the flux at point r = lane
+        for (int n = 0; n < 3; ++n) {
+            const int code = nbr[n * K + k];
+            if (code == NBR_NEUMANN) continue;
+            double nx, ny;
+            edge_normal(n, b11, b12, b21, b22, nx, ny);
+            if (code >= 0 && lane < N) {
+                const int64_t k2 = code >> 2;
+                nb[w][0][lane] = Dc[lane * K + k2];
+                nb[w][1][lane] = Z1[lane * K + k2];
+                nb[w][2][lane] = Z2[lane * K + k2];
+            }
+            __syncwarp();
+            if (lane < R1) {
+                double dm = 0.0, zm1 = 0.0, zm2 = 0.0;
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    const double ph = s.phiE[(n * R1 + lane) * N + j];
+                    dm += ph * own[w][0][j];
+                    zm1 += ph * own[w][1][j];
+                    zm2 += ph * own[w][2][j];
+                }
+                double g;
+                if (code >= 0) {
+                    const int n2 = code & 3, rp = R1 - 1 - lane;  // the neighbour's point (eq. mapEE)
+                    double dp = 0.0, zp1 = 0.0, zp2 = 0.0;
+#pragma unroll
+                    for (int j = 0; j < N; ++j) {
+                        const double ph = s.phiE[(n2 * R1 + rp) * N + j];
+                        dp += ph * nb[w][0][j];
+                        zp1 += ph * nb[w][1][j];
+                        zp2 += ph * nb[w][2][j];
+                    }
+                    g = 0.5 * (nx * (dm * zm1 + dp * zp1) + ny * (dm * zm2 + dp * zp2));
+                } else {  // Dirichlet
+                    g = dm * (nx * zm1 + ny * zm2) + eta * cD[((int64_t)perm[k] * 3 + n) * R1 + lane];
+                }
+                pt[w][0][lane] = g;
+            }
+            __syncwarp();
+            if (lane < N) {
+#pragma unroll
+                for (int r = 0; r < R1; ++r) acc += s.wphiE[(n * R1 + r) * N + lane] * pt[w][0][r];
+            }
+            __syncwarp();
+        }
+        if (lane < N) Y[lane * K + k] += tau * acc;
+        __syncwarp();
     }
 }
 
