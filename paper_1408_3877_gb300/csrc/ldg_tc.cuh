@@ -1,7 +1,7 @@
 // Volume term of the fused apply on the tensor cores (FP32 kernels, p >= 3).
 //
 // For the 32 triangles of a warp the volume term -sum_m G^m Z^m (Sec. 3.6.3, eq. hatG) in
-// the contravariant form of ldg_fused.cuh is two rounds of small dense products with the
+// the contravariant form of ldg_fused.cuh is two passes of small dense products with the
 // reference tables:
 //   1. evaluation  [d_h | zeta^1 | zeta^2] (32 x 16, basis) . Phi^T (16 x R2p, points):
 //      d_h, zeta^1, zeta^2 at the triangle points;
@@ -18,10 +18,10 @@
 //   A (16 x 8):  a0 (g, t), a1 (g + 8, t), a2 (g, t + 4), a3 (g + 8, t + 4);
 //   B (8 x 8):   b0 (t, g), b1 (t + 4, g);
 //   C (16 x 8):  c0 (g, 2t), c1 (g, 2t + 1), c2 (g + 8, 2t), c3 (g + 8, 2t + 1).
-// The products u, v of round 1 sit in C layout; round 2 uses them as A fragments directly by
-// ordering its reduction index so that A column t is point 2t and column t + 4 is point
-// 2t + 1 of each group of 8 points (the B rows follow the same order), with no data exchange
-// between lanes.
+// The products u, v of the first pass sit in C layout; the second pass uses them as A
+// fragments directly by ordering its reduction index so that A column t is point 2t and
+// column t + 4 is point 2t + 1 of each group of 8 points (the B rows follow the same
+// order), with no data exchange between lanes.
 #pragma once
 
 #include <cstdint>
@@ -136,7 +136,7 @@ __device__ __forceinline__ void volume_tc(float (&acc)[N], float *stage, const f
             for (int q = 0; q < 4; ++q) out[mt][nb][q] = 0.0f;
 #pragma unroll 1
         for (int nt = 0; nt < NT; ++nt) {
-            // round 1: d_h, zeta^1, zeta^2 at points 8 nt .. 8 nt + 7
+            // first pass: d_h, zeta^1, zeta^2 at points 8 nt .. 8 nt + 7
             float c[3][4];
 #pragma unroll
             for (int f = 0; f < 3; ++f)
@@ -161,7 +161,7 @@ __device__ __forceinline__ void volume_tc(float (&acc)[N], float *stage, const f
                 }
             }
             // u = d_h zeta^1, v = d_h zeta^2 at the points of this group, as A fragments of
-            // round 2 (column t <-> point 2t, column t + 4 <-> point 2t + 1)
+            // second pass (column t <-> point 2t, column t + 4 <-> point 2t + 1)
             uint32_t uh[4], ul[4], vh[4], vl[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -169,7 +169,7 @@ __device__ __forceinline__ void volume_tc(float (&acc)[N], float *stage, const f
                 tf32_trunc_split(c[0][p] * c[1][p], uh[q], ul[q]);
                 tf32_trunc_split(c[0][p] * c[2][p], vh[q], vl[q]);
             }
-            // round 2: test against the weighted gradients, both groups of 8 basis functions
+            // second pass: test against the weighted gradients, both groups of 8 basis functions
 #pragma unroll
             for (int nb = 0; nb < 2; ++nb) {
                 const int o = (8 * nb + g) * TC_GR + 8 * nt + 2 * t;
