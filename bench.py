@@ -332,10 +332,25 @@ def run_festung(args):
         b.record(stream)
         torch.cuda.synchronize()
         fp64_steps.append((a.elapsed_time(b) / 1e3, info64["iterations"]))
+    # ---- and with the refinement residual in FP64 (FESTUNG_MIXED64: FP32 sweeps, S C in FP64)
+    mixed64_steps = []
+    for j in range(3):
+        d, f, cD, gN = step_inputs(s, cfg, man, (nsteps + args.steps + 2 + j + 1) * dt, dev)
+        s.set_coeff(d)
+        s.set_source(f)
+        s.set_bc(cD, gN)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        a.record(stream)
+        info_m64 = s.step(dt, tol=tol, prec=F.MIXED64, inner_tol=1e-2)
+        b.record(stream)
+        torch.cuda.synchronize()
+        mixed64_steps.append((a.elapsed_time(b) / 1e3, info_m64["iterations"], info_m64["coarse_iterations"],
+                              info_m64["rel_residual"]))
 
     # ---- accuracy of the timed form: one more mixed step (same history, so the same
     # extrapolated guess as the timed steps) against an FP64 step at 1e-13 from the same state
-    t_next = (nsteps + args.steps + 3) * dt
+    t_next = (nsteps + args.steps + 6) * dt
     nxt = step_inputs(s, cfg, man, t_next, dev)
 
     def load(data):
@@ -475,6 +490,11 @@ def run_festung(args):
         "plain_fp64_step": {"value": fp64_steps[-1][0], "unit": "s/step", "iterations": fp64_steps[-1][1],
                             "note": "the same trajectory continued with FESTUNG_FP64 (FP64 Krylov and residual, "
                                     "the same extrapolated initial guess)"},
+        "fp64_residual_step": {"value": float(np.mean([m[0] for m in mixed64_steps[1:]])), "unit": "s/step",
+                               "iterations": [m[1] for m in mixed64_steps], "coarse_iterations": [m[2] for m in mixed64_steps],
+                               "rel_residual_max": float(max(m[3] for m in mixed64_steps)),
+                               "note": "the trajectory continued with FESTUNG_MIXED64: FP32 sweeps with the coarse "
+                                       "correction, refinement residual S C in FP64 (the last two of three steps)"},
         "modes_from_one_state": modes,
         "modes_note": "one step of every precision mode from the same C^n (initial guess C^n) and data, to the "
                       "same tolerance; err_vs_fp64 against an FP64 step at 1e-13 from that state",
